@@ -1,0 +1,153 @@
+"""Seeded synthetic inputs shared by the tests, the bench and the oracle checks.
+
+This module holds no arithmetic of the method: it only builds meshes, samples
+scalar fields at points and draws random numbers. It imports neither the
+CUDA binding nor the oracle.
+
+Recipes (the paper's GMSH meshes and media are not available):
+  * ``cube_mesh(n)``: the unit cube cut into n^3 hexahedra, each split into six
+    tetrahedra around its main diagonal (Kuhn/Freudenthal split), hexes in
+    lexicographic order with x fastest and the six tets of a hex consecutive;
+    ``jitter`` moves interior vertices, ``shuffle`` permutes each element's
+    local vertex order (keeping positive orientation) so that every face
+    orientation code occurs.
+  * Fields are turned into per-element coefficients by *sampling at domain
+    points* x_alpha = sum_i alpha_i v_i / n of each element (the Bezier
+    control-point positions), which is a synthetic recipe, not a projection.
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+
+__all__ = [
+    "cube_mesh", "multi_index_points", "sample_at_domain_points",
+    "c2_smooth_random", "c2_config_small", "gaussian_pulse", "random_state",
+    "PARITY_CONFIG", "SWEEP_CONFIG",
+]
+
+#: the FP64 parity workload: 4^3 hexes x 6 = 384 tets, N=3, M=1, T=0.5
+PARITY_CONFIG = dict(hexes=4, N=3, M=1, T=0.5, cfl=0.5)
+#: the FP32 throughput workload: 32^3 hexes x 6 = 196,608 tets, N=1..9, M=2
+SWEEP_CONFIG = dict(hexes=32, Ns=tuple(range(1, 10)), M=2, steps=100,
+                    source=(0.5, 0.5, 0.5), f0=10.0)
+
+
+def cube_mesh(n: int, jitter: float = 0.0, shuffle: bool = False, seed: int = 0,
+              lo: float = 0.0, hi: float = 1.0):
+    """Return (vxyz (nv,3) float64, etov (K,4) int64) for n^3 hexes x 6 tets."""
+    rng = np.random.default_rng(seed)
+    g = np.linspace(lo, hi, n + 1)
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")  # vertex (i, j, k)
+    vxyz = np.stack([X, Y, Z], axis=-1).transpose(2, 1, 0, 3).reshape(-1, 3).copy()
+    if jitter:
+        h = (hi - lo) / n
+        inner = np.ones(len(vxyz), dtype=bool)
+        for d in range(3):
+            inner &= (vxyz[:, d] > lo + 1e-12) & (vxyz[:, d] < hi - 1e-12)
+        vxyz[inner] += rng.uniform(-jitter * h, jitter * h, size=(inner.sum(), 3))
+
+    def vid(i, j, k):
+        return i + (n + 1) * (j + (n + 1) * k)
+
+    unit = np.eye(3, dtype=int)
+    tets = []
+    for k in range(n):
+        for j in range(n):
+            for i in range(n):
+                base = np.array([i, j, k])
+                for perm in itertools.permutations(range(3)):
+                    c = base.copy()
+                    vs = [vid(*c)]
+                    for ax in perm:
+                        c = c + unit[ax]
+                        vs.append(vid(*c))
+                    tets.append(vs)
+    etov = np.array(tets, dtype=np.int64)
+    if shuffle:
+        for e in range(len(etov)):
+            etov[e] = etov[e][rng.permutation(4)]
+    # positive orientation: swap two vertices where the volume is negative
+    P = vxyz[etov]
+    det = np.einsum("ki,ki->k", np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]), P[:, 3] - P[:, 0])
+    neg = det < 0
+    etov[neg, 2], etov[neg, 3] = etov[neg, 3].copy(), etov[neg, 2].copy()
+    return vxyz, etov
+
+
+def multi_index_points(n: int) -> np.ndarray:
+    """(N_p, 4) array of alpha / n in the library's multi-index order.
+
+    Order: for l in 0..n, for k in 0..n-l, for j in 0..n-l-k, alpha =
+    (n-j-k-l, j, k, l). For n = 0 the single point is the centroid.
+    """
+    out = []
+    for l in range(n + 1):
+        for k in range(n - l + 1):
+            for j in range(n - l - k + 1):
+                out.append((n - j - k - l, j, k, l))
+    a = np.array(out, dtype=np.float64)
+    if n == 0:
+        return np.full((1, 4), 0.25)
+    return a / n
+
+
+def sample_at_domain_points(vxyz, etov, n: int, field) -> np.ndarray:
+    """field(x (P,3)) sampled at every element's degree-n domain points, (K, N_p)."""
+    X = np.asarray(vxyz, dtype=np.float64)[np.asarray(etov)]
+    pts = np.einsum("pa,kai->kpi", multi_index_points(n), X)
+    K, P = pts.shape[:2]
+    return np.asarray(field(pts.reshape(-1, 3)), dtype=np.float64).reshape(K, P)
+
+
+def c2_config_small(x: np.ndarray) -> np.ndarray:
+    """c^2 = 1 + 0.5 sin(pi x) sin(pi y) sin(pi z) (the paper's 3D medium)."""
+    s = np.sin(np.pi * x)
+    return 1.0 + 0.5 * s[:, 0] * s[:, 1] * s[:, 2]
+
+
+def c2_smooth_random(seed: int = 0, modes: int = 8, jump: float = 1.5,
+                     plane=(0.3, 0.2, 1.0, 0.55)):
+    """A seeded smooth random medium in [0.5, 2] with a planar layer jump.
+
+    Sum of ``modes`` random low-frequency Fourier modes, affinely rescaled to
+    [0.5, 2] over a fixed probe grid, times ``jump`` where
+    a x + b y + c z > d (a plane not aligned with any mesh face).
+    """
+    rng = np.random.default_rng(seed)
+    kvec = rng.integers(1, 4, size=(modes, 3)) * np.pi
+    phase = rng.uniform(0, 2 * np.pi, size=modes)
+    amp = rng.normal(size=modes)
+
+    def raw(x):
+        return np.sum(amp[None, :] * np.cos(x @ kvec.T + phase[None, :]), axis=1)
+
+    g = np.linspace(0.0, 1.0, 33)
+    probe = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    r = raw(probe)
+    lo, hi = r.min(), r.max()
+    a, b, c, d = plane
+
+    def field(x):
+        v = 0.5 + 1.5 * np.clip((raw(x) - lo) / (hi - lo), 0.0, 1.0)
+        above = a * x[:, 0] + b * x[:, 1] + c * x[:, 2] > d
+        return np.where(above, jump * v, v)
+
+    return field
+
+
+def gaussian_pulse(center=(0.5, 0.5, 0.5), width: float = 0.1):
+    """p0 = exp(-|x - center|^2 / width^2)."""
+    c = np.asarray(center, dtype=np.float64)
+
+    def field(x):
+        return np.exp(-np.sum((x - c) ** 2, axis=1) / width ** 2)
+
+    return field
+
+
+def random_state(K: int, Np: int, seed: int = 0, dtype=np.float64) -> np.ndarray:
+    """Standard-normal state of shape (4, K, Np), rounded to ``dtype``."""
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((4, K, Np)).astype(dtype)
