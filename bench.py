@@ -1,0 +1,393 @@
+"""Throughput of the fused BBWADG LSRK stage on the FP32 sweep workload.
+
+Workload (synthetic, seeded): the unit cube cut into 32^3 hexes x 6 = 196,608
+affine tetrahedra, degrees N = 1..9, c^2 of degree M = 2 (a smooth random
+medium in [0.5, 2] with a planar x1.5 layer jump cutting through elements,
+sampled at the degree-2 domain points), a 10 Hz Ricker point source at the
+cube centre, Gaussian initial pressure.
+
+One bench step = one full LSRK4 step (5 stages) for each of the nine degrees,
+interleaved by stage (stage s for N = 1..9, then s+1), so every stage kernel
+starts with the other degrees' data (>= 6 GB) having streamed through the
+129 MB L2. The metric is DOF-updates per second per RK stage,
+4 K N_p / t_stage, aggregated over the sweep (sum of DOF updates / sum of
+kernel time); per-degree values are in ``sweep``.
+
+``--impl reference`` times the FP64 CPU oracle (one stage per degree on a
+bounded sub-mesh per step) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1808_08645_gb300 import inputs  # noqa: E402
+
+METRIC = "DOF-updates/s per RK stage vs N"
+UNIT = "DOF-updates/s"
+
+
+def np3(n):
+    return (n + 1) * (n + 2) * (n + 3) // 6
+
+
+def algorithmic_bytes_per_element(N: int, M: int, real: int = 4) -> float:
+    """Bytes one stage must move per element, averaged over the five stages.
+
+    q_in read, q_out and res written (12 N_p values) on every stage; res read
+    (4 N_p) on stages 1-4 only (a_0 = 0); c^2 (M_p values), geometry (9 values)
+    and the packed connectivity (16 B). Neighbour traces are re-reads of q_in
+    and not counted.
+    """
+    vals = (12 + 4 * 4 / 5) * np3(N) + np3(M) + 9
+    return vals * real + 16
+
+
+# ---------------------------------------------------------------------------
+# clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sms, maxs, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                maxs.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "0x1", "1"):
+                    reasons.add(nm)
+        if not sms:
+            return None
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxs),
+                "reasons": sorted(reasons), "samples": len(sms)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+
+def make_workload(N: int, M: int, vxyz, etov, c2_field, pulse):
+    c2 = inputs.sample_at_domain_points(vxyz, etov, M, c2_field)
+    K = len(etov)
+    q0 = np.zeros((4, K, np3(N)))
+    q0[0] = inputs.sample_at_domain_points(vxyz, etov, N, pulse)
+    return c2, q0
+
+
+def run_gpu(args):
+    import torch
+
+    from paper_1808_08645_gb300 import binding as B
+    from paper_1808_08645_gb300 import build as libbuild
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0:
+        libbuild.build()
+    if dist is not None:
+        dist.barrier()
+
+    cfg = inputs.SWEEP_CONFIG
+    Ns = [int(x) for x in args.Ns.split(",")]
+    M = cfg["M"]
+    vxyz, etov = inputs.cube_mesh(args.hexes)
+    K = len(etov)
+    field = inputs.c2_smooth_random(seed=0)
+    pulse = inputs.gaussian_pulse()
+    stream = torch.cuda.Stream()
+    solvers, host_q0 = {}, {}
+    for N in Ns:
+        c2, q0 = make_workload(N, M, vxyz, etov, field, pulse)
+        s = B.Solver(vxyz, etov, N, M, B.F32, stream=stream.cuda_stream)
+        s.set_c2(c2)
+        s.set_state(q0)
+        s.set_point_source(np.array(cfg["source"]), f0=cfg["f0"])
+        solvers[N] = s
+        host_q0[N] = q0
+    dts = {N: solvers[N].cfl_dt(0.5) for N in Ns}
+
+    def sweep_step(events=None):
+        for st in range(5):
+            for N in Ns:
+                if events is not None:
+                    events[N][st][0].record(stream)
+                solvers[N].stage(st, dts[N])
+                if events is not None:
+                    events[N][st][1].record(stream)
+
+    # warm-up
+    for _ in range(args.warmup):
+        sweep_step()
+    torch.cuda.synchronize()
+
+    ev = [{N: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(5)] for N in Ns} for _ in range(args.steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0.record(stream)
+    for k in range(args.steps):
+        sweep_step(ev[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if dist is not None:
+        dist.barrier()
+    for s in solvers.values():
+        s.sync()  # surfaces any asynchronous error (e.g. a non-finite state)
+
+    total_ms = t0.elapsed_time(t1)
+    kern_ms = {N: [sum(ev[k][N][st][0].elapsed_time(ev[k][N][st][1]) for st in range(5))
+                   for k in range(args.steps)] for N in Ns}
+    dof_stage = {N: 4 * K * np3(N) for N in Ns}
+    per_n = {}
+    for N in Ns:
+        t_stage = statistics.median(kern_ms[N]) / 5 / 1e3
+        per_n[str(N)] = {"dof_updates_per_s": dof_stage[N] / t_stage,
+                         "us_per_stage": t_stage * 1e6,
+                         "achieved_gbs": algorithmic_bytes_per_element(N, M) * K / t_stage / 1e9}
+    dofs_total = sum(5 * dof_stage[N] for N in Ns) * args.steps
+    value_local = dofs_total / (total_ms / 1e3)
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        value = dofs_total * world / (total_ms / 1e3)
+    else:
+        value = value_local
+
+    # dominant kernel: the largest share of kernel time
+    top = max(Ns, key=lambda N: statistics.median(kern_ms[N]))
+    t_launch = statistics.mean([x / 5 for x in kern_ms[top]]) / 1e3  # mean launch, seconds
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = algorithmic_bytes_per_element(top, M) * K / t_launch / 1e9
+    traffic = load_traffic(top)
+
+    # end to end through the public API with host buffers
+    e2e = run_e2e(solvers, host_q0, Ns, dts, K, args.e2e_steps, stream)
+
+    out = None
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {
+                "workload": f"BBWADG acoustic LSRK4 stage sweep, {args.hexes}^3 hexes x 6 = {K} "
+                            f"affine tets, N={Ns[0]}..{Ns[-1]}, M={M}, smooth random c2 in [0.5,2] "
+                            "with planar layer jump, Ricker point source",
+                "mesh_elements": K, "Ns": Ns, "M": M,
+                "step": "one LSRK4 step (5 stages) per degree, interleaved by stage",
+                "l2": "inputs larger than L2: between two stages of one degree the other "
+                      "degrees stream >= 6 GB through the 129 MB L2",
+                "parallelism": f"replicas x{world}",
+            },
+            "sweep": per_n,
+            "roofline": {"bound": "hbm", "kernel": f"stage_kernel N={top} M={M} f32",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "algorithmic_bytes_per_launch": algorithmic_bytes_per_element(top, M) * K,
+                         "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"},
+            "e2e": e2e,
+            "gpu_launches": 5 * len(Ns) * args.steps,
+            "clocks": clk,
+        }
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(args)
+    for s in solvers.values():
+        s.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return out
+
+
+def run_e2e(solvers, host_q0, Ns, dts, K, steps, stream):
+    """Upload the initial state from host memory, run ``steps`` RK steps, read
+    the final state back into host memory, per degree; wall-clock timed."""
+    import torch
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    h2d = d2h = 0
+    for N in Ns:
+        s = solvers[N]
+        s.set_state(host_q0[N])
+        s.step(dts[N], steps)
+        q, _ = s.get_state()
+        h2d += 4 * q.size
+        d2h += 4 * q.size
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t
+    dofs = sum(5 * steps * 4 * K * np3(N) for N in Ns)
+    return {"value": dofs / wall, "unit": UNIT, "h2d_bytes_per_step": h2d / steps,
+            "d2h_bytes_per_step": d2h / steps,
+            "note": f"per degree: bbw_set_state (host FP64 -> device FP32), {steps} RK steps, "
+                    "bbw_get_state (device -> host); bytes per step amortised over the run"}
+
+
+def load_traffic(N: int):
+    """DRAM bytes per launch of the stage kernel from the committed ncu summary, if any."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(path) as fh:
+            data = json.load(fh)
+        return data.get(str(N))
+    except (OSError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle arms
+
+def _oracle_sample(hexes: int, Ns, reps: int):
+    """Time one oracle stage per degree on a hexes^3 x 6 sub-mesh; returns
+    (DOF updates, seconds)."""
+    from oracle.acoustic import AcousticOracle
+    cfg = inputs.SWEEP_CONFIG
+    vxyz, etov = inputs.cube_mesh(hexes)
+    field = inputs.c2_smooth_random(seed=0)
+    pulse = inputs.gaussian_pulse()
+    K = len(etov)
+    dofs, secs = 0, 0.0
+    for N in Ns:
+        c2, q0 = make_workload(N, cfg["M"], vxyz, etov, field, pulse)
+        orc = AcousticOracle(vxyz, etov, N, cfg["M"], c2)
+        orc.set_point_source(np.array(cfg["source"]), f0=cfg["f0"])
+        res = np.zeros_like(q0)
+        orc.stage(q0, res, 0, 1e-4, 0.0)  # warm caches
+        t = time.perf_counter()
+        q, r = q0, res
+        for i in range(reps):
+            q, r = orc.stage(q, r, i % 5, 1e-4, 0.0)
+        secs += time.perf_counter() - t
+        dofs += reps * 4 * K * np3(N)
+    return dofs, secs
+
+
+def cpu_baseline(args):
+    """The FP64 oracle on one host core, in a fresh process (spawned)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    Ns = [int(x) for x in args.Ns.split(",")]
+    code = (f"import sys, json; sys.path.insert(0, {ROOT!r}); import bench; "
+            f"d, s = bench._oracle_sample({args.cpu_hexes}, {Ns!r}, 1); print(json.dumps([d, s]))")
+    p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=1800)
+    if p.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": "failed: " + p.stderr.strip().splitlines()[-1] if p.stderr else "failed"}
+    d, s = json.loads(p.stdout.strip().splitlines()[-1])
+    K = 6 * args.cpu_hexes ** 3
+    return {"value": d / s, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one FP64 oracle stage per degree N={Ns[0]}..{Ns[-1]} on the "
+                      f"{args.cpu_hexes}^3 x 6 = {K}-tet sub-cube of the same workload "
+                      f"(same c2 field, source, pulse); {s:.1f} s of CPU work, 1 thread"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    Ns = [int(x) for x in args.Ns.split(",")]
+    for _ in range(args.warmup):
+        _oracle_sample(args.ref_hexes, Ns, 1)
+    per = []
+    dofs_total, secs_total = 0, 0.0
+    for _ in range(args.steps):
+        d, s = _oracle_sample(args.ref_hexes, Ns, 1)
+        dofs_total += d
+        secs_total += s
+        per.append(s)
+    value = dofs_total / secs_total
+    K = 6 * args.ref_hexes ** 3
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs_total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"FP64 oracle: one stage per degree N={Ns[0]}..{Ns[-1]} on the "
+                               f"{args.ref_hexes}^3 x 6 = {K}-tet sub-cube of the sweep workload",
+                   "Ns": Ns, "M": inputs.SWEEP_CONFIG["M"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{K}-tet sub-cube, one stage per degree per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--Ns", default="1,2,3,4,5,6,7,8,9")
+    ap.add_argument("--hexes", type=int, default=inputs.SWEEP_CONFIG["hexes"])
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--cpu-hexes", type=int, default=3)
+    ap.add_argument("--ref-hexes", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        ap.error("--warmup must be >= 3")
+    out = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

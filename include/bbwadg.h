@@ -1,0 +1,232 @@
+/*
+ * bbwadg.h -- C ABI of the GB300 BBWADG acoustic solver (libbbwadg.so).
+ *
+ * Bernstein-Bezier weight-adjusted DG (Guo & Chan) for the first-order
+ * acoustic wave equation (Eq. 1)
+ *
+ *     (1/c^2) dp/dt + div u = f,      du/dt + grad p = 0,
+ *
+ * on affine tetrahedra (Sec. 2), in the strong DG form with penalty fluxes of
+ * Eq. (2) and the weight-adjusted mass of Eq. (4). One call of bbw_stage() is
+ * one stage of the five-stage low-storage RK4 (Sec. 6.3.1) over all
+ * elements, fused in one GPU kernel: sparse Bernstein derivative (Sec. 4),
+ * face flux and factored lift L^f = E_L L0 (Sec. 4), the product with the
+ * degree-M Bernstein polynomial c^2_M (Eq. 11) and the L2 projection back to
+ * degree N by the telescoped form of Eq. (20), and the LSRK update.
+ *
+ * Conventions
+ * -----------
+ *  - Barycentrics (Sec. 2): lambda_0 is attached to the element's first vertex
+ *    etov[e][0], lambda_m to etov[e][m]. Face f of an element is the face
+ *    opposite vertex f ({lambda_f = 0}).
+ *  - Multi-index order for degree n (N_p = (n+1)(n+2)(n+3)/6 entries):
+ *        for l in 0..n, for k in 0..n-l, for j in 0..n-l-k:
+ *            alpha = (n-j-k-l, j, k, l)
+ *    Coefficient i of an element is the Bernstein coefficient of
+ *    B^n_alpha = n!/(alpha!) lambda^alpha for the i-th alpha in that order.
+ *  - State arrays are [4][K][N_p], fields (p, u, v, w), row-major.
+ *  - c^2 arrays are [K][M_p], Bernstein coefficients of degree M in the same
+ *    order; every coefficient must be > 0 (then c^2_M > 0 everywhere).
+ *  - Walls (faces without a neighbour) are p = 0 mirrors: p+ = -p, u+ = u.
+ *  - Face orientation code fperm in 0..5: the local vertices of a face are its
+ *    three element vertices other than f, in increasing order (v0, v1, v2);
+ *    the neighbour's face f' has (w0, w1, w2) likewise. Code c means that
+ *    v_x and w_{PERM[c][x]} are the same mesh vertex, with
+ *    PERM = {012, 021, 102, 120, 201, 210}.
+ *
+ * Ownership and errors
+ * --------------------
+ *  - The caller owns every host array passed in; the library copies what it
+ *    needs before returning and keeps no pointer to it.
+ *  - The library owns all device buffers of a solver. The *_device calls copy
+ *    from/to caller-owned device memory on the solver's stream.
+ *  - Every call returns a bbw_status; no exception or abort crosses the ABI.
+ *    bbw_last_error() returns a thread-local message for the last failure.
+ *  - GPU work is asynchronous on the solver's stream. Asynchronous failures
+ *    (a CUDA error, a non-finite value found by the stage kernel) are
+ *    reported by the next bbw_sync() or bbw_get_*() call.
+ *  - A solver must not be used from two host threads at once.
+ */
+#ifndef BBWADG_H
+#define BBWADG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bbw_solver bbw_solver; /* opaque, library-owned */
+
+typedef enum bbw_status {
+  BBW_OK = 0,
+  BBW_ERR_ARG = -1,          /* bad argument (null pointer, size, range)       */
+  BBW_ERR_MESH = -2,         /* inverted, degenerate or non-manifold mesh      */
+  BBW_ERR_NONPOS_C2 = -3,    /* a c^2 Bernstein coefficient is <= 0 or not finite */
+  BBW_ERR_CUDA = -4,         /* a CUDA runtime call failed                      */
+  BBW_ERR_NONFINITE = -5,    /* the stage kernel produced a NaN or Inf          */
+  BBW_ERR_TIMEOUT = -6,      /* reserved for bounded device waits               */
+  BBW_ERR_UNSUPPORTED = -7   /* (N, M, precision) not compiled into the library */
+} bbw_status;
+
+enum { BBW_MAX_N = 9, BBW_MAX_M = 3 };
+enum { BBW_F32 = 32, BBW_F64 = 64 };
+
+/* Library version (major*10000 + minor*100 + patch). */
+int bbw_version(void);
+
+/* Thread-local text of the last error; never NULL. */
+const char* bbw_last_error(void);
+
+/*
+ * Create a solver on the current CUDA device.
+ *   vxyz      [nverts][3] vertex coordinates.
+ *   etov      [K][4] vertex ids per element (0-based); elements must have
+ *             positive orientation (det[v1-v0, v2-v0, v3-v0] > 0).
+ *   N         solution degree, 1..BBW_MAX_N.
+ *   M         degree of the c^2 approximation, 0..BBW_MAX_M (Sec. 5).
+ *   precision BBW_F32 or BBW_F64: arithmetic and storage type on the GPU.
+ *   cuda_stream  cudaStream_t to run on (NULL = the legacy default stream).
+ * Builds connectivity (faces matched by their vertex triples), geometric
+ * factors, operator tables and the projection constants c_j of Theorem 5.3;
+ * c^2 starts at 1, the state at 0, tau_p = tau_u = 1, t = 0, no source.
+ * Errors: BBW_ERR_ARG, BBW_ERR_MESH (inverted/degenerate element, a face
+ * shared by more than two elements), BBW_ERR_UNSUPPORTED, BBW_ERR_CUDA.
+ */
+bbw_status bbw_create(int64_t nverts, const double* vxyz, int64_t K, const int64_t* etov,
+                      int N, int M, int precision, void* cuda_stream, bbw_solver** out);
+
+/* Free all device and host memory of a solver (NULL is ignored). */
+void bbw_destroy(bbw_solver* s);
+
+/* Sizes of a solver; any output pointer may be NULL. */
+bbw_status bbw_info(const bbw_solver* s, int64_t* K, int* N, int* M, int* Np, int* Mp,
+                    int* precision);
+
+/*
+ * Connectivity (Sec. 4: node-to-node maps on shared faces).
+ *   etoe  [K][4] neighbour element across face f, -1 on a wall.
+ *   etof  [K][4] the neighbour's local face, -1 on a wall.
+ *   fperm [K][4] face orientation code (see Conventions), -1 on a wall.
+ */
+bbw_status bbw_get_connectivity(const bbw_solver* s, int32_t* etoe, int8_t* etof, int8_t* fperm);
+
+/*
+ * Neighbour coefficient of every face node: nmap[e][f][a] is
+ * nb * N_p + i, the flat index of the neighbour coefficient that shares the
+ * physical domain point of face node a of face f (face nodes enumerated as
+ * (b0, b1, b2) over the face's local vertices, b2 outer, b1 inner); -1 on a wall.
+ * nmap has K * 4 * (N+1)(N+2)/2 entries.
+ */
+bbw_status bbw_get_face_node_map(const bbw_solver* s, int64_t* nmap);
+
+/*
+ * Host-only mesh analysis, without a GPU or a solver: the same connectivity,
+ * face-node map and geometry a solver of degree N builds at bbw_create.
+ * Outputs as for bbw_get_connectivity / bbw_get_face_node_map /
+ * bbw_get_geometry; nmap, grad and vol may be NULL. Errors: BBW_ERR_ARG,
+ * BBW_ERR_MESH, BBW_ERR_UNSUPPORTED (N out of range).
+ */
+bbw_status bbw_mesh_analyze(int64_t nverts, const double* vxyz, int64_t K, const int64_t* etov, int N,
+                            int32_t* etoe, int8_t* etof, int8_t* fperm, int64_t* nmap, double* grad,
+                            double* vol);
+
+/* Geometry: grad [K][4][3] = d lambda_m / d x_i, vol [K] element volumes. */
+bbw_status bbw_get_geometry(const bbw_solver* s, double* grad, double* vol);
+
+/*
+ * Per-element Bernstein coefficients of c^2_M (Sec. 5, preprocessing), [K][M_p].
+ * Errors: BBW_ERR_NONPOS_C2 if any coefficient is <= 0 or not finite
+ * (positivity of the coefficients guarantees c^2_M > 0 by the convex hull
+ * property); the solver keeps its previous c^2 then.
+ */
+bbw_status bbw_set_c2(bbw_solver* s, const double* c2);
+
+/* Penalty parameters tau_p, tau_u >= 0 of the fluxes (Sec. 3.1). */
+bbw_status bbw_set_params(bbw_solver* s, double tau_p, double tau_u);
+
+/*
+ * Set the state q [4][K][N_p] and, if res != NULL, the RK residual register
+ * res [4][K][N_p] (else res = 0), and the time t. The stage counter resets to 0.
+ */
+bbw_status bbw_set_state(bbw_solver* s, const double* q, const double* res, double t);
+
+/*
+ * As bbw_set_state, from caller-owned device memory in the solver's layout
+ * [4][K][N_p]; dtype is BBW_F32 or BBW_F64 (converted if it differs from the
+ * solver precision). res may be NULL. Ordered on the solver's stream.
+ */
+bbw_status bbw_set_state_device(bbw_solver* s, const void* q, const void* res, int dtype, double t);
+
+/* Read back q (and res if non-NULL) as FP64 [4][K][N_p] and the time t (if non-NULL). */
+bbw_status bbw_get_state(bbw_solver* s, double* q, double* res, double* t);
+
+/* Copy q (and res if non-NULL) to caller-owned device memory of type dtype. */
+bbw_status bbw_get_state_device(bbw_solver* s, void* q, void* res, int dtype);
+
+/*
+ * Point source delta(x - xs) r(t) in the pressure equation, with the Ricker
+ * wavelet r(t) = (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2).
+ * It is placed in the lowest-numbered element whose closure contains xs,
+ * with coefficients M^{-1} B(xs) / |D^k| and enters inside the
+ * weight-adjusted bracket of the p equation. *elem receives that element
+ * (may be NULL). Errors: BBW_ERR_ARG if xs lies outside the mesh.
+ */
+bbw_status bbw_set_point_source(bbw_solver* s, const double* xs, double f0, double t0,
+                                int64_t* elem);
+
+/* A source with caller-given coefficients [N_p] on element elem, same wavelet. */
+bbw_status bbw_set_source(bbw_solver* s, int64_t elem, const double* coeffs, double f0,
+                          double t0);
+
+/* Remove the source. */
+bbw_status bbw_clear_source(bbw_solver* s);
+
+/*
+ * One LSRK stage s (0..4) with step dt: evaluates the right-hand side at
+ * t + c_s dt, res = a_s res + dt rhs, q = q + b_s res. After s == 4 the
+ * solver time advances by dt. Asynchronous.
+ */
+bbw_status bbw_stage(bbw_solver* s, int stage, double dt);
+
+/* nsteps full RK steps (5 stages each) of size dt. Asynchronous. */
+bbw_status bbw_step(bbw_solver* s, double dt, int64_t nsteps);
+
+/*
+ * CFL time step dt = cfl / (sqrt(max c^2 coefficient) * (N+1)(N+3)/3 *
+ * max_{k,f} |f|/|D^k|). (The paper states no rule; this is the library's.)
+ */
+bbw_status bbw_cfl_dt(const bbw_solver* s, double cfl, double* dt);
+
+/* Advance by T: nsteps = ceil(T / bbw_cfl_dt), dt = T / nsteps. Outputs may be NULL. */
+bbw_status bbw_advance(bbw_solver* s, double T, double cfl, double* dt_used, int64_t* nsteps);
+
+/* Wait for the solver's stream; returns the first pending asynchronous error. */
+bbw_status bbw_sync(bbw_solver* s);
+
+/* Current time and number of stages run since the last set_state. */
+bbw_status bbw_get_time(const bbw_solver* s, double* t, int64_t* stages);
+
+/*
+ * Constants. c [N+1]: the c_j of Theorem 5.3 for P^{N+M}_N, from the
+ * eigenvalues of the Bernstein mass matrix (Lemma 5.2, Corollary 1).
+ * a, b, c [5]: the LSRK coefficients and stage times (any may be NULL).
+ */
+bbw_status bbw_projection_coeffs(int N, int M, double* c);
+bbw_status bbw_lsrk_coeffs(double* a, double* b, double* c);
+
+/*
+ * The weight-adjusted update alone (the paper's timed "update kernel" minus
+ * the RK part): out = P^{N+M}_N (c2_M * rhs) per element, by the product of
+ * Eq. (11) and the telescoped projection of Eq. (20).
+ *   rhs [K][N_p], c2 [K][M_p], out [K][N_p]: device pointers of type precision.
+ *   stream: cudaStream_t (NULL = default). Asynchronous; out may not alias rhs.
+ */
+bbw_status bbw_wadg_update(int N, int M, int precision, int64_t K, const void* rhs,
+                           const void* c2, void* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BBWADG_H */

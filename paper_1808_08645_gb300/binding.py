@@ -1,0 +1,282 @@
+"""ctypes binding of libbbwadg (include/bbwadg.h), argument marshalling only.
+
+Every function here forwards to the C ABI of the same name; no step of the
+solver runs in Python. Host arrays are numpy arrays (copied to contiguous
+float64/int64 as the ABI requires); device arrays are anything with a
+``data_ptr()`` (torch tensors) or a raw integer address. Importing this module
+never loads the library; the first call does, and raises ``RuntimeError`` if
+``_lib/libbbwadg.so`` has not been built (there is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+__all__ = ["BBWError", "lib", "lib_path", "Solver", "mesh_analyze", "projection_coeffs",
+           "lsrk_coeffs", "wadg_update", "EXPORTS", "F32", "F64"]
+
+F32, F64 = 32, 64
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+STATUS = {0: "BBW_OK", -1: "BBW_ERR_ARG", -2: "BBW_ERR_MESH", -3: "BBW_ERR_NONPOS_C2",
+          -4: "BBW_ERR_CUDA", -5: "BBW_ERR_NONFINITE", -6: "BBW_ERR_TIMEOUT",
+          -7: "BBW_ERR_UNSUPPORTED"}
+
+_p = C.c_void_p
+_i64 = C.c_int64
+_d = C.c_double
+_int = C.c_int
+_dp = C.POINTER(C.c_double)
+_i64p = C.POINTER(C.c_int64)
+_i32p = C.POINTER(C.c_int32)
+_i8p = C.POINTER(C.c_int8)
+_ip = C.POINTER(C.c_int)
+
+# name -> (restype, argtypes), in the order of include/bbwadg.h
+EXPORTS = {
+    "bbw_version": (_int, []),
+    "bbw_last_error": (C.c_char_p, []),
+    "bbw_create": (_int, [_i64, _dp, _i64, _i64p, _int, _int, _int, _p, C.POINTER(_p)]),
+    "bbw_destroy": (None, [_p]),
+    "bbw_info": (_int, [_p, _i64p, _ip, _ip, _ip, _ip, _ip]),
+    "bbw_get_connectivity": (_int, [_p, _i32p, _i8p, _i8p]),
+    "bbw_get_face_node_map": (_int, [_p, _i64p]),
+    "bbw_mesh_analyze": (_int, [_i64, _dp, _i64, _i64p, _int, _i32p, _i8p, _i8p, _i64p, _dp, _dp]),
+    "bbw_get_geometry": (_int, [_p, _dp, _dp]),
+    "bbw_set_c2": (_int, [_p, _dp]),
+    "bbw_set_params": (_int, [_p, _d, _d]),
+    "bbw_set_state": (_int, [_p, _dp, _dp, _d]),
+    "bbw_set_state_device": (_int, [_p, _p, _p, _int, _d]),
+    "bbw_get_state": (_int, [_p, _dp, _dp, _dp]),
+    "bbw_get_state_device": (_int, [_p, _p, _p, _int]),
+    "bbw_set_point_source": (_int, [_p, _dp, _d, _d, _i64p]),
+    "bbw_set_source": (_int, [_p, _i64, _dp, _d, _d]),
+    "bbw_clear_source": (_int, [_p]),
+    "bbw_stage": (_int, [_p, _int, _d]),
+    "bbw_step": (_int, [_p, _d, _i64]),
+    "bbw_cfl_dt": (_int, [_p, _d, _dp]),
+    "bbw_advance": (_int, [_p, _d, _d, _dp, _i64p]),
+    "bbw_sync": (_int, [_p]),
+    "bbw_get_time": (_int, [_p, _dp, _i64p]),
+    "bbw_projection_coeffs": (_int, [_int, _int, _dp]),
+    "bbw_lsrk_coeffs": (_int, [_dp, _dp, _dp]),
+    "bbw_wadg_update": (_int, [_int, _int, _int, _i64, _p, _p, _p, _p]),
+}
+
+
+class BBWError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+
+
+_LIB = None
+
+
+def lib_path() -> str:
+    return os.path.join(_HERE, "_lib", "libbbwadg.so")
+
+
+def lib():
+    """The loaded library (loads it on first use; raises if not built)."""
+    global _LIB
+    if _LIB is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libbbwadg.so is not built ({path}); run "
+                               "`python -m paper_1808_08645_gb300.build`")
+        L = C.CDLL(path)
+        for name, (res, args) in EXPORTS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise BBWError(status, where, lib().bbw_last_error().decode())
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+def _dev(x) -> int | None:
+    if x is None:
+        return None
+    return int(x.data_ptr()) if hasattr(x, "data_ptr") else int(x)
+
+
+def projection_coeffs(N: int, M: int) -> np.ndarray:
+    out = np.zeros(N + 1)
+    _check(lib().bbw_projection_coeffs(N, M, _ptr(out, C.c_double)), "bbw_projection_coeffs")
+    return out
+
+
+def lsrk_coeffs():
+    a, b, c = np.zeros(5), np.zeros(5), np.zeros(5)
+    _check(lib().bbw_lsrk_coeffs(_ptr(a, C.c_double), _ptr(b, C.c_double), _ptr(c, C.c_double)),
+           "bbw_lsrk_coeffs")
+    return a, b, c
+
+
+def mesh_analyze(vxyz, etov, N: int):
+    """Host-only connectivity, face-node map and geometry (bbw_mesh_analyze)."""
+    vxyz = _f64(vxyz)
+    etov = np.ascontiguousarray(etov, dtype=np.int64)
+    K = len(etov)
+    nfp = (N + 1) * (N + 2) // 2
+    etoe = np.empty((K, 4), np.int32)
+    etof = np.empty((K, 4), np.int8)
+    fperm = np.empty((K, 4), np.int8)
+    nmap = np.empty((K, 4, nfp), np.int64)
+    grad = np.empty((K, 4, 3))
+    vol = np.empty(K)
+    _check(lib().bbw_mesh_analyze(len(vxyz), _ptr(vxyz, C.c_double), K, _ptr(etov, C.c_int64), N,
+                                  _ptr(etoe, C.c_int32), _ptr(etof, C.c_int8), _ptr(fperm, C.c_int8),
+                                  _ptr(nmap, C.c_int64), _ptr(grad, C.c_double), _ptr(vol, C.c_double)),
+           "bbw_mesh_analyze")
+    return dict(etoe=etoe, etof=etof, fperm=fperm, nmap=nmap, grad=grad, vol=vol)
+
+
+def wadg_update(N: int, M: int, precision: int, K: int, rhs, c2, out, stream=None):
+    """bbw_wadg_update on device arrays (torch tensors or raw addresses)."""
+    _check(lib().bbw_wadg_update(N, M, precision, K, _dev(rhs), _dev(c2), _dev(out), _dev(stream)),
+           "bbw_wadg_update")
+
+
+class Solver:
+    """Owner of one ``bbw_solver`` handle; methods map one-to-one to the ABI."""
+
+    def __init__(self, vxyz, etov, N: int, M: int, precision: int = F32, stream=None):
+        vxyz = _f64(vxyz)
+        etov = np.ascontiguousarray(etov, dtype=np.int64)
+        h = C.c_void_p()
+        _check(lib().bbw_create(len(vxyz), _ptr(vxyz, C.c_double), len(etov), _ptr(etov, C.c_int64),
+                                N, M, precision, _dev(stream), C.byref(h)), "bbw_create")
+        self._h = h
+        self.K, self.N, self.M, self.precision = len(etov), N, M, precision
+        self.Np = (N + 1) * (N + 2) * (N + 3) // 6
+        self.Nfp = (N + 1) * (N + 2) // 2
+        self.Mp = (M + 1) * (M + 2) * (M + 3) // 6
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().bbw_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- mesh --------------------------------------------------------------
+    def connectivity(self):
+        etoe = np.empty((self.K, 4), np.int32)
+        etof = np.empty((self.K, 4), np.int8)
+        fperm = np.empty((self.K, 4), np.int8)
+        _check(lib().bbw_get_connectivity(self._h, _ptr(etoe, C.c_int32), _ptr(etof, C.c_int8),
+                                          _ptr(fperm, C.c_int8)), "bbw_get_connectivity")
+        return etoe, etof, fperm
+
+    def face_node_map(self):
+        out = np.empty((self.K, 4, self.Nfp), np.int64)
+        _check(lib().bbw_get_face_node_map(self._h, _ptr(out, C.c_int64)), "bbw_get_face_node_map")
+        return out
+
+    def geometry(self):
+        grad = np.empty((self.K, 4, 3))
+        vol = np.empty(self.K)
+        _check(lib().bbw_get_geometry(self._h, _ptr(grad, C.c_double), _ptr(vol, C.c_double)),
+               "bbw_get_geometry")
+        return grad, vol
+
+    # -- inputs -------------------------------------------------------------
+    def set_c2(self, c2):
+        c2 = _f64(c2).reshape(self.K, self.Mp)
+        _check(lib().bbw_set_c2(self._h, _ptr(c2, C.c_double)), "bbw_set_c2")
+
+    def set_params(self, tau_p: float, tau_u: float):
+        _check(lib().bbw_set_params(self._h, tau_p, tau_u), "bbw_set_params")
+
+    def set_state(self, q, res=None, t: float = 0.0):
+        q = _f64(q).reshape(4, self.K, self.Np)
+        r = None if res is None else _f64(res).reshape(4, self.K, self.Np)
+        _check(lib().bbw_set_state(self._h, _ptr(q, C.c_double),
+                                   None if r is None else _ptr(r, C.c_double), t), "bbw_set_state")
+
+    def set_state_device(self, q, res=None, dtype: int = F32, t: float = 0.0):
+        _check(lib().bbw_set_state_device(self._h, _dev(q), _dev(res), dtype, t), "bbw_set_state_device")
+
+    def get_state(self, with_res: bool = False):
+        q = np.empty((4, self.K, self.Np))
+        r = np.empty((4, self.K, self.Np)) if with_res else None
+        t = C.c_double()
+        _check(lib().bbw_get_state(self._h, _ptr(q, C.c_double),
+                                   None if r is None else _ptr(r, C.c_double), C.byref(t)),
+               "bbw_get_state")
+        return (q, r, t.value) if with_res else (q, t.value)
+
+    def get_state_device(self, q, res=None, dtype: int = F32):
+        _check(lib().bbw_get_state_device(self._h, _dev(q), _dev(res), dtype), "bbw_get_state_device")
+
+    def set_point_source(self, xs, f0: float = 10.0, t0: float | None = None) -> int:
+        xs = _f64(xs)
+        e = C.c_int64()
+        _check(lib().bbw_set_point_source(self._h, _ptr(xs, C.c_double), f0,
+                                          1.0 / f0 if t0 is None else t0, C.byref(e)),
+               "bbw_set_point_source")
+        return e.value
+
+    def set_source(self, elem: int, coeffs, f0: float, t0: float):
+        c = _f64(coeffs)
+        _check(lib().bbw_set_source(self._h, elem, _ptr(c, C.c_double), f0, t0), "bbw_set_source")
+
+    def clear_source(self):
+        _check(lib().bbw_clear_source(self._h), "bbw_clear_source")
+
+    # -- time stepping -------------------------------------------------------
+    def stage(self, s: int, dt: float):
+        _check(lib().bbw_stage(self._h, s, dt), "bbw_stage")
+
+    def step(self, dt: float, nsteps: int = 1):
+        _check(lib().bbw_step(self._h, dt, nsteps), "bbw_step")
+
+    def cfl_dt(self, cfl: float) -> float:
+        dt = C.c_double()
+        _check(lib().bbw_cfl_dt(self._h, cfl, C.byref(dt)), "bbw_cfl_dt")
+        return dt.value
+
+    def advance(self, T: float, cfl: float):
+        dt = C.c_double()
+        n = C.c_int64()
+        _check(lib().bbw_advance(self._h, T, cfl, C.byref(dt), C.byref(n)), "bbw_advance")
+        return dt.value, n.value
+
+    def sync(self):
+        _check(lib().bbw_sync(self._h), "bbw_sync")
+
+    def time(self):
+        t = C.c_double()
+        n = C.c_int64()
+        _check(lib().bbw_get_time(self._h, C.byref(t), C.byref(n)), "bbw_get_time")
+        return t.value, n.value

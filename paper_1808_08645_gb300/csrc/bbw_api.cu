@@ -1,0 +1,834 @@
+// bbw_api.cu -- host side of libbbwadg: mesh setup, constants, state
+// management and the C ABI declared in include/bbwadg.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "bbw_common.h"
+#include "bbw_ops.h"
+#include "bbw_stage.cuh"
+#include "bbwadg.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+bbw_status fail(bbw_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+#define BBW_CUDA(call)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(BBW_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));    \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// constants
+
+// Eigenvalue of the normalised degree-n Bernstein mass matrix on the
+// tetrahedron for modal degree k <= n: (n!)^2 3! / ((n+k+3)! (n-k)!).
+// (Lemma 5.2 states M_N is diagonal in a modal basis with one eigenvalue per
+// modal degree; this is the closed form of those eigenvalues.)
+long double mass_eig(int n, int k) {
+  return expl(2.0L * lgammal(n + 1.0L) + logl(6.0L) - lgammal(n + k + 4.0L) - lgammal(n - k + 1.0L));
+}
+
+// c_j of Theorem 5.3: in the modal basis the decomposition reads, for each
+// modal degree k = 0..N, sum_{j=0}^{N-k} c_j lam^{N-j}_k = lam^{N+M}_k
+// (Corollary 1 and Lemma 5.2 with the proof of Theorem 5.3); solved
+// top-down from k = N.
+void projection_coeffs(int N, int M, double* c) {
+  long double cc[bbw::kMaxN + 1] = {};
+  for (int k = N; k >= 0; --k) {
+    long double s = mass_eig(N + M, k);
+    for (int j = 0; j < N - k; ++j) s -= cc[j] * mass_eig(N - j, k);
+    cc[N - k] = s / mass_eig(k, k);
+  }
+  for (int j = 0; j <= N; ++j) c[j] = double(cc[j]);
+}
+
+// Carpenter-Kennedy five-stage fourth-order 2N-storage RK coefficients.
+const double kRkA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                        -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+const double kRkB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                        1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                        2277821191437.0 / 14882151754819.0};
+
+// Stage times from the equivalent Butcher rows: stage s sees
+// q_0 + h sum_{m<s} A[s][m] F_m, A[s][m] = sum_{i=m}^{s-1} b_i prod_{r=m+1}^{i} a_r.
+std::array<double, 5> rk_stage_times() {
+  std::array<double, 5> c{};
+  for (int s = 1; s < 5; ++s) {
+    double acc = 0.0;
+    for (int m = 0; m < s; ++m)
+      for (int i = m; i < s; ++i) {
+        double p = kRkB[i];
+        for (int r = m + 1; r <= i; ++r) p *= kRkA[r];
+        acc += p;
+      }
+    c[s] = acc;
+  }
+  return c;
+}
+
+double ricker(double t, double f0, double t0) {
+  const double a = (M_PI * f0 * (t - t0)) * (M_PI * f0 * (t - t0));
+  return (1.0 - 2.0 * a) * std::exp(-a);
+}
+
+double factd(int n) {
+  double r = 1.0;
+  for (int i = 2; i <= n; ++i) r *= i;
+  return r;
+}
+
+// multi-indices of degree n in the library order
+std::vector<std::array<int, 4>> multi_indices(int n) {
+  std::vector<std::array<int, 4>> out;
+  for (int l = 0; l <= n; ++l)
+    for (int k = 0; k <= n - l; ++k)
+      for (int j = 0; j <= n - l - k; ++j) out.push_back({n - j - k - l, j, k, l});
+  return out;
+}
+
+// Solve (normalised Bernstein mass matrix) x = b by Cholesky, in place.
+bool mass_solve(int n, std::vector<double>& b) {
+  const auto A = multi_indices(n);
+  const int P = int(A.size());
+  std::vector<double> L(size_t(P) * P);
+  auto coef = [&](const std::array<int, 4>& a) {
+    return factd(n) / (factd(a[0]) * factd(a[1]) * factd(a[2]) * factd(a[3]));
+  };
+  for (int i = 0; i < P; ++i)
+    for (int j = 0; j < P; ++j) {
+      double m = 6.0 / factd(2 * n + 3);
+      for (int x = 0; x < 4; ++x) m *= factd(A[i][x] + A[j][x]);
+      L[size_t(i) * P + j] = coef(A[i]) * coef(A[j]) * m;
+    }
+  for (int j = 0; j < P; ++j) {
+    double d = L[size_t(j) * P + j];
+    for (int k = 0; k < j; ++k) d -= L[size_t(j) * P + k] * L[size_t(j) * P + k];
+    if (!(d > 0)) return false;
+    d = std::sqrt(d);
+    L[size_t(j) * P + j] = d;
+    for (int i = j + 1; i < P; ++i) {
+      double s = L[size_t(i) * P + j];
+      for (int k = 0; k < j; ++k) s -= L[size_t(i) * P + k] * L[size_t(j) * P + k];
+      L[size_t(i) * P + j] = s / d;
+    }
+  }
+  for (int i = 0; i < P; ++i) {
+    double s = b[i];
+    for (int k = 0; k < i; ++k) s -= L[size_t(i) * P + k] * b[k];
+    b[i] = s / L[size_t(i) * P + i];
+  }
+  for (int i = P - 1; i >= 0; --i) {
+    double s = b[i];
+    for (int k = i + 1; k < P; ++k) s -= L[size_t(k) * P + i] * b[k];
+    b[i] = s / L[size_t(i) * P + i];
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// small device helpers
+
+template <typename From, typename To>
+__global__ void convert_kernel(const From* __restrict__ src, To* __restrict__ dst, size_t n) {
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+    dst[i] = To(src[i]);
+}
+
+template <typename From, typename To>
+cudaError_t convert(const void* src, void* dst, size_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int threads = 256;
+  const int blocks = int(std::min<size_t>((n + threads - 1) / threads, 152 * 16));
+  convert_kernel<From, To><<<blocks, threads, 0, s>>>(static_cast<const From*>(src), static_cast<To*>(dst), n);
+  return cudaGetLastError();
+}
+
+cudaError_t copy_convert(const void* src, int src_prec, void* dst, int dst_prec, size_t n, cudaStream_t s) {
+  if (src_prec == dst_prec)
+    return cudaMemcpyAsync(dst, src, n * (src_prec == 64 ? 8 : 4), cudaMemcpyDeviceToDevice, s);
+  if (src_prec == 64) return convert<double, float>(src, dst, n, s);
+  return convert<float, double>(src, dst, n, s);
+}
+
+// per-process cache of device tables and launch grids for the stateless
+// operator entry point (keyed by device, N, M, precision)
+struct OpCache {
+  void* tables = nullptr;
+  int per_sm_stage = 0, per_sm_wadg = 0;
+};
+std::mutex g_cache_mu;
+std::map<std::tuple<int, int, int, int>, OpCache> g_cache;
+
+bbw_status get_tables(int N, int M, int prec, OpCache** out) {
+  int dev = 0;
+  BBW_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  auto key = std::make_tuple(dev, N, M, prec);
+  auto it = g_cache.find(key);
+  if (it != g_cache.end()) {
+    *out = &it->second;
+    return BBW_OK;
+  }
+  const bbw::KernelOps* ops = bbw::ops_for(N);
+  const bool dbl = prec == 64;
+  double cj[bbw::kMaxN + 1];
+  projection_coeffs(N, M, cj);
+  const size_t bytes = ops->table_bytes(M, dbl);
+  std::vector<unsigned char> host(bytes, 0);
+  ops->build_tables(M, dbl, cj, host.data());
+  OpCache c;
+  BBW_CUDA(ops->prepare(M, dbl, &c.per_sm_stage, &c.per_sm_wadg));
+  BBW_CUDA(cudaMalloc(&c.tables, bytes));
+  BBW_CUDA(cudaMemcpy(c.tables, host.data(), bytes, cudaMemcpyHostToDevice));
+  auto res = g_cache.emplace(key, c);
+  *out = &res.first->second;
+  return BBW_OK;
+}
+
+int num_sms() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// solver object
+
+struct bbw_solver {
+  int N = 0, M = 0, prec = 32;
+  int64_t K = 0;
+  int Np = 0, Nfp = 0, Mp = 0;
+  cudaStream_t stream = nullptr;
+  const bbw::KernelOps* ops = nullptr;
+  OpCache* op = nullptr;
+  int grid_stage = 1;
+  std::vector<double> vxyz;
+  std::vector<int64_t> etov;
+  std::vector<double> grad;  // [K][4][3]
+  std::vector<double> vol;   // [K]
+  std::vector<int32_t> etoe;
+  std::vector<int8_t> etof, fperm;
+  std::vector<double> c2;  // [K][Mp]
+  double cj[bbw::kMaxN + 1] = {};
+  void* q[2] = {nullptr, nullptr};
+  void* res = nullptr;
+  void* d_c2 = nullptr;
+  void* d_geom = nullptr;
+  int32_t* d_conn = nullptr;
+  void* d_src = nullptr;
+  unsigned int* d_status = nullptr;
+  void* pinned = nullptr;
+  size_t pinned_bytes = 0;
+  int cur = 0;
+  double t = 0.0;
+  int64_t stages = 0;
+  double tau_p = 1.0, tau_u = 1.0;
+  int64_t src_elem = -1;
+  double f0 = 0.0, t0 = 0.0;
+  size_t rsz() const { return prec == 64 ? 8 : 4; }
+  size_t nstate() const { return size_t(4) * size_t(K) * size_t(Np); }
+};
+
+namespace {
+
+void free_solver(bbw_solver* s) {
+  if (!s) return;
+  for (void* p : {s->q[0], s->q[1], s->res, s->d_c2, s->d_geom, static_cast<void*>(s->d_conn), s->d_src,
+                  static_cast<void*>(s->d_status)})
+    if (p) cudaFree(p);
+  if (s->pinned) cudaFreeHost(s->pinned);
+  delete s;
+}
+
+bbw_status ensure_pinned(bbw_solver* s, size_t bytes) {
+  if (s->pinned_bytes >= bytes) return BBW_OK;
+  if (s->pinned) cudaFreeHost(s->pinned);
+  s->pinned = nullptr;
+  s->pinned_bytes = 0;
+  BBW_CUDA(cudaMallocHost(&s->pinned, bytes));
+  s->pinned_bytes = bytes;
+  return BBW_OK;
+}
+
+// host doubles -> device buffer of the solver precision, through pinned memory
+bbw_status upload(bbw_solver* s, const double* src, void* dst, size_t n) {
+  bbw_status st = ensure_pinned(s, n * 8);
+  if (st != BBW_OK) return st;
+  if (s->prec == 64) {
+    std::memcpy(s->pinned, src, n * 8);
+  } else {
+    float* p = static_cast<float*>(s->pinned);
+    for (size_t i = 0; i < n; ++i) p[i] = float(src[i]);
+  }
+  BBW_CUDA(cudaMemcpyAsync(dst, s->pinned, n * s->rsz(), cudaMemcpyHostToDevice, s->stream));
+  BBW_CUDA(cudaStreamSynchronize(s->stream));
+  return BBW_OK;
+}
+
+bbw_status download(bbw_solver* s, const void* src, double* dst, size_t n) {
+  bbw_status st = ensure_pinned(s, n * 8);
+  if (st != BBW_OK) return st;
+  BBW_CUDA(cudaMemcpyAsync(s->pinned, src, n * s->rsz(), cudaMemcpyDeviceToHost, s->stream));
+  BBW_CUDA(cudaStreamSynchronize(s->stream));
+  if (s->prec == 64) {
+    std::memcpy(dst, s->pinned, n * 8);
+  } else {
+    const float* p = static_cast<const float*>(s->pinned);
+    for (size_t i = 0; i < n; ++i) dst[i] = double(p[i]);
+  }
+  return BBW_OK;
+}
+
+bbw_status check_status(bbw_solver* s) {
+  BBW_CUDA(cudaStreamSynchronize(s->stream));
+  BBW_CUDA(cudaGetLastError());
+  unsigned int st = 0;
+  BBW_CUDA(cudaMemcpy(&st, s->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+  if (st) {
+    BBW_CUDA(cudaMemset(s->d_status, 0, sizeof(unsigned int)));
+    return fail(BBW_ERR_NONFINITE, "the stage kernel produced a non-finite value");
+  }
+  return BBW_OK;
+}
+
+// connectivity by sorting face keys (sorted global vertex triples)
+bbw_status build_connectivity(bbw_solver* s) {
+  const int64_t K = s->K;
+  struct FaceRec {
+    int64_t a, b, c;
+    int64_t e;
+    int f;
+  };
+  std::vector<FaceRec> faces;
+  faces.reserve(size_t(K) * 4);
+  for (int64_t e = 0; e < K; ++e)
+    for (int f = 0; f < 4; ++f) {
+      int64_t v[3];
+      for (int x = 0; x < 3; ++x) v[x] = s->etov[size_t(e) * 4 + bbw::kFaceVerts[f][x]];
+      std::sort(v, v + 3);
+      faces.push_back({v[0], v[1], v[2], e, f});
+    }
+  std::sort(faces.begin(), faces.end(), [](const FaceRec& x, const FaceRec& y) {
+    return std::tie(x.a, x.b, x.c, x.e, x.f) < std::tie(y.a, y.b, y.c, y.e, y.f);
+  });
+  s->etoe.assign(size_t(K) * 4, -1);
+  s->etof.assign(size_t(K) * 4, -1);
+  s->fperm.assign(size_t(K) * 4, -1);
+  auto same = [](const FaceRec& x, const FaceRec& y) { return x.a == y.a && x.b == y.b && x.c == y.c; };
+  for (size_t i = 0; i < faces.size();) {
+    size_t j = i + 1;
+    while (j < faces.size() && same(faces[i], faces[j])) ++j;
+    if (j - i > 2) return fail(BBW_ERR_MESH, "a face is shared by more than two elements");
+    if (j - i == 2) {
+      const FaceRec& x = faces[i];
+      const FaceRec& y = faces[i + 1];
+      if (x.e == y.e) return fail(BBW_ERR_MESH, "an element repeats a face");
+      for (int side = 0; side < 2; ++side) {
+        const FaceRec& me = side ? y : x;
+        const FaceRec& nb = side ? x : y;
+        int64_t G[3], H[3];
+        for (int q = 0; q < 3; ++q) {
+          G[q] = s->etov[size_t(me.e) * 4 + bbw::kFaceVerts[me.f][q]];
+          H[q] = s->etov[size_t(nb.e) * 4 + bbw::kFaceVerts[nb.f][q]];
+        }
+        int code = -1;
+        for (int c = 0; c < 6 && code < 0; ++c)
+          if (G[0] == H[bbw::kPerm[c][0]] && G[1] == H[bbw::kPerm[c][1]] && G[2] == H[bbw::kPerm[c][2]]) code = c;
+        if (code < 0) return fail(BBW_ERR_MESH, "face vertex mismatch");
+        const size_t slot = size_t(me.e) * 4 + me.f;
+        s->etoe[slot] = int32_t(nb.e);
+        s->etof[slot] = int8_t(nb.f);
+        s->fperm[slot] = int8_t(code);
+      }
+    }
+    i = j;
+  }
+  return BBW_OK;
+}
+
+bbw_status build_geometry(bbw_solver* s) {
+  const int64_t K = s->K;
+  s->grad.assign(size_t(K) * 12, 0.0);
+  s->vol.assign(size_t(K), 0.0);
+  for (int64_t e = 0; e < K; ++e) {
+    double X[4][3];
+    for (int v = 0; v < 4; ++v)
+      for (int d = 0; d < 3; ++d) X[v][d] = s->vxyz[size_t(s->etov[size_t(e) * 4 + v]) * 3 + d];
+    // J columns: v1-v0, v2-v0, v3-v0; lambda_{1..3} = J^{-1}(x - v0)
+    double J[3][3];
+    for (int d = 0; d < 3; ++d)
+      for (int c = 0; c < 3; ++c) J[d][c] = X[c + 1][d] - X[0][d];
+    const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                       J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                       J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    double scale = 0.0;
+    for (int d = 0; d < 3; ++d)
+      for (int c = 0; c < 3; ++c) scale = std::max(scale, std::fabs(J[d][c]));
+    if (!(det > 1e-14 * scale * scale * scale) || !std::isfinite(det))
+      return fail(BBW_ERR_MESH, "element " + std::to_string(e) + " is inverted or degenerate");
+    double inv[3][3];
+    inv[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+    inv[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+    inv[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+    inv[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+    inv[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+    inv[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+    inv[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+    inv[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+    inv[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+    double* g = &s->grad[size_t(e) * 12];
+    for (int m = 1; m <= 3; ++m)
+      for (int d = 0; d < 3; ++d) g[3 * m + d] = inv[m - 1][d];
+    for (int d = 0; d < 3; ++d) g[d] = -(g[3 + d] + g[6 + d] + g[9 + d]);
+    s->vol[size_t(e)] = det / 6.0;
+  }
+  return BBW_OK;
+}
+
+// validate the mesh, then geometry and connectivity (host only)
+bbw_status setup_mesh(bbw_solver* s, int64_t nverts, const double* vxyz, int64_t K, const int64_t* etov, int N) {
+  for (int64_t i = 0; i < K * 4; ++i)
+    if (etov[i] < 0 || etov[i] >= nverts) return fail(BBW_ERR_MESH, "vertex id out of range");
+  for (int64_t i = 0; i < nverts * 3; ++i)
+    if (!std::isfinite(vxyz[i])) return fail(BBW_ERR_MESH, "non-finite vertex coordinate");
+  s->N = N;
+  s->K = K;
+  s->Np = bbw::np3(N);
+  s->Nfp = bbw::np2(N);
+  s->ops = bbw::ops_for(N);
+  s->vxyz.assign(vxyz, vxyz + nverts * 3);
+  s->etov.assign(etov, etov + K * 4);
+  for (int64_t e = 0; e < K; ++e) {
+    const int64_t* v = etov + e * 4;
+    for (int a = 0; a < 4; ++a)
+      for (int b = a + 1; b < 4; ++b)
+        if (v[a] == v[b]) return fail(BBW_ERR_MESH, "element " + std::to_string(e) + " repeats a vertex");
+  }
+  bbw_status st = build_geometry(s);
+  if (st == BBW_OK) st = build_connectivity(s);
+  return st;
+}
+
+template <typename real>
+bbw_status upload_geometry(bbw_solver* s) {
+  std::vector<real> geom(size_t(s->K) * 9);
+  for (int64_t e = 0; e < s->K; ++e)
+    for (int c = 0; c < 9; ++c) geom[size_t(e) * 9 + c] = real(s->grad[size_t(e) * 12 + 3 + c]);
+  BBW_CUDA(cudaMemcpy(s->d_geom, geom.data(), geom.size() * sizeof(real), cudaMemcpyHostToDevice));
+  return BBW_OK;
+}
+
+template <typename real>
+bbw_status launch_stage(bbw_solver* s, int stage, double dt) {
+  static const std::array<double, 5> c = rk_stage_times();
+  bbw::StageParams<real> P;
+  P.qin = static_cast<const real*>(s->q[s->cur]);
+  P.qout = static_cast<real*>(s->q[1 - s->cur]);
+  P.res = static_cast<real*>(s->res);
+  P.c2 = static_cast<const real*>(s->d_c2);
+  P.geom = static_cast<const real*>(s->d_geom);
+  P.conn = s->d_conn;
+  P.tables = s->op->tables;
+  P.K = s->K;
+  P.a = real(kRkA[stage]);
+  P.b = real(kRkB[stage]);
+  P.dt = real(dt);
+  P.tau_p = real(s->tau_p);
+  P.tau_u = real(s->tau_u);
+  P.src_elem = s->src_elem;
+  P.src_vec = static_cast<const real*>(s->d_src);
+  P.src_amp = real(s->src_elem >= 0 ? ricker(s->t + c[stage] * dt, s->f0, s->t0) : 0.0);
+  P.status = s->d_status;
+  BBW_CUDA(s->ops->launch_stage(s->M, s->prec == 64, &P, s->grid_stage, s->stream));
+  s->cur = 1 - s->cur;
+  s->stages += 1;
+  if (stage == 4) s->t += dt;
+  return BBW_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+
+extern "C" {
+
+int bbw_version(void) { return 100; }
+
+const char* bbw_last_error(void) { return g_err.c_str(); }
+
+bbw_status bbw_create(int64_t nverts, const double* vxyz, int64_t K, const int64_t* etov, int N, int M,
+                      int precision, void* cuda_stream, bbw_solver** out) {
+  if (!out) return fail(BBW_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!vxyz || !etov || nverts <= 0 || K <= 0) return fail(BBW_ERR_ARG, "empty mesh or NULL array");
+  if (K >= bbw::kMaxElements) return fail(BBW_ERR_ARG, "too many elements (limit 2^26)");
+  if (N < 1 || N > bbw::kMaxN) return fail(BBW_ERR_UNSUPPORTED, "N must be in 1..9");
+  if (M < 0 || M > bbw::kMaxM) return fail(BBW_ERR_UNSUPPORTED, "M must be in 0..3");
+  if (precision != 32 && precision != 64) return fail(BBW_ERR_ARG, "precision must be 32 or 64");
+  auto* s = new bbw_solver();
+  s->M = M;
+  s->prec = precision;
+  s->Mp = bbw::np3(M);
+  s->stream = static_cast<cudaStream_t>(cuda_stream);
+  bbw_status st = setup_mesh(s, nverts, vxyz, K, etov, N);
+  if (st != BBW_OK) {
+    free_solver(s);
+    return st;
+  }
+  projection_coeffs(N, M, s->cj);
+  st = get_tables(N, M, precision, &s->op);
+  if (st != BBW_OK) {
+    free_solver(s);
+    return st;
+  }
+  const int64_t tiles = (K + s->ops->elems_per_cta - 1) / s->ops->elems_per_cta;
+  s->grid_stage = int(std::min<int64_t>(tiles, int64_t(std::max(1, s->op->per_sm_stage)) * num_sms()));
+
+  const size_t rs = s->rsz();
+  auto alloc = [&](void** p, size_t bytes) -> bool {
+    if (cudaMalloc(p, bytes) != cudaSuccess) return false;
+    return cudaMemset(*p, 0, bytes) == cudaSuccess;
+  };
+  bool ok = alloc(&s->q[0], s->nstate() * rs) && alloc(&s->q[1], s->nstate() * rs) &&
+            alloc(&s->res, s->nstate() * rs) && alloc(&s->d_c2, size_t(K) * s->Mp * rs) &&
+            alloc(&s->d_geom, size_t(K) * 9 * rs) && alloc(reinterpret_cast<void**>(&s->d_conn), size_t(K) * 16) &&
+            alloc(&s->d_src, size_t(s->Np) * rs) && alloc(reinterpret_cast<void**>(&s->d_status), 16);
+  if (!ok) {
+    std::string msg = std::string("device allocation failed: ") + cudaGetErrorString(cudaGetLastError());
+    free_solver(s);
+    return fail(BBW_ERR_CUDA, msg);
+  }
+  st = precision == 64 ? upload_geometry<double>(s) : upload_geometry<float>(s);
+  if (st == BBW_OK) {
+    std::vector<int32_t> conn(size_t(K) * 4);
+    for (size_t i = 0; i < conn.size(); ++i)
+      conn[i] = s->etoe[i] < 0 ? -1 : (s->etoe[i] << 5) | (int32_t(s->etof[i]) << 3) | int32_t(s->fperm[i]);
+    if (cudaMemcpy(s->d_conn, conn.data(), conn.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+      st = fail(BBW_ERR_CUDA, "connectivity upload failed");
+  }
+  if (st == BBW_OK) {
+    std::vector<double> ones(size_t(K) * s->Mp, 1.0);
+    st = bbw_set_c2(s, ones.data());
+  }
+  if (st != BBW_OK) {
+    free_solver(s);
+    return st;
+  }
+  *out = s;
+  return BBW_OK;
+}
+
+void bbw_destroy(bbw_solver* s) {
+  if (s && s->stream) cudaStreamSynchronize(s->stream);
+  else if (s) cudaDeviceSynchronize();
+  free_solver(s);
+}
+
+bbw_status bbw_info(const bbw_solver* s, int64_t* K, int* N, int* M, int* Np, int* Mp, int* precision) {
+  if (!s) return fail(BBW_ERR_ARG, "solver is NULL");
+  if (K) *K = s->K;
+  if (N) *N = s->N;
+  if (M) *M = s->M;
+  if (Np) *Np = s->Np;
+  if (Mp) *Mp = s->Mp;
+  if (precision) *precision = s->prec;
+  return BBW_OK;
+}
+
+bbw_status bbw_get_connectivity(const bbw_solver* s, int32_t* etoe, int8_t* etof, int8_t* fperm) {
+  if (!s) return fail(BBW_ERR_ARG, "solver is NULL");
+  const size_t n = size_t(s->K) * 4;
+  if (etoe) std::memcpy(etoe, s->etoe.data(), n * 4);
+  if (etof) std::memcpy(etof, s->etof.data(), n);
+  if (fperm) std::memcpy(fperm, s->fperm.data(), n);
+  return BBW_OK;
+}
+
+bbw_status bbw_get_face_node_map(const bbw_solver* s, int64_t* nmap) {
+  if (!s || !nmap) return fail(BBW_ERR_ARG, "NULL argument");
+  const int Nfp = s->Nfp;
+  std::vector<int> fidx(4 * Nfp), nidx(24 * Nfp);
+  s->ops->face_maps(fidx.data(), nidx.data());
+  for (int64_t e = 0; e < s->K; ++e)
+    for (int f = 0; f < 4; ++f) {
+      const size_t slot = size_t(e) * 4 + f;
+      for (int a = 0; a < Nfp; ++a) {
+        int64_t v = -1;
+        if (s->etoe[slot] >= 0)
+          v = int64_t(s->etoe[slot]) * s->Np + nidx[(s->etof[slot] * 6 + s->fperm[slot]) * Nfp + a];
+        nmap[slot * Nfp + a] = v;
+      }
+    }
+  return BBW_OK;
+}
+
+bbw_status bbw_get_geometry(const bbw_solver* s, double* grad, double* vol) {
+  if (!s) return fail(BBW_ERR_ARG, "solver is NULL");
+  if (grad) std::memcpy(grad, s->grad.data(), s->grad.size() * 8);
+  if (vol) std::memcpy(vol, s->vol.data(), s->vol.size() * 8);
+  return BBW_OK;
+}
+
+bbw_status bbw_mesh_analyze(int64_t nverts, const double* vxyz, int64_t K, const int64_t* etov, int N,
+                            int32_t* etoe, int8_t* etof, int8_t* fperm, int64_t* nmap, double* grad,
+                            double* vol) {
+  if (!vxyz || !etov || nverts <= 0 || K <= 0) return fail(BBW_ERR_ARG, "empty mesh or NULL array");
+  if (K >= bbw::kMaxElements) return fail(BBW_ERR_ARG, "too many elements (limit 2^26)");
+  if (N < 1 || N > bbw::kMaxN) return fail(BBW_ERR_UNSUPPORTED, "N must be in 1..9");
+  bbw_solver s;
+  bbw_status st = setup_mesh(&s, nverts, vxyz, K, etov, N);
+  if (st != BBW_OK) return st;
+  st = bbw_get_connectivity(&s, etoe, etof, fperm);
+  if (st == BBW_OK && nmap) st = bbw_get_face_node_map(&s, nmap);
+  if (st == BBW_OK) st = bbw_get_geometry(&s, grad, vol);
+  return st;
+}
+
+bbw_status bbw_set_c2(bbw_solver* s, const double* c2) {
+  if (!s || !c2) return fail(BBW_ERR_ARG, "NULL argument");
+  const size_t n = size_t(s->K) * s->Mp;
+  for (size_t i = 0; i < n; ++i)
+    if (!(c2[i] > 0.0) || !std::isfinite(c2[i]))
+      return fail(BBW_ERR_NONPOS_C2, "c^2 coefficient " + std::to_string(i) + " is not positive and finite");
+  bbw_status st = upload(s, c2, s->d_c2, n);
+  if (st != BBW_OK) return st;
+  s->c2.assign(c2, c2 + n);
+  return BBW_OK;
+}
+
+bbw_status bbw_set_params(bbw_solver* s, double tau_p, double tau_u) {
+  if (!s) return fail(BBW_ERR_ARG, "solver is NULL");
+  if (!(tau_p >= 0.0) || !(tau_u >= 0.0) || !std::isfinite(tau_p) || !std::isfinite(tau_u))
+    return fail(BBW_ERR_ARG, "penalty parameters must be finite and >= 0");
+  s->tau_p = tau_p;
+  s->tau_u = tau_u;
+  return BBW_OK;
+}
+
+bbw_status bbw_set_state(bbw_solver* s, const double* q, const double* res, double t) {
+  if (!s || !q) return fail(BBW_ERR_ARG, "NULL argument");
+  bbw_status st = upload(s, q, s->q[s->cur], s->nstate());
+  if (st != BBW_OK) return st;
+  if (res) {
+    st = upload(s, res, s->res, s->nstate());
+    if (st != BBW_OK) return st;
+  } else {
+    BBW_CUDA(cudaMemsetAsync(s->res, 0, s->nstate() * s->rsz(), s->stream));
+  }
+  s->t = t;
+  s->stages = 0;
+  return BBW_OK;
+}
+
+bbw_status bbw_set_state_device(bbw_solver* s, const void* q, const void* res, int dtype, double t) {
+  if (!s || !q) return fail(BBW_ERR_ARG, "NULL argument");
+  if (dtype != 32 && dtype != 64) return fail(BBW_ERR_ARG, "dtype must be 32 or 64");
+  BBW_CUDA(copy_convert(q, dtype, s->q[s->cur], s->prec, s->nstate(), s->stream));
+  if (res)
+    BBW_CUDA(copy_convert(res, dtype, s->res, s->prec, s->nstate(), s->stream));
+  else
+    BBW_CUDA(cudaMemsetAsync(s->res, 0, s->nstate() * s->rsz(), s->stream));
+  s->t = t;
+  s->stages = 0;
+  return BBW_OK;
+}
+
+bbw_status bbw_get_state(bbw_solver* s, double* q, double* res, double* t) {
+  if (!s) return fail(BBW_ERR_ARG, "solver is NULL");
+  bbw_status st = check_status(s);
+  if (st != BBW_OK) return st;
+  if (q) {
+    st = download(s, s->q[s->cur], q, s->nstate());
+    if (st != BBW_OK) return st;
+  }
+  if (res) {
+    st = download(s, s->res, res, s->nstate());
+    if (st != BBW_OK) return st;
+  }
+  if (t) *t = s->t;
+  return BBW_OK;
+}
+
+bbw_status bbw_get_state_device(bbw_solver* s, void* q, void* res, int dtype) {
+  if (!s) return fail(BBW_ERR_ARG, "solver is NULL");
+  if (dtype != 32 && dtype != 64) return fail(BBW_ERR_ARG, "dtype must be 32 or 64");
+  if (q) BBW_CUDA(copy_convert(s->q[s->cur], s->prec, q, dtype, s->nstate(), s->stream));
+  if (res) BBW_CUDA(copy_convert(s->res, s->prec, res, dtype, s->nstate(), s->stream));
+  return BBW_OK;
+}
+
+bbw_status bbw_set_source(bbw_solver* s, int64_t elem, const double* coeffs, double f0, double t0) {
+  if (!s || !coeffs) return fail(BBW_ERR_ARG, "NULL argument");
+  if (elem < 0 || elem >= s->K) return fail(BBW_ERR_ARG, "source element out of range");
+  if (!std::isfinite(f0) || !std::isfinite(t0)) return fail(BBW_ERR_ARG, "non-finite wavelet parameter");
+  bbw_status st = upload(s, coeffs, s->d_src, size_t(s->Np));
+  if (st != BBW_OK) return st;
+  s->src_elem = elem;
+  s->f0 = f0;
+  s->t0 = t0;
+  return BBW_OK;
+}
+
+bbw_status bbw_set_point_source(bbw_solver* s, const double* xs, double f0, double t0, int64_t* elem) {
+  if (!s || !xs) return fail(BBW_ERR_ARG, "NULL argument");
+  int64_t found = -1;
+  double lam[4] = {0, 0, 0, 0};
+  for (int64_t e = 0; e < s->K && found < 0; ++e) {
+    const double* g = &s->grad[size_t(e) * 12];
+    const double* v0 = &s->vxyz[size_t(s->etov[size_t(e) * 4]) * 3];
+    double l[4];
+    bool inside = true;
+    for (int m = 0; m < 4; ++m) {
+      l[m] = (m == 0 ? 1.0 : 0.0);
+      for (int d = 0; d < 3; ++d) l[m] += g[3 * m + d] * (xs[d] - v0[d]);
+      inside = inside && l[m] >= -1e-12;
+    }
+    if (inside) {
+      found = e;
+      std::memcpy(lam, l, sizeof(lam));
+    }
+  }
+  if (found < 0) return fail(BBW_ERR_ARG, "source point lies outside the mesh");
+  const auto A = multi_indices(s->N);
+  std::vector<double> b(A.size());
+  for (size_t i = 0; i < A.size(); ++i) {
+    double v = factd(s->N) / (factd(A[i][0]) * factd(A[i][1]) * factd(A[i][2]) * factd(A[i][3]));
+    for (int x = 0; x < 4; ++x) v *= std::pow(std::max(lam[x], 0.0), A[i][x]);
+    b[i] = v;
+  }
+  if (!mass_solve(s->N, b)) return fail(BBW_ERR_ARG, "mass matrix factorisation failed");
+  for (double& v : b) v /= s->vol[size_t(found)];
+  if (elem) *elem = found;
+  return bbw_set_source(s, found, b.data(), f0, t0);
+}
+
+bbw_status bbw_clear_source(bbw_solver* s) {
+  if (!s) return fail(BBW_ERR_ARG, "solver is NULL");
+  s->src_elem = -1;
+  return BBW_OK;
+}
+
+bbw_status bbw_stage(bbw_solver* s, int stage, double dt) {
+  if (!s) return fail(BBW_ERR_ARG, "solver is NULL");
+  if (stage < 0 || stage > 4) return fail(BBW_ERR_ARG, "stage must be in 0..4");
+  if (!std::isfinite(dt)) return fail(BBW_ERR_ARG, "dt is not finite");
+  return s->prec == 64 ? launch_stage<double>(s, stage, dt) : launch_stage<float>(s, stage, dt);
+}
+
+bbw_status bbw_step(bbw_solver* s, double dt, int64_t nsteps) {
+  if (!s) return fail(BBW_ERR_ARG, "solver is NULL");
+  if (nsteps < 0) return fail(BBW_ERR_ARG, "nsteps < 0");
+  for (int64_t i = 0; i < nsteps; ++i)
+    for (int st = 0; st < 5; ++st) {
+      bbw_status r = bbw_stage(s, st, dt);
+      if (r != BBW_OK) return r;
+    }
+  return BBW_OK;
+}
+
+bbw_status bbw_cfl_dt(const bbw_solver* s, double cfl, double* dt) {
+  if (!s || !dt) return fail(BBW_ERR_ARG, "NULL argument");
+  if (!(cfl > 0.0)) return fail(BBW_ERR_ARG, "cfl must be > 0");
+  double cmax = 0.0, ratio = 0.0;
+  for (double v : s->c2) cmax = std::max(cmax, v);
+  for (int64_t e = 0; e < s->K; ++e)
+    for (int f = 0; f < 4; ++f) {
+      const double* g = &s->grad[size_t(e) * 12 + 3 * f];
+      ratio = std::max(ratio, 3.0 * std::sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]));
+    }
+  const double cn = (s->N + 1) * (s->N + 3) / 3.0;
+  *dt = cfl / (std::sqrt(cmax) * cn * ratio);
+  return BBW_OK;
+}
+
+bbw_status bbw_advance(bbw_solver* s, double T, double cfl, double* dt_used, int64_t* nsteps) {
+  if (!s) return fail(BBW_ERR_ARG, "solver is NULL");
+  if (!(T >= 0.0)) return fail(BBW_ERR_ARG, "T must be >= 0");
+  double dt = 0.0;
+  bbw_status st = bbw_cfl_dt(s, cfl, &dt);
+  if (st != BBW_OK) return st;
+  const int64_t n = int64_t(std::ceil(T / dt));
+  const double h = n > 0 ? T / double(n) : 0.0;
+  if (dt_used) *dt_used = h;
+  if (nsteps) *nsteps = n;
+  return bbw_step(s, h, n);
+}
+
+bbw_status bbw_sync(bbw_solver* s) {
+  if (!s) return fail(BBW_ERR_ARG, "solver is NULL");
+  return check_status(s);
+}
+
+bbw_status bbw_get_time(const bbw_solver* s, double* t, int64_t* stages) {
+  if (!s) return fail(BBW_ERR_ARG, "solver is NULL");
+  if (t) *t = s->t;
+  if (stages) *stages = s->stages;
+  return BBW_OK;
+}
+
+bbw_status bbw_projection_coeffs(int N, int M, double* c) {
+  if (!c) return fail(BBW_ERR_ARG, "c is NULL");
+  if (N < 0 || N > bbw::kMaxN || M < 0 || M > 8) return fail(BBW_ERR_ARG, "N or M out of range");
+  projection_coeffs(N, M, c);
+  return BBW_OK;
+}
+
+bbw_status bbw_lsrk_coeffs(double* a, double* b, double* c) {
+  const auto cs = rk_stage_times();
+  for (int i = 0; i < 5; ++i) {
+    if (a) a[i] = kRkA[i];
+    if (b) b[i] = kRkB[i];
+    if (c) c[i] = cs[i];
+  }
+  return BBW_OK;
+}
+
+bbw_status bbw_wadg_update(int N, int M, int precision, int64_t K, const void* rhs, const void* c2, void* out,
+                           void* stream) {
+  if (N < 1 || N > bbw::kMaxN || M < 0 || M > bbw::kMaxM) return fail(BBW_ERR_UNSUPPORTED, "N or M out of range");
+  if (precision != 32 && precision != 64) return fail(BBW_ERR_ARG, "precision must be 32 or 64");
+  if (K < 0) return fail(BBW_ERR_ARG, "K < 0");
+  if (K == 0) return BBW_OK;
+  if (!rhs || !c2 || !out) return fail(BBW_ERR_ARG, "NULL device pointer");
+  if (rhs == out) return fail(BBW_ERR_ARG, "out may not alias rhs");
+  OpCache* op = nullptr;
+  bbw_status st = get_tables(N, M, precision, &op);
+  if (st != BBW_OK) return st;
+  const bbw::KernelOps* ops = bbw::ops_for(N);
+  const int64_t tiles = (K + ops->elems_per_cta - 1) / ops->elems_per_cta;
+  const int grid = int(std::min<int64_t>(tiles, int64_t(std::max(1, op->per_sm_wadg)) * num_sms()));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (precision == 64) {
+    bbw::WadgParams<double> P{static_cast<const double*>(rhs), static_cast<const double*>(c2),
+                              static_cast<double*>(out), op->tables, K};
+    BBW_CUDA(ops->launch_wadg(M, true, &P, grid, s));
+  } else {
+    bbw::WadgParams<float> P{static_cast<const float*>(rhs), static_cast<const float*>(c2),
+                             static_cast<float*>(out), op->tables, K};
+    BBW_CUDA(ops->launch_wadg(M, false, &P, grid, s));
+  }
+  return BBW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,261 @@
+"""GPU parity of the fused BBWADG stage against the FP64 oracle (needs a GB300).
+
+Every test calls the CUDA path through the C ABI (binding.Solver /
+binding.wadg_update) and compares element by element with the oracle on the
+same seeded inputs: per stage relative L2 <= 1e-5 in FP32 (1e-11 in FP64),
+final time <= 1e-4 (1e-10). Meshes span several CTA tiles with a ragged tail.
+"""
+import numpy as np
+import pytest
+
+from oracle import bernstein as bb
+from oracle.acoustic import AcousticOracle
+from paper_1808_08645_gb300 import binding as B
+from paper_1808_08645_gb300 import inputs
+
+from parity_util import (TOL_FINAL, TOL_STAGE, oracle_stage_on_patch, random_case,
+                         rel_l2, rounded)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1808_08645_gb300 import build
+    build.build()
+    torch.cuda.init()
+
+
+def _solver(vxyz, etov, N, M, prec, c2, q, res, t=0.0):
+    s = B.Solver(vxyz, etov, N, M, prec)
+    s.set_c2(c2)
+    s.set_state(q, res, t)
+    return s
+
+
+# -- the weight-adjusted update alone -----------------------------------------
+
+@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("N", range(1, 10))
+@pytest.mark.parametrize("M", [0, 1, 2, 3])
+def test_wadg_update_parity(N, M, prec):
+    """out = P^{N+M}_N(c2 * r) equals the oracle's M^{-1} M_{c2} r."""
+    rng = np.random.default_rng(N * 7 + M)
+    K = 37  # several tiles at every N, ragged tail
+    Np, Mp = bb.np_count(N), bb.np_count(M)
+    r = rounded(rng.standard_normal((K, Np)), prec)
+    c2 = rounded(rng.uniform(0.5, 2.0, (K, Mp)), prec)
+    T = bb.weighted_mass_terms(N, M)
+    want = np.linalg.solve(bb.mass(N), np.einsum("kb,bij,kj->ki", c2, T, r).T).T
+    dt = torch.float32 if prec == 32 else torch.float64
+    dr = torch.tensor(r, dtype=dt, device="cuda")
+    dc = torch.tensor(c2, dtype=dt, device="cuda")
+    out = torch.full_like(dr, float("nan"))
+    B.wadg_update(N, M, prec, K, dr, dc, out)
+    torch.cuda.synchronize()
+    got = out.double().cpu().numpy()
+    assert rel_l2(got, want) <= TOL_STAGE[prec]
+
+
+def test_wadg_update_empty_is_noop():
+    B.wadg_update(3, 2, 32, 0, 0, 0, 0)
+
+
+# -- one stage ------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("N", range(1, 10))
+def test_stage_parity_all_degrees(N, prec):
+    M = 2
+    vxyz, etov, c2, q, res = random_case(3 if N <= 6 else 2, N, M, prec, seed=N)
+    dt, t = 1e-3, 0.37
+    orc = AcousticOracle(vxyz, etov, N, M, c2)
+    for s in (0, 3):
+        solver = _solver(vxyz, etov, N, M, prec, c2, q, res, t)
+        solver.stage(s, dt)
+        qg, rg, _ = solver.get_state(with_res=True)
+        qo, ro = orc.stage(q, res, s, dt, t)
+        assert rel_l2(rg, ro) <= TOL_STAGE[prec], (s, rel_l2(rg, ro))
+        assert rel_l2(qg, qo) <= TOL_STAGE[prec]
+        solver.close()
+
+
+@pytest.mark.parametrize("M", [0, 1, 3])
+def test_stage_parity_other_weight_degrees(M):
+    N, prec = 4, 32
+    vxyz, etov, c2, q, res = random_case(2, N, M, prec, seed=11)
+    orc = AcousticOracle(vxyz, etov, N, M, c2)
+    solver = _solver(vxyz, etov, N, M, prec, c2, q, res)
+    solver.stage(2, 2e-3)
+    qg, rg, _ = solver.get_state(with_res=True)
+    qo, ro = orc.stage(q, res, 2, 2e-3, 0.0)
+    assert rel_l2(rg, ro) <= TOL_STAGE[prec]
+
+
+@pytest.mark.parametrize("tau", [(0.0, 0.0), (0.5, 2.0)])
+def test_stage_parity_penalties(tau):
+    N, M, prec = 3, 2, 64
+    vxyz, etov, c2, q, res = random_case(2, N, M, prec, seed=5)
+    orc = AcousticOracle(vxyz, etov, N, M, c2, tau_p=tau[0], tau_u=tau[1])
+    solver = _solver(vxyz, etov, N, M, prec, c2, q, res)
+    solver.set_params(*tau)
+    solver.stage(1, 1e-3)
+    _, rg, _ = solver.get_state(with_res=True)
+    _, ro = orc.stage(q, res, 1, 1e-3, 0.0)
+    assert rel_l2(rg, ro) <= TOL_STAGE[prec]
+
+
+def test_stage_parity_single_element_and_unjittered_mesh():
+    for hexes, jitter, shuffle in ((0, 0.0, False), (2, 0.0, False)):
+        if hexes == 0:
+            vxyz = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1.0]])
+            etov = np.array([[0, 1, 2, 3]])
+            rng = np.random.default_rng(0)
+            c2 = rounded(rng.uniform(0.5, 2, (1, 10)), 32)
+            q = rounded(rng.standard_normal((4, 1, 20)), 32)
+            res = rounded(rng.standard_normal((4, 1, 20)), 32)
+        else:
+            vxyz, etov, c2, q, res = random_case(hexes, 3, 2, 32, seed=3, jitter=jitter, shuffle=shuffle)
+        orc = AcousticOracle(vxyz, etov, 3, 2, c2)
+        solver = _solver(vxyz, etov, 3, 2, 32, c2, q, res)
+        solver.stage(4, 1e-3)
+        _, rg, _ = solver.get_state(with_res=True)
+        _, ro = orc.stage(q, res, 4, 1e-3, 0.0)
+        assert rel_l2(rg, ro) <= TOL_STAGE[32]
+
+
+def test_stage_parity_point_source():
+    N, M, prec = 4, 2, 32
+    vxyz, etov, c2, q, res = random_case(2, N, M, prec, seed=8)
+    q *= 1e-3  # make the source dominate its element
+    xs = np.array([0.41, 0.52, 0.37])
+    orc = AcousticOracle(vxyz, etov, N, M, c2)
+    e_or, _ = orc.set_point_source(xs, f0=10.0, t0=0.1)
+    solver = _solver(vxyz, etov, N, M, prec, c2, q, res, t=0.08)
+    e_gpu = solver.set_point_source(xs, f0=10.0, t0=0.1)
+    assert e_gpu == e_or
+    for s in range(5):
+        solver.stage(s, 2e-3)
+    qg, rg, tg = solver.get_state(with_res=True)
+    qo, ro = q, res
+    for s in range(5):
+        qo, ro = orc.stage(qo, ro, s, 2e-3, 0.08)
+    assert abs(tg - 0.082) < 1e-15
+    assert rel_l2(rg[:, e_or], ro[:, e_or]) <= 1e-5
+    assert rel_l2(rg, ro) <= 1e-5
+
+
+# -- whole runs -------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_final_time_parity_small_config(prec):
+    """4^3 x 6 = 384 tets, N=3, M=1, c2 = 1 + 0.5 sin sin sin, p = 0 walls,
+    Gaussian pulse, CFL dt, T = 0.5."""
+    cfg = inputs.PARITY_CONFIG
+    N, M = cfg["N"], cfg["M"]
+    vxyz, etov = inputs.cube_mesh(cfg["hexes"])
+    c2 = rounded(inputs.sample_at_domain_points(vxyz, etov, M, inputs.c2_config_small), prec)
+    K, Np = len(etov), bb.np_count(N)
+    q0 = np.zeros((4, K, Np))
+    q0[0] = inputs.sample_at_domain_points(vxyz, etov, N, inputs.gaussian_pulse())
+    q0 = rounded(q0, prec)
+    orc = AcousticOracle(vxyz, etov, N, M, c2)
+    dt, nsteps = orc.dt_for(cfg["T"], cfg["cfl"])
+    solver = _solver(vxyz, etov, N, M, prec, c2, q0, None)
+    dtg, ng = solver.advance(cfg["T"], cfg["cfl"])
+    assert ng == nsteps and abs(dtg - dt) <= 1e-14 * dt
+    qg, tg = solver.get_state()
+    qo, _ = orc.run(q0, dt, nsteps)
+    assert abs(tg - cfg["T"]) < 1e-12
+    assert rel_l2(qg, qo) <= TOL_FINAL[prec]
+
+
+def test_checkpoint_resume_is_bit_identical():
+    N, M = 5, 2
+    vxyz, etov, c2, q, _ = random_case(2, N, M, 32, seed=21)
+    xs = np.array([0.5, 0.5, 0.5])
+    a = _solver(vxyz, etov, N, M, 32, c2, q, None)
+    a.set_point_source(xs)
+    a.step(1e-3, 5)
+    qa, ra, ta = a.get_state(with_res=True)
+    b = _solver(vxyz, etov, N, M, 32, c2, q, None)
+    b.set_point_source(xs)
+    b.step(1e-3, 2)
+    qb, rb, tb = b.get_state(with_res=True)
+    c = _solver(vxyz, etov, N, M, 32, c2, qb, rb, tb)
+    c.set_point_source(xs)
+    c.step(1e-3, 3)
+    qc, rc, tc = c.get_state(with_res=True)
+    assert np.array_equal(qa, qc) and np.array_equal(ra, rc) and ta == tc
+
+
+def test_device_state_roundtrip_and_dtype_conversion():
+    N, M = 3, 2
+    vxyz, etov, c2, q, res = random_case(2, N, M, 32, seed=4)
+    s = _solver(vxyz, etov, N, M, 32, c2, q, res)
+    dq = torch.tensor(q, dtype=torch.float64, device="cuda")
+    s.set_state_device(dq, None, dtype=64, t=0.0)
+    out = torch.empty_like(dq, dtype=torch.float32)
+    s.get_state_device(out, None, dtype=32)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy().astype(np.float64), q)
+    s.stage(0, 1e-3)
+    qg, rg, _ = s.get_state(with_res=True)
+    orc = AcousticOracle(vxyz, etov, N, M, c2)
+    _, ro = orc.stage(q, np.zeros_like(q), 0, 1e-3, 0.0)
+    assert rel_l2(rg, ro) <= TOL_STAGE[32]
+
+
+def test_nonfinite_state_is_reported_on_the_host():
+    N, M = 2, 1
+    vxyz, etov, c2, q, res = random_case(1, N, M, 32, seed=2)
+    q[0, 0, 0] = np.nan
+    s = _solver(vxyz, etov, N, M, 32, c2, q, res)
+    s.stage(0, 1e-3)
+    with pytest.raises(B.BBWError) as ei:
+        s.sync()
+    assert ei.value.status == -5
+    s.sync()  # the flag is cleared once reported
+
+
+def test_rejects_nonpositive_c2():
+    vxyz, etov, c2, q, res = random_case(1, 2, 1, 32, seed=2)
+    s = B.Solver(vxyz, etov, 2, 1, 32)
+    c2[3, 1] = 0.0
+    with pytest.raises(B.BBWError) as ei:
+        s.set_c2(c2)
+    assert ei.value.status == -3
+
+
+# -- full size, sampled -------------------------------------------------------------
+
+@pytest.mark.parametrize("N", [1, 5, 9])
+def test_full_size_sweep_mesh_sampled(N):
+    """196,608 tets (the throughput workload) in the bench's launch shape:
+    one stage on GPU, sampled elements checked against the oracle patch by patch."""
+    cfg = inputs.SWEEP_CONFIG
+    M, prec = cfg["M"], 32
+    vxyz, etov = inputs.cube_mesh(cfg["hexes"])
+    K, Np = len(etov), bb.np_count(N)
+    field = inputs.c2_smooth_random(seed=0)
+    c2 = rounded(inputs.sample_at_domain_points(vxyz, etov, M, field), prec)
+    rng = np.random.default_rng(N)
+    q = rounded(rng.standard_normal((4, K, Np)), prec)
+    res = rounded(rng.standard_normal((4, K, Np)), prec)
+    s = _solver(vxyz, etov, N, M, prec, c2, q, res, t=0.05)
+    src = s.set_point_source(np.array(cfg["source"]), f0=cfg["f0"])
+    s.stage(2, 1e-4)
+    qg, rg, _ = s.get_state(with_res=True)
+    etoe = B.mesh_analyze(vxyz, etov, N)["etoe"]
+    sample = sorted(set([0, K - 1, src] + list(rng.choice(K, 24, replace=False))))
+    got, want = [], []
+    for e in sample:
+        qo, ro = oracle_stage_on_patch(vxyz, etov, etoe, e, N, M, c2, q, res, 2, 1e-4, 0.05,
+                                       source=(np.array(cfg["source"]), cfg["f0"], 1.0 / cfg["f0"])
+                                       if e == src else None)
+        got.append(rg[:, e])
+        want.append(ro)
+    assert rel_l2(np.array(got), np.array(want)) <= TOL_STAGE[prec]
