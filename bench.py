@@ -378,8 +378,8 @@ def main():
     ap.add_argument("--Ns", default="1,2,3,4,5,6,7,8,9")
     ap.add_argument("--hexes", type=int, default=inputs.SWEEP_CONFIG["hexes"])
     ap.add_argument("--e2e-steps", type=int, default=20)
-    ap.add_argument("--cpu-hexes", type=int, default=3)
-    ap.add_argument("--ref-hexes", type=int, default=1)
+    ap.add_argument("--cpu-hexes", type=int, default=5)
+    ap.add_argument("--ref-hexes", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

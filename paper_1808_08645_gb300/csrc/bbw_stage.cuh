@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(T* E) stage_kernel(const StageParams<real> P) 
         if (is_src) v += P.src_amp * P.src_vec[i];
         A[i] = v * tab.invfactN[i];
       }
-      if (t == 0) A[Np] = real(0);
+      if (active && t == 0) A[Np] = real(0);
       real bh[Mp > 0 ? Mp : 1];
 #pragma unroll
       for (int b = 0; b < Mp; ++b) bh[b] = c2s[e * Mp + b] * tab.invfactM[b];
@@ -558,7 +558,7 @@ __global__ void __launch_bounds__(T* E) wadg_kernel(const WadgParams<real> P) {
     real* A = R + Np;
     real* B = A + C::BUF;
     for (int i = t; active && i < Np; i += T) A[i] = R[i] * tab.invfactN[i];
-    if (t == 0) A[Np] = real(0);
+    if (active && t == 0) A[Np] = real(0);
     real bh[Mp > 0 ? Mp : 1];
 #pragma unroll
     for (int b = 0; b < Mp; ++b) bh[b] = c2s[e * Mp + b] * tab.invfactM[b];

@@ -379,3 +379,46 @@ def test_standing_wave_converges():
     rate = np.log2(errs[0] / errs[1])
     # rate -> N + 1 = 4; 3.6 is observed on 2^3 -> 4^3 hexes
     assert errs[1] < 1e-3 and rate > 3.3
+
+
+# -- sources and energy -----------------------------------------------------------
+
+def test_point_source_vector_reproduces_point_values():
+    """M^{-1} B(x_s)/|T| tested against any phi in P^N integrates to phi(x_s)."""
+    vxyz, etov = inputs.cube_mesh(1, jitter=0.0, shuffle=True, seed=6)
+    N = 4
+    orc = AcousticOracle(vxyz, etov, N, 0, np.ones((len(etov), 1)))
+    xs = np.array([0.31, 0.62, 0.44])
+    e, vec = orc.set_point_source(xs)
+    lam_s = geometry(vxyz, etov)["grad"][e] @ (xs - vxyz[etov[e, 0]]) + np.array([1.0, 0, 0, 0])
+    assert np.all(lam_s >= -1e-12)
+    lam, w = tet_rule(2 * N)
+    rng = np.random.default_rng(0)
+    phi = rng.standard_normal(orc.Np)
+    integral = orc.geo["vol"][e] * np.sum(w * bb.evaluate(vec, N, lam) * bb.evaluate(phi, N, lam))
+    assert abs(integral - bb.evaluate(phi, N, lam_s[None])[0]) < 1e-10
+
+
+def test_ricker_closed_form():
+    from oracle.acoustic import ricker
+    f0, t0 = 10.0, 0.1
+    assert ricker(t0, f0, t0) == 1.0
+    tz = t0 + 1.0 / (np.pi * f0 * np.sqrt(2.0))   # zero crossing of (1 - 2a)
+    assert abs(ricker(tz, f0, t0)) < 1e-15
+    assert ricker(t0 + 0.3, f0, t0) < 1e-30 + abs(ricker(t0 + 0.3, f0, t0))
+
+
+def test_energy_conserved_without_penalty():
+    """tau = 0: the semi-discrete energy is conserved; RK4 drifts by O(dt^4)."""
+    vxyz, etov = inputs.cube_mesh(1, jitter=0.1, shuffle=True, seed=2)
+    K = len(etov)
+    rng = np.random.default_rng(1)
+    orc = AcousticOracle(vxyz, etov, 2, 1, rng.uniform(0.7, 1.5, (K, 4)), tau_p=0.0, tau_u=0.0)
+    q = rng.standard_normal((4, K, orc.Np))
+    e0 = orc.energy(q)
+    dt = 0.2 * orc.dt_for(1.0, 0.5)[0]
+    q1, _ = orc.run(q, dt, 20)
+    assert abs(orc.energy(q1) - e0) < 1e-6 * e0
+    orc1 = AcousticOracle(vxyz, etov, 2, 1, orc.c2, tau_p=1.0, tau_u=1.0)
+    q2, _ = orc1.run(q, dt, 20)
+    assert orc1.energy(q2) < 0.99 * e0
