@@ -225,6 +225,33 @@ bbw_status bbw_lsrk_coeffs(double* a, double* b, double* c);
 bbw_status bbw_wadg_update(int N, int M, int precision, int64_t K, const void* rhs,
                            const void* c2, void* out, void* stream);
 
+/*
+ * bbw_wadg_update without any device allocation. The paper has no counterpart:
+ * this is a convenience of this library.
+ *
+ * For callers that cannot call cudaMalloc -- code running while another stream
+ * is being captured into a CUDA graph, frameworks that own the whole device
+ * memory pool and forbid allocations outside it, latency-critical loops that
+ * must not block on the allocator. bbw_wadg_update caches its operator tables
+ * in device memory it allocates on first use; this variant instead copies the
+ * tables of each call into one fixed 32 KiB array in the library's static
+ * device memory (present on every GPU that loads the library until the process
+ * exits). It calls no cudaMalloc or cudaFree and no allocating library routine.
+ *   Arguments, layout and result: as bbw_wadg_update.
+ *   Limit: the tables must fit in 32 KiB; every supported (N, M, precision)
+ *   does except N = 9 with M = 3, which returns BBW_ERR_ARG with a message.
+ *   Set-up: the first call on a device (and the first call for each
+ *   (N, M, precision) on it) looks up the array's device address and sets the
+ *   kernel's shared-memory attribute; make that first call before any stream
+ *   capture begins.
+ *   Sharing: every call uses the same array and leaves its tables there (each
+ *   call overwrites the whole region it uses). Calls whose work overlaps on the
+ *   GPU (different streams, or different host threads without ordering) race
+ *   on the array; order them on one stream.
+ */
+bbw_status bbw_wadg_update_noalloc(int N, int M, int precision, int64_t K, const void* rhs,
+                                   const void* c2, void* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

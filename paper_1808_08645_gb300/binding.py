@@ -15,7 +15,7 @@ import os
 import numpy as np
 
 __all__ = ["BBWError", "lib", "lib_path", "Solver", "mesh_analyze", "projection_coeffs",
-           "lsrk_coeffs", "wadg_update", "EXPORTS", "F32", "F64"]
+           "lsrk_coeffs", "wadg_update", "wadg_update_noalloc", "EXPORTS", "F32", "F64"]
 
 F32, F64 = 32, 64
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -63,6 +63,7 @@ EXPORTS = {
     "bbw_projection_coeffs": (_int, [_int, _int, _dp]),
     "bbw_lsrk_coeffs": (_int, [_dp, _dp, _dp]),
     "bbw_wadg_update": (_int, [_int, _int, _int, _i64, _p, _p, _p, _p]),
+    "bbw_wadg_update_noalloc": (_int, [_int, _int, _int, _i64, _p, _p, _p, _p]),
 }
 
 
@@ -151,6 +152,12 @@ def wadg_update(N: int, M: int, precision: int, K: int, rhs, c2, out, stream=Non
     """bbw_wadg_update on device arrays (torch tensors or raw addresses)."""
     _check(lib().bbw_wadg_update(N, M, precision, K, _dev(rhs), _dev(c2), _dev(out), _dev(stream)),
            "bbw_wadg_update")
+
+
+def wadg_update_noalloc(N: int, M: int, precision: int, K: int, rhs, c2, out, stream=None):
+    """bbw_wadg_update_noalloc: as wadg_update, allocating no device memory."""
+    _check(lib().bbw_wadg_update_noalloc(N, M, precision, K, _dev(rhs), _dev(c2), _dev(out), _dev(stream)),
+           "bbw_wadg_update_noalloc")
 
 
 class Solver:

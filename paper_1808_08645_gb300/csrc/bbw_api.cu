@@ -211,6 +211,10 @@ int num_sms() {
 
 }  // namespace
 
+namespace bbw {
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace bbw
+
 // ---------------------------------------------------------------------------
 // solver object
 

@@ -37,6 +37,9 @@ const KernelOps& ops_n7();
 const KernelOps& ops_n8();
 const KernelOps& ops_n9();
 
+// Set the thread-local message returned by bbw_last_error() (defined in bbw_api.cu).
+void set_last_error(const char* msg);
+
 inline const KernelOps* ops_for(int N) {
   switch (N) {
     case 1: return &ops_n1();
