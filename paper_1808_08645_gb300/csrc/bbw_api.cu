@@ -11,6 +11,7 @@
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "bbw_common.h"
@@ -145,26 +146,72 @@ bool mass_solve(int n, std::vector<double>& b) {
 // ---------------------------------------------------------------------------
 // small device helpers
 
-template <typename From, typename To>
-__global__ void convert_kernel(const From* __restrict__ src, To* __restrict__ dst, size_t n) {
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
-    dst[i] = To(src[i]);
+// State layouts: the ABI's [4][K][Np] ("user") and the kernels' grouped
+// [G][4][Np][V] ("internal", V elements per group, G = ceil(K / V); entries of
+// the padding elements of the last group are zero).
+__host__ __device__ inline size_t internal_index(int64_t e, int i, int f, int Np, int V) {
+  return ((size_t(e / V) * 4 + f) * Np + i) * V + size_t(e % V);
 }
 
 template <typename From, typename To>
-cudaError_t convert(const void* src, void* dst, size_t n, cudaStream_t s) {
-  if (n == 0) return cudaSuccess;
-  const int threads = 256;
-  const int blocks = int(std::min<size_t>((n + threads - 1) / threads, 152 * 16));
-  convert_kernel<From, To><<<blocks, threads, 0, s>>>(static_cast<const From*>(src), static_cast<To*>(dst), n);
+__global__ void to_internal_kernel(const From* __restrict__ src, To* __restrict__ dst, int64_t K, int Np, int V,
+                                   size_t n_internal) {
+  for (size_t x = blockIdx.x * size_t(blockDim.x) + threadIdx.x; x < n_internal; x += size_t(gridDim.x) * blockDim.x) {
+    // x enumerates the internal layout: decode (g, f, i, v)
+    const int v = int(x % V);
+    const size_t r = x / V;
+    const int i = int(r % Np);
+    const size_t r2 = r / Np;
+    const int f = int(r2 % 4);
+    const int64_t e = int64_t(r2 / 4) * V + v;
+    dst[x] = e < K ? To(src[(size_t(f) * K + e) * Np + i]) : To(0);
+  }
+}
+
+template <typename From, typename To>
+__global__ void to_user_kernel(const From* __restrict__ src, To* __restrict__ dst, int64_t K, int Np, int V) {
+  const size_t n = size_t(4) * K * Np;
+  for (size_t x = blockIdx.x * size_t(blockDim.x) + threadIdx.x; x < n; x += size_t(gridDim.x) * blockDim.x) {
+    const int i = int(x % Np);
+    const size_t r = x / Np;
+    const int64_t e = int64_t(r % K);
+    const int f = int(r / K);
+    dst[x] = To(src[internal_index(e, i, f, Np, V)]);
+  }
+}
+
+template <typename From, typename To>
+cudaError_t state_to_internal(const void* src, void* dst, int64_t K, int Np, int V, cudaStream_t s) {
+  const size_t n = size_t((K + V - 1) / V) * V * Np * 4;
+  const int blocks = int(std::min<size_t>((n + 255) / 256, 152 * 16));
+  to_internal_kernel<From, To><<<blocks, 256, 0, s>>>(static_cast<const From*>(src), static_cast<To*>(dst), K, Np, V, n);
   return cudaGetLastError();
 }
 
-cudaError_t copy_convert(const void* src, int src_prec, void* dst, int dst_prec, size_t n, cudaStream_t s) {
-  if (src_prec == dst_prec)
-    return cudaMemcpyAsync(dst, src, n * (src_prec == 64 ? 8 : 4), cudaMemcpyDeviceToDevice, s);
-  if (src_prec == 64) return convert<double, float>(src, dst, n, s);
-  return convert<float, double>(src, dst, n, s);
+template <typename From, typename To>
+cudaError_t state_to_user(const void* src, void* dst, int64_t K, int Np, int V, cudaStream_t s) {
+  const size_t n = size_t(4) * K * Np;
+  const int blocks = int(std::min<size_t>((n + 255) / 256, 152 * 16));
+  to_user_kernel<From, To><<<blocks, 256, 0, s>>>(static_cast<const From*>(src), static_cast<To*>(dst), K, Np, V);
+  return cudaGetLastError();
+}
+
+cudaError_t copy_to_internal(const void* src, int src_prec, void* dst, int dst_prec, int64_t K, int Np, int V,
+                             cudaStream_t s) {
+  if (src_prec == 64)
+    return dst_prec == 64 ? state_to_internal<double, double>(src, dst, K, Np, V, s)
+                          : state_to_internal<double, float>(src, dst, K, Np, V, s);
+  return dst_prec == 64 ? state_to_internal<float, double>(src, dst, K, Np, V, s)
+                        : state_to_internal<float, float>(src, dst, K, Np, V, s);
+}
+
+cudaError_t copy_to_user(const void* src, int src_prec, void* dst, int dst_prec, int64_t K, int Np, int V,
+                         cudaStream_t s) {
+  if (src_prec == 64)
+    return dst_prec == 64 ? state_to_user<double, double>(src, dst, K, Np, V, s)
+                          : state_to_user<double, float>(src, dst, K, Np, V, s);
+  return dst_prec == 64 ? state_to_user<float, double>(src, dst, K, Np, V, s)
+                        : state_to_user<float, float>(src, dst, K, Np, V, s);
 }
 
 // per-process cache of device tables and launch grids for the stateless
@@ -249,8 +296,11 @@ struct bbw_solver {
   double tau_p = 1.0, tau_u = 1.0;
   int64_t src_elem = -1;
   double f0 = 0.0, t0 = 0.0;
+  int V = 1;        // elements per group of the kernel's layout
+  int64_t G = 0;   // number of groups, ceil(K / V)
   size_t rsz() const { return prec == 64 ? 8 : 4; }
-  size_t nstate() const { return size_t(4) * size_t(K) * size_t(Np); }
+  size_t nstate() const { return size_t(4) * size_t(K) * size_t(Np); }           // user layout
+  size_t nstate_internal() const { return size_t(4) * size_t(G) * V * Np; }      // grouped layout
 };
 
 namespace {
@@ -289,17 +339,71 @@ bbw_status upload(bbw_solver* s, const double* src, void* dst, size_t n) {
   return BBW_OK;
 }
 
-bbw_status download(bbw_solver* s, const void* src, double* dst, size_t n) {
+// host [4][K][Np] doubles -> device grouped state of the solver precision
+bbw_status upload_state(bbw_solver* s, const double* src, void* dst) {
+  const size_t n = s->nstate_internal();
+  bbw_status st = ensure_pinned(s, n * 8);
+  if (st != BBW_OK) return st;
+  const int64_t K = s->K;
+  const int Np = s->Np, V = s->V;
+  auto fill = [&](auto* p) {
+    using T = std::remove_pointer_t<decltype(p)>;
+    std::memset(p, 0, n * sizeof(T));
+    for (int f = 0; f < 4; ++f)
+      for (int64_t e = 0; e < K; ++e) {
+        const double* row = src + (size_t(f) * K + e) * Np;
+        for (int i = 0; i < Np; ++i) p[internal_index(e, i, f, Np, V)] = T(row[i]);
+      }
+  };
+  if (s->prec == 64)
+    fill(static_cast<double*>(s->pinned));
+  else
+    fill(static_cast<float*>(s->pinned));
+  BBW_CUDA(cudaMemcpyAsync(dst, s->pinned, n * s->rsz(), cudaMemcpyHostToDevice, s->stream));
+  BBW_CUDA(cudaStreamSynchronize(s->stream));
+  return BBW_OK;
+}
+
+bbw_status download_state(bbw_solver* s, const void* src, double* dst) {
+  const size_t n = s->nstate_internal();
   bbw_status st = ensure_pinned(s, n * 8);
   if (st != BBW_OK) return st;
   BBW_CUDA(cudaMemcpyAsync(s->pinned, src, n * s->rsz(), cudaMemcpyDeviceToHost, s->stream));
   BBW_CUDA(cudaStreamSynchronize(s->stream));
-  if (s->prec == 64) {
-    std::memcpy(dst, s->pinned, n * 8);
-  } else {
-    const float* p = static_cast<const float*>(s->pinned);
-    for (size_t i = 0; i < n; ++i) dst[i] = double(p[i]);
-  }
+  const int64_t K = s->K;
+  const int Np = s->Np, V = s->V;
+  auto take = [&](const auto* p) {
+    for (int f = 0; f < 4; ++f)
+      for (int64_t e = 0; e < K; ++e) {
+        double* row = dst + (size_t(f) * K + e) * Np;
+        for (int i = 0; i < Np; ++i) row[i] = double(p[internal_index(e, i, f, Np, V)]);
+      }
+  };
+  if (s->prec == 64)
+    take(static_cast<const double*>(s->pinned));
+  else
+    take(static_cast<const float*>(s->pinned));
+  return BBW_OK;
+}
+
+// host [K][W] doubles -> device [G][W][V] (padding elements get pad)
+bbw_status upload_grouped(bbw_solver* s, const double* src, int W, double pad, void* dst) {
+  const size_t n = size_t(s->G) * W * s->V;
+  bbw_status st = ensure_pinned(s, n * 8);
+  if (st != BBW_OK) return st;
+  const int V = s->V;
+  auto fill = [&](auto* p) {
+    using T = std::remove_pointer_t<decltype(p)>;
+    for (int64_t e = 0; e < s->G * V; ++e)
+      for (int w = 0; w < W; ++w)
+        p[(size_t(e / V) * W + w) * V + size_t(e % V)] = T(e < s->K ? src[size_t(e) * W + w] : pad);
+  };
+  if (s->prec == 64)
+    fill(static_cast<double*>(s->pinned));
+  else
+    fill(static_cast<float*>(s->pinned));
+  BBW_CUDA(cudaMemcpyAsync(dst, s->pinned, n * s->rsz(), cudaMemcpyHostToDevice, s->stream));
+  BBW_CUDA(cudaStreamSynchronize(s->stream));
   return BBW_OK;
 }
 
@@ -435,9 +539,14 @@ bbw_status setup_mesh(bbw_solver* s, int64_t nverts, const double* vxyz, int64_t
 
 template <typename real>
 bbw_status upload_geometry(bbw_solver* s) {
-  std::vector<real> geom(size_t(s->K) * 9);
-  for (int64_t e = 0; e < s->K; ++e)
-    for (int c = 0; c < 9; ++c) geom[size_t(e) * 9 + c] = real(s->grad[size_t(e) * 12 + 3 + c]);
+  // [G][9][V]; padding elements of the last group get the unit tetrahedron
+  // (grad lambda_m = e_m), whose results are never read back
+  const int V = s->V;
+  std::vector<real> geom(size_t(s->G) * 9 * V);
+  for (int64_t e = 0; e < s->G * V; ++e)
+    for (int c = 0; c < 9; ++c)
+      geom[(size_t(e / V) * 9 + c) * V + size_t(e % V)] =
+          real(e < s->K ? s->grad[size_t(e) * 12 + 3 + c] : (c % 4 == 0 ? 1.0 : 0.0));
   BBW_CUDA(cudaMemcpy(s->d_geom, geom.data(), geom.size() * sizeof(real), cudaMemcpyHostToDevice));
   return BBW_OK;
 }
@@ -453,7 +562,7 @@ bbw_status launch_stage(bbw_solver* s, int stage, double dt) {
   P.geom = static_cast<const real*>(s->d_geom);
   P.conn = s->d_conn;
   P.tables = s->op->tables;
-  P.K = s->K;
+  P.G = s->G;
   P.a = real(kRkA[stage]);
   P.b = real(kRkB[stage]);
   P.dt = real(dt);
@@ -506,7 +615,10 @@ bbw_status bbw_create(int64_t nverts, const double* vxyz, int64_t K, const int64
     free_solver(s);
     return st;
   }
-  const int64_t tiles = (K + s->ops->elems_per_cta - 1) / s->ops->elems_per_cta;
+  const int pi = precision == 64 ? 1 : 0;
+  s->V = s->ops->group_width[pi];
+  s->G = (K + s->V - 1) / s->V;
+  const int64_t tiles = (s->G + s->ops->groups_per_cta[pi] - 1) / s->ops->groups_per_cta[pi];
   s->grid_stage = int(std::min<int64_t>(tiles, int64_t(std::max(1, s->op->per_sm_stage)) * num_sms()));
 
   const size_t rs = s->rsz();
@@ -514,9 +626,10 @@ bbw_status bbw_create(int64_t nverts, const double* vxyz, int64_t K, const int64
     if (cudaMalloc(p, bytes) != cudaSuccess) return false;
     return cudaMemset(*p, 0, bytes) == cudaSuccess;
   };
-  bool ok = alloc(&s->q[0], s->nstate() * rs) && alloc(&s->q[1], s->nstate() * rs) &&
-            alloc(&s->res, s->nstate() * rs) && alloc(&s->d_c2, size_t(K) * s->Mp * rs) &&
-            alloc(&s->d_geom, size_t(K) * 9 * rs) && alloc(reinterpret_cast<void**>(&s->d_conn), size_t(K) * 16) &&
+  const size_t ng = size_t(s->G) * s->V;  // elements including group padding
+  bool ok = alloc(&s->q[0], s->nstate_internal() * rs) && alloc(&s->q[1], s->nstate_internal() * rs) &&
+            alloc(&s->res, s->nstate_internal() * rs) && alloc(&s->d_c2, ng * s->Mp * rs) &&
+            alloc(&s->d_geom, ng * 9 * rs) && alloc(reinterpret_cast<void**>(&s->d_conn), ng * 16) &&
             alloc(&s->d_src, size_t(s->Np) * rs) && alloc(reinterpret_cast<void**>(&s->d_status), 16);
   if (!ok) {
     std::string msg = std::string("device allocation failed: ") + cudaGetErrorString(cudaGetLastError());
@@ -525,9 +638,15 @@ bbw_status bbw_create(int64_t nverts, const double* vxyz, int64_t K, const int64
   }
   st = precision == 64 ? upload_geometry<double>(s) : upload_geometry<float>(s);
   if (st == BBW_OK) {
-    std::vector<int32_t> conn(size_t(K) * 4);
-    for (size_t i = 0; i < conn.size(); ++i)
-      conn[i] = s->etoe[i] < 0 ? -1 : (s->etoe[i] << 5) | (int32_t(s->etof[i]) << 3) | int32_t(s->fperm[i]);
+    // [G][4][V]; padding elements have walls on all faces
+    const int V = s->V;
+    std::vector<int32_t> conn(ng * 4, -1);
+    for (int64_t e = 0; e < K; ++e)
+      for (int f = 0; f < 4; ++f) {
+        const size_t i = size_t(e) * 4 + f;
+        conn[(size_t(e / V) * 4 + f) * V + size_t(e % V)] =
+            s->etoe[i] < 0 ? -1 : (s->etoe[i] << 5) | (int32_t(s->etof[i]) << 3) | int32_t(s->fperm[i]);
+      }
     if (cudaMemcpy(s->d_conn, conn.data(), conn.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
       st = fail(BBW_ERR_CUDA, "connectivity upload failed");
   }
@@ -615,7 +734,7 @@ bbw_status bbw_set_c2(bbw_solver* s, const double* c2) {
   for (size_t i = 0; i < n; ++i)
     if (!(c2[i] > 0.0) || !std::isfinite(c2[i]))
       return fail(BBW_ERR_NONPOS_C2, "c^2 coefficient " + std::to_string(i) + " is not positive and finite");
-  bbw_status st = upload(s, c2, s->d_c2, n);
+  bbw_status st = upload_grouped(s, c2, s->Mp, 1.0, s->d_c2);
   if (st != BBW_OK) return st;
   s->c2.assign(c2, c2 + n);
   return BBW_OK;
@@ -632,13 +751,13 @@ bbw_status bbw_set_params(bbw_solver* s, double tau_p, double tau_u) {
 
 bbw_status bbw_set_state(bbw_solver* s, const double* q, const double* res, double t) {
   if (!s || !q) return fail(BBW_ERR_ARG, "NULL argument");
-  bbw_status st = upload(s, q, s->q[s->cur], s->nstate());
+  bbw_status st = upload_state(s, q, s->q[s->cur]);
   if (st != BBW_OK) return st;
   if (res) {
-    st = upload(s, res, s->res, s->nstate());
+    st = upload_state(s, res, s->res);
     if (st != BBW_OK) return st;
   } else {
-    BBW_CUDA(cudaMemsetAsync(s->res, 0, s->nstate() * s->rsz(), s->stream));
+    BBW_CUDA(cudaMemsetAsync(s->res, 0, s->nstate_internal() * s->rsz(), s->stream));
   }
   s->t = t;
   s->stages = 0;
@@ -648,11 +767,11 @@ bbw_status bbw_set_state(bbw_solver* s, const double* q, const double* res, doub
 bbw_status bbw_set_state_device(bbw_solver* s, const void* q, const void* res, int dtype, double t) {
   if (!s || !q) return fail(BBW_ERR_ARG, "NULL argument");
   if (dtype != 32 && dtype != 64) return fail(BBW_ERR_ARG, "dtype must be 32 or 64");
-  BBW_CUDA(copy_convert(q, dtype, s->q[s->cur], s->prec, s->nstate(), s->stream));
+  BBW_CUDA(copy_to_internal(q, dtype, s->q[s->cur], s->prec, s->K, s->Np, s->V, s->stream));
   if (res)
-    BBW_CUDA(copy_convert(res, dtype, s->res, s->prec, s->nstate(), s->stream));
+    BBW_CUDA(copy_to_internal(res, dtype, s->res, s->prec, s->K, s->Np, s->V, s->stream));
   else
-    BBW_CUDA(cudaMemsetAsync(s->res, 0, s->nstate() * s->rsz(), s->stream));
+    BBW_CUDA(cudaMemsetAsync(s->res, 0, s->nstate_internal() * s->rsz(), s->stream));
   s->t = t;
   s->stages = 0;
   return BBW_OK;
@@ -663,11 +782,11 @@ bbw_status bbw_get_state(bbw_solver* s, double* q, double* res, double* t) {
   bbw_status st = check_status(s);
   if (st != BBW_OK) return st;
   if (q) {
-    st = download(s, s->q[s->cur], q, s->nstate());
+    st = download_state(s, s->q[s->cur], q);
     if (st != BBW_OK) return st;
   }
   if (res) {
-    st = download(s, s->res, res, s->nstate());
+    st = download_state(s, s->res, res);
     if (st != BBW_OK) return st;
   }
   if (t) *t = s->t;
@@ -677,8 +796,8 @@ bbw_status bbw_get_state(bbw_solver* s, double* q, double* res, double* t) {
 bbw_status bbw_get_state_device(bbw_solver* s, void* q, void* res, int dtype) {
   if (!s) return fail(BBW_ERR_ARG, "solver is NULL");
   if (dtype != 32 && dtype != 64) return fail(BBW_ERR_ARG, "dtype must be 32 or 64");
-  if (q) BBW_CUDA(copy_convert(s->q[s->cur], s->prec, q, dtype, s->nstate(), s->stream));
-  if (res) BBW_CUDA(copy_convert(s->res, s->prec, res, dtype, s->nstate(), s->stream));
+  if (q) BBW_CUDA(copy_to_user(s->q[s->cur], s->prec, q, dtype, s->K, s->Np, s->V, s->stream));
+  if (res) BBW_CUDA(copy_to_user(s->res, s->prec, res, dtype, s->K, s->Np, s->V, s->stream));
   return BBW_OK;
 }
 
@@ -820,7 +939,9 @@ bbw_status bbw_wadg_update(int N, int M, int precision, int64_t K, const void* r
   bbw_status st = get_tables(N, M, precision, &op);
   if (st != BBW_OK) return st;
   const bbw::KernelOps* ops = bbw::ops_for(N);
-  const int64_t tiles = (K + ops->elems_per_cta - 1) / ops->elems_per_cta;
+  const int pi = precision == 64 ? 1 : 0;
+  const int64_t per_cta = int64_t(ops->group_width[pi]) * ops->groups_per_cta[pi];
+  const int64_t tiles = (K + per_cta - 1) / per_cta;
   const int grid = int(std::min<int64_t>(tiles, int64_t(std::max(1, op->per_sm_wadg)) * num_sms()));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (precision == 64) {

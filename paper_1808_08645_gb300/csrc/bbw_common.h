@@ -34,10 +34,6 @@ BBW_HD constexpr int idx3(int n, int j, int k, int l) {
 }
 BBW_HD constexpr int idx2(int n, int b1, int b2) { return b2 * (n + 1) - b2 * (b2 - 1) / 2 + b1; }
 
-BBW_HD constexpr uint32_t pack4(int a0, int a1, int a2, int a3) {
-  return uint32_t(a0) | (uint32_t(a1) << 8) | (uint32_t(a2) << 16) | (uint32_t(a3) << 24);
-}
-
 // local vertices of face f (the three vertices other than f, increasing)
 constexpr int kFaceVerts[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
 // face orientation codes: own face vertex x <-> neighbour face vertex kPerm[c][x]
@@ -46,6 +42,28 @@ constexpr int kPerm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 
 // Packed connectivity word per (element, face): (nb << 5) | (nface << 3) | perm,
 // or -1 on a wall. Limits the mesh to 2^26 elements.
 constexpr int64_t kMaxElements = int64_t(1) << 26;
+
+// Packed stencil words. A one-degree reduction (E^n_{n-1})^T produces output
+// beta (degree n-1) from inputs beta + e_m (degree n) at
+//   base, base + 1, base + dk, base + dl,   base = idx3(n, j, k, l),
+//   dk = n - l - k + 1,  dl = (n-l+1)(n-l+2)/2 - k,
+// with weights (beta_0+1, j+1, k+1, l+1) / n where beta_0 + 1 = n + 3 - the
+// other three. A one-degree elevation E^n_{n-1} produces output gamma (degree
+// n) from gamma - e_m (degree n-1) at base, base - 1, base - dk, base - dl,
+// base = idx3(n-1, j, k, l) (a virtual index when gamma_0 = 0, whose term has
+// weight 0), the same dk, dl, and weights (gamma_0, j, k, l) / n.
+// Word: base (9 bits) | dk (4) | dl (7) | w1 (4) | w2 (4) | w3 (4).
+BBW_HD constexpr uint32_t pack_stencil3(int base, int dk, int dl, int w1, int w2, int w3) {
+  return uint32_t(base) | (uint32_t(dk) << 9) | (uint32_t(dl) << 13) | (uint32_t(w1) << 20) |
+         (uint32_t(w2) << 24) | (uint32_t(w3) << 28);
+}
+// 2D analogue on a face: inputs base, base + 1, base + db (reduction) or
+// base, base - 1, base - db (elevation); db = n + 1 - b2 for a reduction from
+// degree n, db = n - a2 + 1 for an elevation to degree n.
+// Word: base (7 bits) | db (4) | w1 (4) | w2 (4).
+BBW_HD constexpr uint32_t pack_stencil2(int base, int db, int w1, int w2) {
+  return uint32_t(base) | (uint32_t(db) << 7) | (uint32_t(w1) << 11) | (uint32_t(w2) << 15);
+}
 
 // Operator tables for one (N, M, real). Plain data, built on the host by
 // build_tables(), copied once to device memory and from there into each
@@ -56,20 +74,20 @@ struct Tables {
   static constexpr int Nfp = np2(N);
   static constexpr int Mp = np3(M);
   static constexpr int NMp = np3(N + M);
-  static constexpr int kDec3 = off3(N + M + 1);  // decode of degrees 0..N+M
-  static constexpr int kDec2 = off2(N + 1);      // 2D decode of degrees 0..N
 
-  real invfactN[Np + 1];  // 1 / alpha!        (degree N; pad entry unused)
+  real invfactN[Np + 1];  // 1 / alpha!        (degree N; pad entry 0)
   real factNM[NMp];       // gamma! / C(N+M,N)  (degree N+M)
   real invfactM[Mp];      // 1 / beta!          (degree M)
   real cj[N + 1];         // projection constants c_j of Theorem 5.3
   real ell[N + 1];        // lift layer factors (-1)^i C(N,i) / (i+1)
-  uint32_t dec3[kDec3];   // packed alpha of each index, per degree
-  uint32_t dec2[kDec2];   // packed (b0,b1,b2) of each 2D index, per degree
-  uint16_t prod[NMp * Mp];  // index of gamma-beta in degree N, or Np if gamma !>= beta
-  uint16_t fidx[4 * Nfp];   // own volume index of face node a of face f
-  uint16_t nidx[24 * Nfp];  // neighbour volume index for (nface, perm, a)
-  uint16_t lidx[4 * Np];    // volume index of (face f, layer i, face coords b)
+  uint32_t red3[off3(N + M)];   // reduction words, outputs of degree d = 0..N+M-1
+  uint32_t elev3[off3(N + 1)];  // elevation words, outputs of degree n = 0..N
+  uint32_t red2[off2(N)];       // 2D reduction words, outputs of degree 0..N-1
+  uint32_t elev2[np2(N)];       // 2D elevation words, outputs of degree N
+  uint16_t prod[NMp * Mp];      // index of gamma-beta in degree N, or Np if gamma !>= beta
+  uint16_t fidx[4 * Nfp];       // own volume index of face node a of face f
+  uint16_t nidx[24 * Nfp];      // neighbour volume index for (nface, perm, a)
+  uint16_t lidx[4 * Np];        // volume index of (face f, layer i, face coords b)
 };
 
 template <int N, int M, typename real>
@@ -87,54 +105,95 @@ void build_tables(Tables<N, M, real>& t, const double* cj) {
     return r;
   };
   auto binom = [&](int n, int k) { return fact(n) / (fact(k) * fact(n - k)); };
-  for (int n = 0; n <= N + M; ++n) {
+  // reductions into degree d from d + 1
+  for (int d = 0; d < N + M; ++d) {
+    const int n = d + 1;
+    int c = 0;
+    for (int l = 0; l <= d; ++l)
+      for (int k = 0; k <= d - l; ++k)
+        for (int j = 0; j <= d - l - k; ++j)
+          t.red3[off3(d) + c++] = pack_stencil3(idx3(n, j, k, l), n - l - k + 1,
+                                                (n - l + 1) * (n - l + 2) / 2 - k, j + 1, k + 1, l + 1);
+  }
+  // elevations into degree n from n - 1
+  for (int n = 1; n <= N; ++n) {
     int c = 0;
     for (int l = 0; l <= n; ++l)
       for (int k = 0; k <= n - l; ++k)
-        for (int j = 0; j <= n - l - k; ++j) t.dec3[off3(n) + c++] = pack4(n - j - k - l, j, k, l);
+        for (int j = 0; j <= n - l - k; ++j)
+          t.elev3[off3(n) + c++] = pack_stencil3(idx3(n - 1, j, k, l), n - l - k + 1,
+                                                 (n - l + 1) * (n - l + 2) / 2 - k, j, k, l);
   }
-  for (int n = 0; n <= N; ++n) {
+  t.elev3[0] = 0;
+  for (int d = 0; d < N; ++d) {
+    const int n = d + 1;
+    int c = 0;
+    for (int b2 = 0; b2 <= d; ++b2)
+      for (int b1 = 0; b1 <= d - b2; ++b1)
+        t.red2[off2(d) + c++] = pack_stencil2(idx2(n, b1, b2), n + 1 - b2, b1 + 1, b2 + 1);
+  }
+  {
+    int c = 0;
+    for (int a2 = 0; a2 <= N; ++a2)
+      for (int a1 = 0; a1 <= N - a2; ++a1) t.elev2[c++] = pack_stencil2(idx2(N - 1, a1, a2), N - a2 + 1, a1, a2);
+  }
+  // multi-indices in the library order
+  auto mi = [](int n, int i, int a[4]) {
+    int c = 0;
+    for (int l = 0; l <= n; ++l)
+      for (int k = 0; k <= n - l; ++k)
+        for (int j = 0; j <= n - l - k; ++j, ++c)
+          if (c == i) {
+            a[0] = n - j - k - l;
+            a[1] = j;
+            a[2] = k;
+            a[3] = l;
+            return;
+          }
+  };
+  auto mi2 = [](int n, int i, int b[3]) {
     int c = 0;
     for (int b2 = 0; b2 <= n; ++b2)
-      for (int b1 = 0; b1 <= n - b2; ++b1) t.dec2[off2(n) + c++] = pack4(n - b1 - b2, b1, b2, 0);
-  }
-  auto unpack = [](uint32_t w, int a[4]) {
-    for (int x = 0; x < 4; ++x) a[x] = int((w >> (8 * x)) & 255u);
+      for (int b1 = 0; b1 <= n - b2; ++b1, ++c)
+        if (c == i) {
+          b[0] = n - b1 - b2;
+          b[1] = b1;
+          b[2] = b2;
+          return;
+        }
   };
   for (int i = 0; i < Tb::Np; ++i) {
     int a[4];
-    unpack(t.dec3[off3(N) + i], a);
+    mi(N, i, a);
     t.invfactN[i] = real(1.0 / (fact(a[0]) * fact(a[1]) * fact(a[2]) * fact(a[3])));
   }
   t.invfactN[Tb::Np] = real(0);
   const double cnm = binom(N + M, N);
   for (int i = 0; i < Tb::NMp; ++i) {
     int g[4];
-    unpack(t.dec3[off3(N + M) + i], g);
+    mi(N + M, i, g);
     t.factNM[i] = real(fact(g[0]) * fact(g[1]) * fact(g[2]) * fact(g[3]) / cnm);
     for (int b = 0; b < Tb::Mp; ++b) {
       int be[4];
-      unpack(t.dec3[off3(M) + b], be);
+      mi(M, b, be);
       bool ok = true;
       for (int x = 0; x < 4; ++x) ok = ok && g[x] >= be[x];
-      t.prod[i * Tb::Mp + b] =
-          uint16_t(ok ? idx3(N, g[1] - be[1], g[2] - be[2], g[3] - be[3]) : Tb::Np);
+      t.prod[i * Tb::Mp + b] = uint16_t(ok ? idx3(N, g[1] - be[1], g[2] - be[2], g[3] - be[3]) : Tb::Np);
     }
   }
   for (int b = 0; b < Tb::Mp; ++b) {
     int be[4];
-    unpack(t.dec3[off3(M) + b], be);
+    mi(M, b, be);
     t.invfactM[b] = real(1.0 / (fact(be[0]) * fact(be[1]) * fact(be[2]) * fact(be[3])));
   }
   for (int j = 0; j <= N; ++j) {
     t.cj[j] = real(cj[j]);
     t.ell[j] = real(((j & 1) ? -1.0 : 1.0) * binom(N, j) / (j + 1));
   }
-  // face maps
   for (int f = 0; f < 4; ++f) {
     for (int a = 0; a < Tb::Nfp; ++a) {
-      int b[4];
-      unpack(t.dec2[off2(N) + a], b);
+      int b[3];
+      mi2(N, a, b);
       int al[4] = {0, 0, 0, 0};
       for (int x = 0; x < 3; ++x) al[kFaceVerts[f][x]] = b[x];
       t.fidx[f * Tb::Nfp + a] = uint16_t(idx3(N, al[1], al[2], al[3]));
@@ -148,8 +207,8 @@ void build_tables(Tables<N, M, real>& t, const double* cj) {
     for (int layer = 0; layer <= N; ++layer) {
       const int n2 = N - layer;
       for (int a = 0; a < np2(n2); ++a) {
-        int b[4];
-        unpack(t.dec2[off2(n2) + a], b);
+        int b[3];
+        mi2(n2, a, b);
         int al[4] = {0, 0, 0, 0};
         al[f] = layer;
         for (int x = 0; x < 3; ++x) al[kFaceVerts[f][x]] = b[x];

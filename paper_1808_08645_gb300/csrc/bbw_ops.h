@@ -23,8 +23,8 @@ struct KernelOps {
   cudaError_t (*launch_stage)(int M, bool dbl, const void* params, int grid, cudaStream_t s);
   // launch the weight-adjusted update; params points to WadgParams<float|double>
   cudaError_t (*launch_wadg)(int M, bool dbl, const void* params, int grid, cudaStream_t s);
-  int elems_per_cta;  // E of the launch shape
-  int team;           // T of the launch shape
+  // launch shape: lanes per group, elements per group, groups per CTA
+  int team[2], group_width[2], groups_per_cta[2];  // [0] float, [1] double
 };
 
 const KernelOps& ops_n1();

@@ -2,38 +2,40 @@
 //
 // One launch runs one stage of the five-stage low-storage RK4 (Sec. 6.3.1)
 // over all elements. The paper splits a stage into volume, surface and update
-// kernels (Sec. 6.3.1); here the three are one kernel so that each element's
-// coefficients are read from HBM once and its right-hand side never leaves
-// shared memory.
+// kernels (Sec. 6.3.1); here the three are one kernel, so each element's
+// coefficients are read from HBM once per stage and its right-hand side never
+// leaves shared memory.
 //
-// Work decomposition: a persistent CTA walks over tiles of E consecutive
-// elements; a team of T threads owns one element of the tile. Tile data is
-// staged in shared memory with an odd per-element stride; the sparse Bernstein
-// operators are applied as gather stencils on the multi-index lattice, each
-// thread producing output coefficients i = t, t+T, t+2T, ... of a phase, with
-// neighbour indices computed from the decoded multi-index (closed-form index
-// arithmetic, no CSR loads). Phases of one element are separated by team
-// barriers (__syncwarp for T <= 32).
+// Work decomposition. Elements are processed in groups of V: the V elements
+// of a group are interleaved in memory ([group][field][coefficient][V]) and
+// every thread of the group's team of T lanes works on all V at once with
+// vector loads and packed FP32x2 FMAs, so index arithmetic, table reads and
+// barriers are paid once per V elements. A CTA holds GC teams that share the
+// operator tables in shared memory and otherwise run independently: each
+// team walks over groups with a grid-wide stride, staging one group at a time
+// in its own shared region; the sparse Bernstein operators are gather stencils
+// on the multi-index lattice driven by one packed word per output item
+// (base index, lattice offsets, integer weights). Team phases are separated
+// by __syncwarp (teams never span warps).
 //
-// Per element and stage:
-//   V1/V2  grad p and div u (Sec. 4): degree N-1 barycentric combinations
+// Per group and stage:
+//   V1/V2  grad p and div u (Sec. 4): degree N-1 combinations
 //          w_beta = sum_m g_m a_{beta+e_m}, then one degree elevation
 //          (E^N_{N-1}, Eq. 12) with integer weights gamma_j.
-//   F      penalty fluxes of Eq. (2) on the 4 x N_fp face coefficients;
-//          neighbour traces come from shared memory when the neighbour is in
-//          the tile, else from q_in in global memory.
-//   L      lift L^f = E_L L0 (Sec. 4): L0 = ((2N+3)/3) I + (N^2/3) E E^T on
-//          the face, then layer i of the element receives
-//          ell_i (E^N_{N-i})^T L0 F with ell_i = (-1)^i C(N,i)/(i+1),
-//          evaluated as i successive 2D one-degree reductions.
+//   F      penalty fluxes of Eq. (2) on the 4 N_fp face coefficients, with the
+//          neighbour traces gathered from q_in (L2),
+//   L      then per face the lift L^f = E_L L0 (Sec. 4):
+//          L0 = ((2N+3)/3) I + (N^2/3) E E^T on the face, and layer i of the
+//          element receives ell_i (E^N_{N-i})^T L0 F,
+//          ell_i = (-1)^i C(N,i)/(i+1), by i successive 2D reductions.
 //   W      weight-adjusted update of the p right-hand side: Bernstein product
-//          with c^2_M (Eq. 11, as a convolution of factorial-scaled
-//          coefficients), M degree reductions, then P~_N of Eq. (20) by a
-//          downward reduction sweep (levels kept in registers) and an upward
-//          elevation sweep scaled by c_j.
-//   RK     res = a res + dt rhs, q_out = q_in + b res (stage 0 skips reading
-//          res because a_0 = 0), coalesced over the tile; non-finite values
-//          raise a status bit.
+//          with c^2_M (Eq. 11 as a convolution of factorial-scaled
+//          coefficients), M degree reductions, then P~_N of Eq. (20): a
+//          downward reduction sweep whose levels stay in registers and an
+//          upward elevation sweep scaled by c_j.
+//   RK     res = a res + dt rhs, q_out = q_in + b res over the group with vector
+//          loads and stores (stage 0 skips reading res, a_0 = 0); non-finite
+//          values raise a status bit.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -44,14 +46,14 @@ namespace bbw {
 
 template <typename real>
 struct StageParams {
-  const real* __restrict__ qin;   // [4][K][Np]
-  real* __restrict__ qout;        // [4][K][Np]
-  real* __restrict__ res;         // [4][K][Np], updated in place
-  const real* __restrict__ c2;    // [K][Mp]
-  const real* __restrict__ geom;  // [K][9]: d lambda_m / d x_i, m = 1..3
-  const int32_t* __restrict__ conn;  // [K][4] packed neighbour words
+  const real* __restrict__ qin;   // [G][4][Np][V]
+  real* __restrict__ qout;        // [G][4][Np][V]
+  real* __restrict__ res;         // [G][4][Np][V], updated in place
+  const real* __restrict__ c2;    // [G][Mp][V]
+  const real* __restrict__ geom;  // [G][9][V]: d lambda_m / d x_i, m = 1..3
+  const int32_t* __restrict__ conn;  // [G][4][V] packed neighbour words
   const void* __restrict__ tables;   // Tables<N, M, real>
-  int64_t K;
+  int64_t G;                      // number of element groups
   real a, b, dt;
   real tau_p, tau_u;
   int64_t src_elem;               // -1: no source
@@ -69,14 +71,157 @@ struct WadgParams {
   int64_t K;
 };
 
-// Launch shape per degree: T threads per element, E elements per CTA.
+// Launch shape per degree and precision: T lanes per group, V elements per
+// group, GC groups per CTA.
+template <int N, typename real>
+struct TileShape;
 template <int N>
-struct TileShape {
+struct TileShape<N, float> {
   static constexpr int T = N == 1 ? 4 : N == 2 ? 8 : N == 3 ? 16 : 32;
-  static constexpr int E = 256 / T;
+  static constexpr int V = N <= 5 ? 4 : 2;
+  static constexpr int GC = N <= 2 ? 128 / T : N <= 4 ? 256 / T : N <= 6 ? 8 : 4;
+};
+template <int N>
+struct TileShape<N, double> {
+  static constexpr int T = N == 1 ? 4 : N == 2 ? 8 : N == 3 ? 16 : 32;
+  static constexpr int V = N <= 4 ? 2 : 1;
+  static constexpr int GC = N <= 4 ? 256 / T : N <= 6 ? 8 : 4;
 };
 
-template <int N, int M, typename real, int T, int E>
+// ---------------------------------------------------------------------------
+// V-wide vectors of real. Float vectors of even width are stored as float2
+// pairs so that arithmetic maps to the packed FP32x2 instructions of sm_100+.
+
+template <typename real, int V>
+struct vec {
+  real x[V];
+  __device__ __forceinline__ real get(int i) const { return x[i]; }
+  __device__ __forceinline__ void set(int i, real v) { x[i] = v; }
+};
+template <int V>
+struct vec2f {
+  float2 h[V / 2];
+  __device__ __forceinline__ float get(int i) const { return (i & 1) ? h[i >> 1].y : h[i >> 1].x; }
+  __device__ __forceinline__ void set(int i, float v) {
+    if (i & 1)
+      h[i >> 1].y = v;
+    else
+      h[i >> 1].x = v;
+  }
+};
+template <>
+struct vec<float, 2> : vec2f<2> {};
+template <>
+struct vec<float, 4> : vec2f<4> {};
+
+template <typename real, int V>
+__device__ __forceinline__ vec<real, V> vzero() {
+  vec<real, V> r;
+#pragma unroll
+  for (int i = 0; i < V; ++i) r.set(i, real(0));
+  return r;
+}
+
+// shared/global vector load and store (V * sizeof(real) aligned)
+template <typename real, int V>
+__device__ __forceinline__ vec<real, V> vld(const real* p) {
+  vec<real, V> r;
+  if constexpr (V == 4 && sizeof(real) == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    r.h[0] = make_float2(t.x, t.y);
+    r.h[1] = make_float2(t.z, t.w);
+  } else if constexpr (V == 2 && sizeof(real) == 4) {
+    r.h[0] = *reinterpret_cast<const float2*>(p);
+  } else if constexpr (V == 2 && sizeof(real) == 8) {
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    r.x[0] = t.x;
+    r.x[1] = t.y;
+  } else {
+#pragma unroll
+    for (int i = 0; i < V; ++i) r.x[i] = p[i];
+  }
+  return r;
+}
+template <typename real, int V>
+__device__ __forceinline__ void vst(real* p, const vec<real, V>& v) {
+  if constexpr (V == 4 && sizeof(real) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v.h[0].x, v.h[0].y, v.h[1].x, v.h[1].y);
+  } else if constexpr (V == 2 && sizeof(real) == 4) {
+    *reinterpret_cast<float2*>(p) = v.h[0];
+  } else if constexpr (V == 2 && sizeof(real) == 8) {
+    *reinterpret_cast<double2*>(p) = make_double2(v.x[0], v.x[1]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < V; ++i) p[i] = v.x[i];
+  }
+}
+
+// acc += a * b (elementwise)
+template <typename real, int V>
+__device__ __forceinline__ void vfma(vec<real, V>& acc, const vec<real, V>& a, const vec<real, V>& b) {
+  if constexpr (sizeof(real) == 4 && V % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < V / 2; ++i) acc.h[i] = __ffma2_rn(a.h[i], b.h[i], acc.h[i]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < V; ++i) acc.x[i] = fma(a.x[i], b.x[i], acc.x[i]);
+  }
+}
+// acc += w * b (scalar w)
+template <typename real, int V>
+__device__ __forceinline__ void vfmas(vec<real, V>& acc, real w, const vec<real, V>& b) {
+  if constexpr (sizeof(real) == 4 && V % 2 == 0) {
+    const float2 ww = make_float2(w, w);
+#pragma unroll
+    for (int i = 0; i < V / 2; ++i) acc.h[i] = __ffma2_rn(ww, b.h[i], acc.h[i]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < V; ++i) acc.x[i] = fma(w, b.x[i], acc.x[i]);
+  }
+}
+// w * a
+template <typename real, int V>
+__device__ __forceinline__ vec<real, V> vmuls(real w, const vec<real, V>& a) {
+  vec<real, V> r;
+  if constexpr (sizeof(real) == 4 && V % 2 == 0) {
+    const float2 ww = make_float2(w, w);
+#pragma unroll
+    for (int i = 0; i < V / 2; ++i) r.h[i] = __fmul2_rn(ww, a.h[i]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < V; ++i) r.x[i] = w * a.x[i];
+  }
+  return r;
+}
+// a * b (elementwise)
+template <typename real, int V>
+__device__ __forceinline__ vec<real, V> vmul(const vec<real, V>& a, const vec<real, V>& b) {
+  vec<real, V> r;
+  if constexpr (sizeof(real) == 4 && V % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < V / 2; ++i) r.h[i] = __fmul2_rn(a.h[i], b.h[i]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < V; ++i) r.x[i] = a.x[i] * b.x[i];
+  }
+  return r;
+}
+// a + w * b
+template <typename real, int V>
+__device__ __forceinline__ vec<real, V> vaxpy(const vec<real, V>& a, real w, const vec<real, V>& b) {
+  vec<real, V> r = a;
+  vfmas(r, w, b);
+  return r;
+}
+// a - b
+template <typename real, int V>
+__device__ __forceinline__ vec<real, V> vsub(const vec<real, V>& a, const vec<real, V>& b) {
+  return vaxpy(a, real(-1), b);
+}
+
+// ---------------------------------------------------------------------------
+
+template <int N, int M, typename real, int T, int V, int GC>
 struct StageCfg {
   using Tab = Tables<N, M, real>;
   static constexpr int Np = np3(N);
@@ -84,20 +229,27 @@ struct StageCfg {
   static constexpr int Nfp = np2(N);
   static constexpr int Mp = np3(M);
   static constexpr int NMp = np3(N + M);
-  static constexpr int THREADS = T * E;
+  static constexpr int THREADS = T * GC;
   static constexpr int BUF = NMp > Np + 1 ? NMp : Np + 1;
+  // scratch per group, in vectors: V1 (4 (N-1)_p), neighbour traces of the
+  // four faces, later the fluxes and two lift pyramid levels (16 N_fp), WADG
+  // ping-pong (2 BUF)
   static constexpr int S_VOL = 4 * Nm1p;
-  static constexpr int S_LIFT = 12 * Nfp;
+  static constexpr int S_LIFT = 16 * Nfp;
   static constexpr int S_WADG = 2 * BUF;
   static constexpr int S_SZ =
       S_VOL > S_LIFT ? (S_VOL > S_WADG ? S_VOL : S_WADG) : (S_LIFT > S_WADG ? S_LIFT : S_WADG);
-  static constexpr int STRIDE = (8 * Np + S_SZ) | 1;  // odd: spreads elements over banks
-  static constexpr int GEO = 28;  // g[4][3] then (nx, ny, nz, |f|/|D|) per face
+  // per-team region, in vectors: Q [4][Np] | R [4][Np] | S | normals [4][4] |
+  // c2 [Mp] | connectivity words [4][V] (int32); odd, so that teams start in
+  // different shared-memory banks
+  static constexpr int CONNV = (16 + int(sizeof(real)) - 1) / int(sizeof(real));
+  static constexpr int TEAMV = (8 * Np + S_SZ + 16 + Mp + CONNV) | 1;
   static constexpr int TAB = table_bytes<N, M, real>();
-  static constexpr int SMEM =
-      TAB + int(sizeof(real)) * (E * STRIDE + E * GEO + E * Mp) + 4 * E * 4;
+  static constexpr int SMEM = TAB + int(sizeof(real)) * V * GC * TEAMV;
   static constexpr int RMAX = (Np + T - 1) / T;
-  static_assert(T <= 32 && 32 % T == 0, "team must divide a warp");
+  static constexpr int RK_IT = (4 * Np + T - 1) / T;  // RK vectors per lane
+  static_assert(T >= 4 && T <= 32 && 32 % T == 0, "team must divide a warp and cover the 4 faces");
+  static_assert(V == 1 || V == 2 || V == 4, "group width");
 };
 
 template <int T>
@@ -105,11 +257,18 @@ __device__ __forceinline__ void team_sync() {
   if constexpr (T > 1) __syncwarp();
 }
 
-__device__ __forceinline__ void unpack4(uint32_t w, int& a0, int& a1, int& a2, int& a3) {
-  a0 = int(w & 255u);
-  a1 = int((w >> 8) & 255u);
-  a2 = int((w >> 16) & 255u);
-  a3 = int(w >> 24);
+struct Stencil3 {
+  int base, dk, dl, w1, w2, w3;
+};
+__device__ __forceinline__ Stencil3 unpack_stencil3(uint32_t w) {
+  return {int(w & 511u), int((w >> 9) & 15u), int((w >> 13) & 127u), int((w >> 20) & 15u),
+          int((w >> 24) & 15u), int(w >> 28)};
+}
+struct Stencil2 {
+  int base, db, w1, w2;
+};
+__device__ __forceinline__ Stencil2 unpack_stencil2(uint32_t w) {
+  return {int(w & 127u), int((w >> 7) & 15u), int((w >> 11) & 15u), int((w >> 15) & 15u)};
 }
 
 // Copy the operator tables into shared memory (16-byte words).
@@ -120,26 +279,48 @@ __device__ __forceinline__ void load_tables(unsigned char* dst, const void* src)
   for (int i = threadIdx.x; i < BYTES / 16; i += THREADS) d[i] = s[i];
 }
 
-// Weight-adjusted update of one element (Sec. 5): out = P^{N+M}_N (c2 * r).
-// On entry A[0..Np) holds r * invfactN (A[Np] = 0), bh the c2 coefficients
+// Bulk prefetch of [p, p + bytes) into L2 (sm_90+); p 16-byte aligned.
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  bytes &= ~15u;
+  if (bytes && (reinterpret_cast<uintptr_t>(p) & 15u) == 0)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Asynchronous global -> shared copies (cp.async, sm_80+) of 4, 8 or 16 bytes.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  const uint32_t s = uint32_t(__cvta_generic_to_shared(smem));
+  if constexpr (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+  else if constexpr (BYTES == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Weight-adjusted update of one group (Sec. 5): out = P^{N+M}_N (c2 * r).
+// On entry A[0..Np) holds r * invfactN (A[Np] = 0) and bh the c2 coefficients
 // scaled by invfactM. The result for items i = t + r*T is left in lv[0][r].
-template <int N, int M, typename real, int T, int RMAX>
-__device__ __forceinline__ void wadg_element(const Tables<N, M, real>& tab, real* A, real* B,
-                                             const real (&bh)[np3(M) > 0 ? np3(M) : 1],
-                                             bool active, int t, real (&lv)[N + 1][RMAX]) {
+// A and B are vector buffers of BUF vectors each.
+template <int N, int M, typename real, int T, int V, int RMAX>
+__device__ __forceinline__ void wadg_group(const Tables<N, M, real>& tab, real* A, real* B,
+                                           const vec<real, V> (&bh)[np3(M)], bool active, int t,
+                                           vec<real, V> (&lv)[N + 1][RMAX]) {
+  using vt = vec<real, V>;
   constexpr int Np = np3(N);
   constexpr int Mp = np3(M);
   constexpr int NMp = np3(N + M);
   // product h_gamma = gamma!/C(N+M,N) sum_beta (b_beta/beta!) (a_{gamma-beta}/(gamma-beta)!)
   for (int i = t; active && i < NMp; i += T) {
     const uint16_t* pr = tab.prod + i * Mp;
-    real h = real(0);
+    vt h = vzero<real, V>();
 #pragma unroll
-    for (int b = 0; b < Mp; ++b) h += bh[b] * A[pr[b]];
-    B[i] = h * tab.factNM[i];
+    for (int b = 0; b < Mp; ++b) vfma(h, bh[b], vld<real, V>(A + pr[b] * V));
+    vst(B + i * V, vmuls(tab.factNM[i], h));
   }
   team_sync<T>();
-  // M one-degree reductions (E^{n}_{n-1})^T, n = N+M .. N+1 (Eq. 20, right factors)
+  // M one-degree reductions (E^{n}_{n-1})^T, n = N+M .. N+1 (right factors of Eq. 20)
   real* X = B;
   real* Y = A;
 #pragma unroll
@@ -147,11 +328,12 @@ __device__ __forceinline__ void wadg_element(const Tables<N, M, real>& tab, real
     const int n = N + M - r;
     const real inv = real(1) / real(n);
     for (int i = t; active && i < np3(n - 1); i += T) {
-      int b0, j, k, l;
-      unpack4(tab.dec3[off3(n - 1) + i], b0, j, k, l);
-      const real v = real(b0 + 1) * X[idx3(n, j, k, l)] + real(j + 1) * X[idx3(n, j + 1, k, l)] +
-                     real(k + 1) * X[idx3(n, j, k + 1, l)] + real(l + 1) * X[idx3(n, j, k, l + 1)];
-      Y[i] = v * inv;
+      const Stencil3 s = unpack_stencil3(tab.red3[off3(n - 1) + i]);
+      vt v = vmuls(real(n + 3 - s.w1 - s.w2 - s.w3), vld<real, V>(X + s.base * V));
+      vfmas(v, real(s.w1), vld<real, V>(X + (s.base + 1) * V));
+      vfmas(v, real(s.w2), vld<real, V>(X + (s.base + s.dk) * V));
+      vfmas(v, real(s.w3), vld<real, V>(X + (s.base + s.dl) * V));
+      vst(Y + i * V, vmuls(inv, v));
     }
     real* tmp = X;
     X = Y;
@@ -162,7 +344,7 @@ __device__ __forceinline__ void wadg_element(const Tables<N, M, real>& tab, real
 #pragma unroll
   for (int r = 0; r < RMAX; ++r) {
     const int i = t + r * T;
-    lv[0][r] = (active && i < Np) ? X[i] : real(0);
+    lv[0][r] = (active && i < Np) ? vld<real, V>(X + i * V) : vzero<real, V>();
   }
   // downward sweep v_j = (E^{n}_{n-1})^T v_{j-1}, n = N-j+1
 #pragma unroll
@@ -173,14 +355,14 @@ __device__ __forceinline__ void wadg_element(const Tables<N, M, real>& tab, real
     for (int r = 0; r < RMAX; ++r) {
       const int i = t + r * T;
       if (r * T < np3(n - 1) && active && i < np3(n - 1)) {
-        int b0, j, k, l;
-        unpack4(tab.dec3[off3(n - 1) + i], b0, j, k, l);
-        const real v = (real(b0 + 1) * X[idx3(n, j, k, l)] + real(j + 1) * X[idx3(n, j + 1, k, l)] +
-                        real(k + 1) * X[idx3(n, j, k + 1, l)] +
-                        real(l + 1) * X[idx3(n, j, k, l + 1)]) *
-                       inv;
+        const Stencil3 s = unpack_stencil3(tab.red3[off3(n - 1) + i]);
+        vt v = vmuls(real(n + 3 - s.w1 - s.w2 - s.w3), vld<real, V>(X + s.base * V));
+        vfmas(v, real(s.w1), vld<real, V>(X + (s.base + 1) * V));
+        vfmas(v, real(s.w2), vld<real, V>(X + (s.base + s.dk) * V));
+        vfmas(v, real(s.w3), vld<real, V>(X + (s.base + s.dl) * V));
+        v = vmuls(inv, v);
         lv[jl][r] = v;
-        Y[i] = v;
+        vst(Y + i * V, v);
       }
     }
     real* tmp = X;
@@ -189,7 +371,7 @@ __device__ __forceinline__ void wadg_element(const Tables<N, M, real>& tab, real
     team_sync<T>();
   }
   // upward sweep: w_N = c_N v_N, w_j = c_j v_j + E^{n}_{n-1} w_{j+1}, n = N-j
-  if (active && t == 0) X[0] = tab.cj[N] * lv[N][0];
+  if (active && t == 0) vst(X, vmuls(tab.cj[N], lv[N][0]));
   team_sync<T>();
 #pragma unroll
   for (int jl = N - 1; jl >= 0; --jl) {
@@ -200,16 +382,17 @@ __device__ __forceinline__ void wadg_element(const Tables<N, M, real>& tab, real
     for (int r = 0; r < RMAX; ++r) {
       const int i = t + r * T;
       if (r * T < np3(n) && active && i < np3(n)) {
-        int a0, j, k, l;
-        unpack4(tab.dec3[off3(n) + i], a0, j, k, l);
-        real acc = real(0);
-        if (a0 > 0) acc += real(a0) * X[idx3(n - 1, j, k, l)];
-        if (j > 0) acc += real(j) * X[idx3(n - 1, j - 1, k, l)];
-        if (k > 0) acc += real(k) * X[idx3(n - 1, j, k - 1, l)];
-        if (l > 0) acc += real(l) * X[idx3(n - 1, j, k, l - 1)];
-        const real w = c * lv[jl][r] + acc * inv;
+        const Stencil3 s = unpack_stencil3(tab.elev3[off3(n) + i]);
+        const int a0 = n - s.w1 - s.w2 - s.w3;
+        vt acc = vzero<real, V>();
+        if (a0 > 0) vfmas(acc, real(a0), vld<real, V>(X + s.base * V));
+        if (s.w1 > 0) vfmas(acc, real(s.w1), vld<real, V>(X + (s.base - 1) * V));
+        if (s.w2 > 0) vfmas(acc, real(s.w2), vld<real, V>(X + (s.base - s.dk) * V));
+        if (s.w3 > 0) vfmas(acc, real(s.w3), vld<real, V>(X + (s.base - s.dl) * V));
+        vt w = vmuls(c, lv[jl][r]);
+        vfmas(w, inv, acc);
         if (jl > 0)
-          Y[i] = w;
+          vst(Y + i * V, w);
         else
           lv[0][r] = w;
       }
@@ -221,228 +404,233 @@ __device__ __forceinline__ void wadg_element(const Tables<N, M, real>& tab, real
   }
 }
 
-template <int N, int M, typename real, int T, int E>
-__global__ void __launch_bounds__(T* E) stage_kernel(const StageParams<real> P) {
-  using C = StageCfg<N, M, real, T, E>;
+template <int N, int M, typename real, int T, int V, int GC>
+__global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P) {
+  using C = StageCfg<N, M, real, T, V, GC>;
   using Tab = typename C::Tab;
+  using vt = vec<real, V>;
   constexpr int Np = C::Np, Nm1p = C::Nm1p, Nfp = C::Nfp, Mp = C::Mp;
-  constexpr int STRIDE = C::STRIDE, THREADS = C::THREADS;
+  constexpr int QV = 4 * Np;  // vectors of one state block of a group
 
   extern __shared__ __align__(16) unsigned char smem[];
   const Tab& tab = *reinterpret_cast<const Tab*>(smem);
-  real* el = reinterpret_cast<real*>(smem + C::TAB);
-  real* gs = el + E * STRIDE;
-  real* c2s = gs + E * C::GEO;
-  int* cs = reinterpret_cast<int*>(c2s + E * Mp);
-
-  load_tables<C::TAB, THREADS>(smem, P.tables);
+  load_tables<C::TAB, C::THREADS>(smem, P.tables);
+  __syncthreads();  // the only CTA-wide barrier: teams run independently below
 
   const int team = threadIdx.x / T;
   const int t = threadIdx.x % T;
-  const int64_t K = P.K;
-  const size_t fs = size_t(K) * Np;  // field stride in global memory
-  const int64_t ntiles = (K + E - 1) / E;
+  real* Q = reinterpret_cast<real*>(smem + C::TAB) + team * C::TEAMV * V;  // [4][Np]
+  real* R = Q + QV * V;                                                   // [4][Np]
+  real* S = R + QV * V;                                                   // scratch
+  real* NRM = S + C::S_SZ * V;  // [4 faces][nx, ny, nz, (1/2)|f|/|D|]
+  real* C2S = NRM + 16 * V;     // [Mp]
+  int* CS = reinterpret_cast<int*>(C2S + Mp * V);  // [4][V]
+  const int64_t G = P.G;
+  const int64_t stride = int64_t(gridDim.x) * GC;
+  const bool read_res = P.a != real(0);
   bool bad = false;
 
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t e0 = tile * E;
-    const int nE = int(K - e0 < E ? K - e0 : E);
-    __syncthreads();  // tables ready / previous tile finished with shared memory
-
-    // ---- stage the tile: q, geometry, c2, connectivity ----
+  for (int64_t g = int64_t(blockIdx.x) * GC + team; g < G; g += stride) {
+    // the team's next group into L2
+    if (t == 0 && g + stride < G) {
+      const size_t qb = size_t(QV) * V * sizeof(real);
+      prefetch_l2(P.qin + size_t(g + stride) * QV * V, uint32_t(qb));
+      if (read_res) prefetch_l2(P.res + size_t(g + stride) * QV * V, uint32_t(qb));
+    }
+    // ---- stage the group: q, c2, connectivity into shared; geometry into registers ----
+    {
+      constexpr int VB = V * int(sizeof(real));  // bytes per vector: 4, 8 or 16
+      const real* qg = P.qin + size_t(g) * QV * V;
+      for (int idx = t; idx < QV; idx += T) cp_async<VB>(Q + idx * V, qg + size_t(idx) * V);
+      for (int idx = t; idx < Mp; idx += T) cp_async<VB>(C2S + idx * V, P.c2 + (size_t(g) * Mp + idx) * V);
+      for (int idx = t; idx < 4 * V; idx += T) cp_async<4>(CS + idx, P.conn + size_t(g) * 4 * V + idx);
+    }
+    vt gm[4][3];
 #pragma unroll
-    for (int fld = 0; fld < 4; ++fld) {
-      const real* src = P.qin + fld * fs + size_t(e0) * Np;
-      for (int idx = threadIdx.x; idx < nE * Np; idx += THREADS) {
-        const int e = idx / Np;
-        el[e * STRIDE + fld * Np + (idx - e * Np)] = src[idx];
+    for (int m = 1; m < 4; ++m)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) gm[m][d] = vld<real, V>(P.geom + (size_t(g) * 9 + 3 * (m - 1) + d) * V);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      gm[0][d] = vmuls(real(-1), gm[1][d]);
+      gm[0][d] = vaxpy(gm[0][d], real(-1), gm[2][d]);
+      gm[0][d] = vaxpy(gm[0][d], real(-1), gm[3][d]);
+    }
+    // face f = t: n = -g_f / |g_f|, (1/2) |f|/|D| = (3/2) |g_f|
+    if (t < 4) {
+      vt fx = gm[0][0], fy = gm[0][1], fz = gm[0][2];
+#pragma unroll
+      for (int m = 1; m < 4; ++m)
+        if (t == m) {
+          fx = gm[m][0];
+          fy = gm[m][1];
+          fz = gm[m][2];
+        }
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const real gx = fx.get(v), gy = fy.get(v), gz = fz.get(v);
+        const real gn = sqrt(gx * gx + gy * gy + gz * gz);
+        const real inv = real(1) / gn;
+        real* nr = NRM + 4 * t * V + v;
+        nr[0] = -gx * inv;
+        nr[V] = -gy * inv;
+        nr[2 * V] = -gz * inv;
+        nr[3 * V] = real(1.5) * gn;
       }
     }
-    for (int idx = threadIdx.x; idx < nE * 9; idx += THREADS) {
-      const int e = idx / 9;
-      gs[e * C::GEO + 3 + (idx - e * 9)] = P.geom[size_t(e0) * 9 + idx];
-    }
-    for (int idx = threadIdx.x; idx < nE * Mp; idx += THREADS) c2s[idx] = P.c2[size_t(e0) * Mp + idx];
-    for (int idx = threadIdx.x; idx < nE * 4; idx += THREADS) cs[idx] = P.conn[size_t(e0) * 4 + idx];
-    __syncthreads();
-    // derived geometry: g_0 = -(g_1 + g_2 + g_3); face f: n = -g_f/|g_f|, |f|/|D| = 3 |g_f|
-    for (int idx = threadIdx.x; idx < nE * 4; idx += THREADS) {
-      const int e = idx >> 2, f = idx & 3;
-      real* G = gs + e * C::GEO;
-      real gx, gy, gz;
-      if (f == 0) {
-        gx = -(G[3] + G[6] + G[9]);
-        gy = -(G[4] + G[7] + G[10]);
-        gz = -(G[5] + G[8] + G[11]);
-      } else {
-        gx = G[3 * f];
-        gy = G[3 * f + 1];
-        gz = G[3 * f + 2];
-      }
-      const real gn = sqrt(gx * gx + gy * gy + gz * gz);
-      const real inv = real(1) / gn;
-      real* nr = G + 12 + 4 * f;
-      nr[0] = -gx * inv;
-      nr[1] = -gy * inv;
-      nr[2] = -gz * inv;
-      nr[3] = real(3) * gn;
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < nE; idx += THREADS) {
-      real* G = gs + idx * C::GEO;
-      G[0] = -(G[3] + G[6] + G[9]);
-      G[1] = -(G[4] + G[7] + G[10]);
-      G[2] = -(G[5] + G[8] + G[11]);
-    }
-    __syncthreads();
+    cp_async_wait_all();
+    team_sync<T>();
 
-    const bool active = team < nE;
-    const int e = active ? team : 0;
-    real* Q = el + e * STRIDE;
-    real* R = Q + 4 * Np;
-    real* S = R + 4 * Np;
-    const real* G = gs + e * C::GEO;
-    real g[4][3];
-#pragma unroll
-    for (int m = 0; m < 4; ++m)
-#pragma unroll
-      for (int d = 0; d < 3; ++d) g[m][d] = G[3 * m + d];
-
-    // ---- V1: barycentric combinations at degree N-1 ----
-    for (int i = t; active && i < Nm1p; i += T) {
-      int b0, j, k, l;
-      unpack4(tab.dec3[off3(N - 1) + i], b0, j, k, l);
-      const int im[4] = {idx3(N, j, k, l), idx3(N, j + 1, k, l), idx3(N, j, k + 1, l),
-                         idx3(N, j, k, l + 1)};
-      real gx = 0, gy = 0, gz = 0, dv = 0;
+    // ---- V1: barycentric combinations at degree N-1, S = [4][Nm1p] ----
+    for (int i = t; i < Nm1p; i += T) {
+      const Stencil3 s = unpack_stencil3(tab.red3[off3(N - 1) + i]);
+      const int im[4] = {s.base, s.base + 1, s.base + s.dk, s.base + s.dl};
+      vt gx = vzero<real, V>(), gy = vzero<real, V>(), gz = vzero<real, V>(), dv = vzero<real, V>();
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
-        const real p = Q[im[m]];
-        gx += g[m][0] * p;
-        gy += g[m][1] * p;
-        gz += g[m][2] * p;
-        dv += g[m][0] * Q[Np + im[m]] + g[m][1] * Q[2 * Np + im[m]] + g[m][2] * Q[3 * Np + im[m]];
+        const vt p = vld<real, V>(Q + im[m] * V);
+        vfma(gx, gm[m][0], p);
+        vfma(gy, gm[m][1], p);
+        vfma(gz, gm[m][2], p);
+        vfma(dv, gm[m][0], vld<real, V>(Q + (Np + im[m]) * V));
+        vfma(dv, gm[m][1], vld<real, V>(Q + (2 * Np + im[m]) * V));
+        vfma(dv, gm[m][2], vld<real, V>(Q + (3 * Np + im[m]) * V));
       }
-      S[i] = gx;
-      S[Nm1p + i] = gy;
-      S[2 * Nm1p + i] = gz;
-      S[3 * Nm1p + i] = dv;
+      vst(S + i * V, gx);
+      vst(S + (Nm1p + i) * V, gy);
+      vst(S + (2 * Nm1p + i) * V, gz);
+      vst(S + (3 * Nm1p + i) * V, dv);
     }
     team_sync<T>();
     // ---- V2: elevate to degree N; rhs_u = -grad p, rhs_p = -div u ----
-    for (int i = t; active && i < Np; i += T) {
-      int a0, j, k, l;
-      unpack4(tab.dec3[off3(N) + i], a0, j, k, l);
-      real ax = 0, ay = 0, az = 0, ad = 0;
-      auto add = [&](int s, int w) {
-        const real wt = real(w);
-        ax += wt * S[s];
-        ay += wt * S[Nm1p + s];
-        az += wt * S[2 * Nm1p + s];
-        ad += wt * S[3 * Nm1p + s];
+    for (int i = t; i < Np; i += T) {
+      const Stencil3 s = unpack_stencil3(tab.elev3[off3(N) + i]);
+      const int a0 = N - s.w1 - s.w2 - s.w3;
+      vt ax = vzero<real, V>(), ay = vzero<real, V>(), az = vzero<real, V>(), ad = vzero<real, V>();
+      auto add = [&](int idx, int w) {
+        const real wt = real(-w);
+        vfmas(ax, wt, vld<real, V>(S + idx * V));
+        vfmas(ay, wt, vld<real, V>(S + (Nm1p + idx) * V));
+        vfmas(az, wt, vld<real, V>(S + (2 * Nm1p + idx) * V));
+        vfmas(ad, wt, vld<real, V>(S + (3 * Nm1p + idx) * V));
       };
-      if (a0 > 0) add(idx3(N - 1, j, k, l), a0);
-      if (j > 0) add(idx3(N - 1, j - 1, k, l), j);
-      if (k > 0) add(idx3(N - 1, j, k - 1, l), k);
-      if (l > 0) add(idx3(N - 1, j, k, l - 1), l);
-      R[i] = -ad;
-      R[Np + i] = -ax;
-      R[2 * Np + i] = -ay;
-      R[3 * Np + i] = -az;
+      if (a0 > 0) add(s.base, a0);
+      if (s.w1 > 0) add(s.base - 1, s.w1);
+      if (s.w2 > 0) add(s.base - s.dk, s.w2);
+      if (s.w3 > 0) add(s.base - s.dl, s.w3);
+      vst(R + i * V, ad);
+      vst(R + (Np + i) * V, ax);
+      vst(R + (2 * Np + i) * V, ay);
+      vst(R + (3 * Np + i) * V, az);
     }
     team_sync<T>();
 
-    // ---- F: penalty fluxes on the four faces, scaled by |f|/|D| ----
-    real* Fp = S;
-    real* Fu = S + 4 * Nfp;
-    for (int it = t; active && it < 4 * Nfp; it += T) {
+    // ---- F: neighbour traces of all four faces into NB = [field][4 Nfp]
+    // (asynchronous 4-byte copies, many in flight), then the penalty fluxes
+    // of Eq. (2) in place: F_p over field 0 and F_u over field 1 ----
+    real* NB = S;
+    for (int it = t; it < 4 * Nfp; it += T) {
       const int f = it / Nfp;
       const int a = it - f * Nfp;
-      const int io = tab.fidx[it];
-      const real pm = Q[io], um = Q[Np + io], vm = Q[2 * Np + io], wm = Q[3 * Np + io];
-      const int code = cs[e * 4 + f];
-      real pp, up, vp, wp;
-      if (code < 0) {  // p = 0 wall: mirror state
-        pp = -pm;
-        up = um;
-        vp = vm;
-        wp = wm;
-      } else {
-        const int64_t nb = int64_t(code >> 5);
-        const int ni = tab.nidx[(((code >> 3) & 3) * 6 + (code & 7)) * Nfp + a];
-        const int64_t loc = nb - e0;
-        if (loc >= 0 && loc < nE) {
-          const real* Qn = el + loc * STRIDE;
-          pp = Qn[ni];
-          up = Qn[Np + ni];
-          vp = Qn[2 * Np + ni];
-          wp = Qn[3 * Np + ni];
-        } else {
-          const real* qn = P.qin + size_t(nb) * Np + ni;
-          pp = qn[0];
-          up = qn[fs];
-          vp = qn[2 * fs];
-          wp = qn[3 * fs];
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const int c = CS[f * V + v];
+        if (c >= 0) {
+          const int64_t nb = int64_t(c >> 5);
+          const int ni = tab.nidx[(((c >> 3) & 3) * 6 + (c & 7)) * Nfp + a];
+          const int64_t gq = nb / V;
+          const real* src = P.qin + (size_t(gq) * QV + ni) * V + (nb - gq * V);
+#pragma unroll
+          for (int fld = 0; fld < 4; ++fld) cp_async<int(sizeof(real))>(NB + (fld * 4 * Nfp + it) * V + v, src + fld * Np * V);
         }
       }
-      const real* nr = G + 12 + 4 * f;
-      const real jp = pp - pm;
-      const real ndu = nr[0] * (up - um) + nr[1] * (vp - vm) + nr[2] * (wp - wm);
-      const real hs = real(0.5) * nr[3];
-      Fp[it] = hs * (P.tau_p * jp - ndu);
-      Fu[it] = hs * (P.tau_u * ndu - jp);
+    }
+    cp_async_wait_all();
+    for (int it = t; it < 4 * Nfp; it += T) {
+      const int f = it / Nfp;
+      const int io = tab.fidx[it];
+      const vt pm = vld<real, V>(Q + io * V), um = vld<real, V>(Q + (Np + io) * V),
+               vm = vld<real, V>(Q + (2 * Np + io) * V), wm = vld<real, V>(Q + (3 * Np + io) * V);
+      vt pp = vld<real, V>(NB + it * V), up = vld<real, V>(NB + (4 * Nfp + it) * V),
+         vp = vld<real, V>(NB + (8 * Nfp + it) * V), wp = vld<real, V>(NB + (12 * Nfp + it) * V);
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+        if (CS[f * V + v] < 0) {  // p = 0 wall: mirror state
+          pp.set(v, -pm.get(v));
+          up.set(v, um.get(v));
+          vp.set(v, vm.get(v));
+          wp.set(v, wm.get(v));
+        }
+      const real* nr = NRM + 4 * f * V;
+      const vt nx = vld<real, V>(nr), ny = vld<real, V>(nr + V), nz = vld<real, V>(nr + 2 * V),
+               hs = vld<real, V>(nr + 3 * V);
+      const vt jp = vsub(pp, pm);
+      vt ndu = vmul(nx, vsub(up, um));
+      vfma(ndu, ny, vsub(vp, vm));
+      vfma(ndu, nz, vsub(wp, wm));
+      vst(NB + it * V, vmul(hs, vaxpy(vmuls(P.tau_p, jp), real(-1), ndu)));
+      vst(NB + (4 * Nfp + it) * V, vmul(hs, vaxpy(vmuls(P.tau_u, ndu), real(-1), jp)));
     }
     team_sync<T>();
 
     // ---- L: lift L^f = E_L L0 per face, accumulated into rhs ----
     {
-      real* bufA = S + 8 * Nfp;  // [p | u], Nfp each
-      real* bufB = bufA + 2 * Nfp;
+      real* bufA = NB + 8 * Nfp * V;  // [p, u][Nfp], over the traces of fields 2, 3
+      real* bufB = bufA + 2 * Nfp * V;
       const real third = real(1) / real(3);
 #pragma unroll 1
       for (int f = 0; f < 4; ++f) {
-        const real* fp = Fp + f * Nfp;
-        const real* fu = Fu + f * Nfp;
-        const real* nr = G + 12 + 4 * f;
-        const real nx = nr[0], ny = nr[1], nz = nr[2];
+        const real* Fp = NB + f * Nfp * V;
+        const real* Fu = NB + (4 * Nfp + f * Nfp) * V;
+        const real* nr = NRM + 4 * f * V;
+        const vt nx = vld<real, V>(nr), ny = vld<real, V>(nr + V), nz = vld<real, V>(nr + 2 * V);
         // t = E'^T F at degree N-1 (integer weights b_x + 1)
-        for (int i = t; active && i < np2(N - 1); i += T) {
-          int b0, b1, b2, unused;
-          unpack4(tab.dec2[off2(N - 1) + i], b0, b1, b2, unused);
-          const int i0 = idx2(N, b1, b2), i1 = idx2(N, b1 + 1, b2), i2 = idx2(N, b1, b2 + 1);
-          bufB[i] = real(b0 + 1) * fp[i0] + real(b1 + 1) * fp[i1] + real(b2 + 1) * fp[i2];
-          bufB[Nfp + i] = real(b0 + 1) * fu[i0] + real(b1 + 1) * fu[i1] + real(b2 + 1) * fu[i2];
+        for (int i = t; i < np2(N - 1); i += T) {
+          const Stencil2 s = unpack_stencil2(tab.red2[off2(N - 1) + i]);
+          const real w0 = real(N + 2 - s.w1 - s.w2), w1 = real(s.w1), w2 = real(s.w2);
+          vt tp = vmuls(w0, vld<real, V>(Fp + s.base * V));
+          vfmas(tp, w1, vld<real, V>(Fp + (s.base + 1) * V));
+          vfmas(tp, w2, vld<real, V>(Fp + (s.base + s.db) * V));
+          vt tu = vmuls(w0, vld<real, V>(Fu + s.base * V));
+          vfmas(tu, w1, vld<real, V>(Fu + (s.base + 1) * V));
+          vfmas(tu, w2, vld<real, V>(Fu + (s.base + s.db) * V));
+          vst(bufB + i * V, tp);
+          vst(bufB + (Nfp + i) * V, tu);
         }
         team_sync<T>();
         // g0 = L0 F = ((2N+3) F + E' t) / 3; layer 0 (ell_0 = 1)
-        for (int i = t; active && i < Nfp; i += T) {
-          int a0, a1, a2, unused;
-          unpack4(tab.dec2[off2(N) + i], a0, a1, a2, unused);
-          real ep = 0, eu = 0;
+        for (int i = t; i < Nfp; i += T) {
+          const Stencil2 s = unpack_stencil2(tab.elev2[i]);
+          const int a0 = N - s.w1 - s.w2;
+          vt ep = vmuls(real(2 * N + 3), vld<real, V>(Fp + i * V));
+          vt eu = vmuls(real(2 * N + 3), vld<real, V>(Fu + i * V));
           if (a0 > 0) {
-            const int s = idx2(N - 1, a1, a2);
-            ep += real(a0) * bufB[s];
-            eu += real(a0) * bufB[Nfp + s];
+            vfmas(ep, real(a0), vld<real, V>(bufB + s.base * V));
+            vfmas(eu, real(a0), vld<real, V>(bufB + (Nfp + s.base) * V));
           }
-          if (a1 > 0) {
-            const int s = idx2(N - 1, a1 - 1, a2);
-            ep += real(a1) * bufB[s];
-            eu += real(a1) * bufB[Nfp + s];
+          if (s.w1 > 0) {
+            vfmas(ep, real(s.w1), vld<real, V>(bufB + (s.base - 1) * V));
+            vfmas(eu, real(s.w1), vld<real, V>(bufB + (Nfp + s.base - 1) * V));
           }
-          if (a2 > 0) {
-            const int s = idx2(N - 1, a1, a2 - 1);
-            ep += real(a2) * bufB[s];
-            eu += real(a2) * bufB[Nfp + s];
+          if (s.w2 > 0) {
+            vfmas(ep, real(s.w2), vld<real, V>(bufB + (s.base - s.db) * V));
+            vfmas(eu, real(s.w2), vld<real, V>(bufB + (Nfp + s.base - s.db) * V));
           }
-          const real gp = (real(2 * N + 3) * fp[i] + ep) * third;
-          const real gu = (real(2 * N + 3) * fu[i] + eu) * third;
-          bufA[i] = gp;
-          bufA[Nfp + i] = gu;
-          const int vi = tab.lidx[f * Np + i];
-          R[vi] += gp;
-          R[Np + vi] += nx * gu;
-          R[2 * Np + vi] += ny * gu;
-          R[3 * Np + vi] += nz * gu;
+          const vt gp = vmuls(third, ep);
+          const vt gu = vmuls(third, eu);
+          vst(bufA + i * V, gp);
+          vst(bufA + (Nfp + i) * V, gu);
+          real* r = R + tab.lidx[f * Np + i] * V;
+          vst(r, vaxpy(vld<real, V>(r), real(1), gp));
+          vt ru = vld<real, V>(r + Np * V);
+          vfma(ru, nx, gu);
+          vst(r + Np * V, ru);
+          vt rv = vld<real, V>(r + 2 * Np * V);
+          vfma(rv, ny, gu);
+          vst(r + 2 * Np * V, rv);
+          vt rw = vld<real, V>(r + 3 * Np * V);
+          vfma(rw, nz, gu);
+          vst(r + 3 * Np * V, rw);
         }
         team_sync<T>();
         real* cur = bufA;
@@ -450,27 +638,34 @@ __global__ void __launch_bounds__(T* E) stage_kernel(const StageParams<real> P) 
         int off = Nfp;
 #pragma unroll 1
         for (int layer = 1; layer <= N; ++layer) {
-          const int n2 = N - layer;
-          const real inv = real(1) / real(n2 + 1);
-          const real ell = tab.ell[layer];
-          for (int i = t; active && i < np2(n2); i += T) {
-            int b0, b1, b2, unused;
-            unpack4(tab.dec2[off2(n2) + i], b0, b1, b2, unused);
-            const int i0 = idx2(n2 + 1, b1, b2), i1 = idx2(n2 + 1, b1 + 1, b2),
-                      i2 = idx2(n2 + 1, b1, b2 + 1);
-            const real gp =
-                (real(b0 + 1) * cur[i0] + real(b1 + 1) * cur[i1] + real(b2 + 1) * cur[i2]) * inv;
-            const real gu = (real(b0 + 1) * cur[Nfp + i0] + real(b1 + 1) * cur[Nfp + i1] +
-                             real(b2 + 1) * cur[Nfp + i2]) *
-                            inv;
-            nxt[i] = gp;
-            nxt[Nfp + i] = gu;
-            const int vi = tab.lidx[f * Np + off + i];
-            R[vi] += ell * gp;
-            const real eu = ell * gu;
-            R[Np + vi] += nx * eu;
-            R[2 * Np + vi] += ny * eu;
-            R[3 * Np + vi] += nz * eu;
+          const int n2 = N - layer;  // output degree; input degree n2 + 1
+          const real scale = real(1) / real(n2 + 1);
+          const real ell = tab.ell[layer] * scale;
+          const vt enx = vmuls(ell, nx), eny = vmuls(ell, ny), enz = vmuls(ell, nz);
+          for (int i = t; i < np2(n2); i += T) {
+            const Stencil2 s = unpack_stencil2(tab.red2[off2(n2) + i]);
+            const real w0 = real(n2 + 3 - s.w1 - s.w2), w1 = real(s.w1), w2 = real(s.w2);
+            vt gp = vmuls(w0, vld<real, V>(cur + s.base * V));
+            vfmas(gp, w1, vld<real, V>(cur + (s.base + 1) * V));
+            vfmas(gp, w2, vld<real, V>(cur + (s.base + s.db) * V));
+            vt gu = vmuls(w0, vld<real, V>(cur + (Nfp + s.base) * V));
+            vfmas(gu, w1, vld<real, V>(cur + (Nfp + s.base + 1) * V));
+            vfmas(gu, w2, vld<real, V>(cur + (Nfp + s.base + s.db) * V));
+            // gp, gu are (n2+1) times the reduced values: the next level
+            // stores them divided by n2+1, the scatter has 1/(n2+1) in ell
+            vst(nxt + i * V, vmuls(scale, gp));
+            vst(nxt + (Nfp + i) * V, vmuls(scale, gu));
+            real* r = R + tab.lidx[f * Np + off + i] * V;
+            vst(r, vaxpy(vld<real, V>(r), ell, gp));
+            vt ru = vld<real, V>(r + Np * V);
+            vfma(ru, enx, gu);
+            vst(r + Np * V, ru);
+            vt rv = vld<real, V>(r + 2 * Np * V);
+            vfma(rv, eny, gu);
+            vst(r + 2 * Np * V, rv);
+            vt rw = vld<real, V>(r + 3 * Np * V);
+            vfma(rw, enz, gu);
+            vst(r + 3 * Np * V, rw);
           }
           off += np2(n2);
           real* tmp = cur;
@@ -484,97 +679,112 @@ __global__ void __launch_bounds__(T* E) stage_kernel(const StageParams<real> P) 
     // ---- W: weight-adjusted update of the p right-hand side ----
     {
       real* A = S;
-      real* B = S + C::BUF;
-      const bool is_src = active && (e0 + e == P.src_elem);
-      for (int i = t; active && i < Np; i += T) {
-        real v = R[i];
-        if (is_src) v += P.src_amp * P.src_vec[i];
-        A[i] = v * tab.invfactN[i];
-      }
-      if (active && t == 0) A[Np] = real(0);
-      real bh[Mp > 0 ? Mp : 1];
+      real* B = S + C::BUF * V;
+      const int src_lane = (P.src_elem >= 0 && P.src_elem / V == g) ? int(P.src_elem % V) : -1;
+      for (int i = t; i < Np; i += T) {
+        vt v = vld<real, V>(R + i * V);
+        if (src_lane >= 0) {
 #pragma unroll
-      for (int b = 0; b < Mp; ++b) bh[b] = c2s[e * Mp + b] * tab.invfactM[b];
+          for (int l = 0; l < V; ++l)
+            if (l == src_lane) v.set(l, v.get(l) + P.src_amp * P.src_vec[i]);
+        }
+        vst(A + i * V, vmuls(tab.invfactN[i], v));
+      }
+      if (t == 0) vst(A + Np * V, vzero<real, V>());
+      vt bh[Mp];
+#pragma unroll
+      for (int b = 0; b < Mp; ++b) bh[b] = vmuls(tab.invfactM[b], vld<real, V>(C2S + b * V));
       team_sync<T>();
-      real lv[N + 1][C::RMAX];
-      wadg_element<N, M, real, T, C::RMAX>(tab, A, B, bh, active, t, lv);
+      vt lv[N + 1][C::RMAX];
+      wadg_group<N, M, real, T, V, C::RMAX>(tab, A, B, bh, true, t, lv);
 #pragma unroll
       for (int r = 0; r < C::RMAX; ++r) {
         const int i = t + r * T;
-        if (active && i < Np) R[i] = lv[0][r];
+        if (i < Np) vst(R + i * V, lv[0][r]);
       }
     }
-    __syncthreads();
+    team_sync<T>();
 
-    // ---- RK: res = a res + dt rhs; q_out = q_in + b res (coalesced over the tile) ----
-    const bool read_res = P.a != real(0);
+    // ---- RK: res = a res + dt rhs; q_out = q_in + b res ([4][Np] vectors, coalesced) ----
+    {
+      real* resg = P.res + size_t(g) * QV * V;
+      real* qog = P.qout + size_t(g) * QV * V;
+      vt rold[C::RK_IT];  // all of this lane's res loads in flight at once
 #pragma unroll
-    for (int fld = 0; fld < 4; ++fld) {
-      const size_t base = fld * fs + size_t(e0) * Np;
-      for (int idx = threadIdx.x; idx < nE * Np; idx += THREADS) {
-        const int ee = idx / Np;
-        const int i = idx - ee * Np;
-        const real rhs = el[ee * STRIDE + 4 * Np + fld * Np + i];
-        const real q = el[ee * STRIDE + fld * Np + i];
-        real r = P.dt * rhs;
-        if (read_res) r += P.a * P.res[base + idx];
-        P.res[base + idx] = r;
-        const real qn = q + P.b * r;
-        P.qout[base + idx] = qn;
-        bad |= !isfinite(qn);
+      for (int r = 0; r < C::RK_IT; ++r) {
+        const int idx = t + r * T;
+        rold[r] = (read_res && idx < QV) ? vld<real, V>(resg + size_t(idx) * V) : vzero<real, V>();
+      }
+#pragma unroll
+      for (int r = 0; r < C::RK_IT; ++r) {
+        const int idx = t + r * T;
+        if (idx < QV) {
+          vt rn = vmuls(P.dt, vld<real, V>(R + idx * V));
+          vfmas(rn, P.a, rold[r]);
+          vst(resg + size_t(idx) * V, rn);
+          const vt qn = vaxpy(vld<real, V>(Q + idx * V), P.b, rn);
+          vst(qog + size_t(idx) * V, qn);
+#pragma unroll
+          for (int v = 0; v < V; ++v) bad |= !isfinite(qn.get(v));
+        }
       }
     }
+    team_sync<T>();  // the next group reuses this team's shared region
   }
   if (bad) atomicOr(P.status, 1u);
 }
 
-// The weight-adjusted update alone: out = P^{N+M}_N (c2 * rhs) per element.
-template <int N, int M, typename real, int T, int E>
-__global__ void __launch_bounds__(T* E) wadg_kernel(const WadgParams<real> P) {
-  using C = StageCfg<N, M, real, T, E>;
+// The weight-adjusted update alone: out = P^{N+M}_N (c2 * rhs) per element,
+// on [K][Np] arrays (V consecutive elements form a group).
+template <int N, int M, typename real, int T, int V, int GC>
+__global__ void __launch_bounds__(T* GC) wadg_kernel(const WadgParams<real> P) {
+  using C = StageCfg<N, M, real, T, V, GC>;
   using Tab = typename C::Tab;
-  constexpr int Np = C::Np, Mp = C::Mp, STRIDE = C::STRIDE, THREADS = C::THREADS;
+  using vt = vec<real, V>;
+  constexpr int Np = C::Np, Mp = C::Mp;
   extern __shared__ __align__(16) unsigned char smem[];
   const Tab& tab = *reinterpret_cast<const Tab*>(smem);
-  real* el = reinterpret_cast<real*>(smem + C::TAB);
-  real* c2s = el + E * STRIDE;
-  load_tables<C::TAB, THREADS>(smem, P.tables);
+  load_tables<C::TAB, C::THREADS>(smem, P.tables);
+  __syncthreads();
   const int team = threadIdx.x / T;
   const int t = threadIdx.x % T;
-  const int64_t ntiles = (P.K + E - 1) / E;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t e0 = tile * E;
-    const int nE = int(P.K - e0 < E ? P.K - e0 : E);
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < nE * Np; idx += THREADS) {
-      const int e = idx / Np;
-      el[e * STRIDE + (idx - e * Np)] = P.rhs[size_t(e0) * Np + idx];
+  real* R = reinterpret_cast<real*>(smem + C::TAB) + team * C::TEAMV * V;  // [Np]
+  real* A = R + Np * V;
+  real* B = A + C::BUF * V;
+  real* C2S = B + C::BUF * V;  // [Mp]
+  const int64_t G = (P.K + V - 1) / V;
+  const int64_t stride = int64_t(gridDim.x) * GC;
+  for (int64_t g = int64_t(blockIdx.x) * GC + team; g < G; g += stride) {
+    const int64_t e0 = g * V;
+    // gather [K][Np] into vectors; lanes past the last element get 0 and c2 = 1
+    for (int idx = t; idx < V * Np; idx += T) {
+      const int v = idx / Np, i = idx - v * Np;
+      R[i * V + v] = e0 + v < P.K ? P.rhs[size_t(e0) * Np + idx] : real(0);
     }
-    for (int idx = threadIdx.x; idx < nE * Mp; idx += THREADS) c2s[idx] = P.c2[size_t(e0) * Mp + idx];
-    __syncthreads();
-    const bool active = team < nE;
-    const int e = active ? team : 0;
-    real* R = el + e * STRIDE;
-    real* A = R + Np;
-    real* B = A + C::BUF;
-    for (int i = t; active && i < Np; i += T) A[i] = R[i] * tab.invfactN[i];
-    if (active && t == 0) A[Np] = real(0);
-    real bh[Mp > 0 ? Mp : 1];
-#pragma unroll
-    for (int b = 0; b < Mp; ++b) bh[b] = c2s[e * Mp + b] * tab.invfactM[b];
+    for (int idx = t; idx < V * Mp; idx += T) {
+      const int v = idx / Mp, b = idx - v * Mp;
+      C2S[b * V + v] = e0 + v < P.K ? P.c2[size_t(e0) * Mp + idx] : real(1);
+    }
     team_sync<T>();
-    real lv[N + 1][C::RMAX];
-    wadg_element<N, M, real, T, C::RMAX>(tab, A, B, bh, active, t, lv);
+    for (int i = t; i < Np; i += T) vst(A + i * V, vmuls(tab.invfactN[i], vld<real, V>(R + i * V)));
+    if (t == 0) vst(A + Np * V, vzero<real, V>());
+    vt bh[Mp];
+#pragma unroll
+    for (int b = 0; b < Mp; ++b) bh[b] = vmuls(tab.invfactM[b], vld<real, V>(C2S + b * V));
+    team_sync<T>();
+    vt lv[N + 1][C::RMAX];
+    wadg_group<N, M, real, T, V, C::RMAX>(tab, A, B, bh, true, t, lv);
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r) {
       const int i = t + r * T;
-      if (active && i < Np) R[i] = lv[0][r];
+      if (i < Np) vst(R + i * V, lv[0][r]);
     }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < nE * Np; idx += THREADS) {
-      const int e2 = idx / Np;
-      P.out[size_t(e0) * Np + idx] = el[e2 * STRIDE + (idx - e2 * Np)];
+    team_sync<T>();
+    for (int idx = t; idx < V * Np; idx += T) {
+      const int v = idx / Np, i = idx - v * Np;
+      if (e0 + v < P.K) P.out[size_t(e0) * Np + idx] = R[i * V + v];
     }
+    team_sync<T>();
   }
 }
 

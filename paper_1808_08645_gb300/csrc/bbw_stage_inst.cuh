@@ -15,11 +15,21 @@ namespace bbw {
 namespace {
 
 constexpr int kN = BBW_N;
-constexpr int kT = TileShape<kN>::T;
-constexpr int kE = TileShape<kN>::E;
+
+template <typename real>
+using Shape = TileShape<kN, real>;
 
 template <int M, typename real>
-using Cfg = StageCfg<kN, M, real, kT, kE>;
+using Cfg = StageCfg<kN, M, real, Shape<real>::T, Shape<real>::V, Shape<real>::GC>;
+
+template <int M, typename real>
+constexpr auto stage_fn() {
+  return stage_kernel<kN, M, real, Shape<real>::T, Shape<real>::V, Shape<real>::GC>;
+}
+template <int M, typename real>
+constexpr auto wadg_fn() {
+  return wadg_kernel<kN, M, real, Shape<real>::T, Shape<real>::V, Shape<real>::GC>;
+}
 
 template <typename F>
 auto dispatch(int M, bool dbl, F&& f) {
@@ -55,8 +65,8 @@ void face_maps(int* fidx, int* nidx) {
 cudaError_t prepare(int M, bool dbl, int* per_sm_stage, int* per_sm_wadg) {
   return dispatch(M, dbl, [&]<int MM, typename real>() {
     using C = Cfg<MM, real>;
-    auto ks = stage_kernel<kN, MM, real, kT, kE>;
-    auto kw = wadg_kernel<kN, MM, real, kT, kE>;
+    auto ks = stage_fn<MM, real>();
+    auto kw = wadg_fn<MM, real>();
     cudaError_t err = cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute(kw, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
@@ -70,7 +80,7 @@ cudaError_t prepare(int M, bool dbl, int* per_sm_stage, int* per_sm_wadg) {
 cudaError_t launch_stage(int M, bool dbl, const void* params, int grid, cudaStream_t s) {
   return dispatch(M, dbl, [&]<int MM, typename real>() {
     using C = Cfg<MM, real>;
-    stage_kernel<kN, MM, real, kT, kE><<<grid, C::THREADS, C::SMEM, s>>>(
+    stage_fn<MM, real>()<<<grid, C::THREADS, C::SMEM, s>>>(
         *static_cast<const StageParams<real>*>(params));
     return cudaGetLastError();
   });
@@ -79,7 +89,7 @@ cudaError_t launch_stage(int M, bool dbl, const void* params, int grid, cudaStre
 cudaError_t launch_wadg(int M, bool dbl, const void* params, int grid, cudaStream_t s) {
   return dispatch(M, dbl, [&]<int MM, typename real>() {
     using C = Cfg<MM, real>;
-    wadg_kernel<kN, MM, real, kT, kE><<<grid, C::THREADS, C::SMEM, s>>>(
+    wadg_fn<MM, real>()<<<grid, C::THREADS, C::SMEM, s>>>(
         *static_cast<const WadgParams<real>*>(params));
     return cudaGetLastError();
   });
@@ -90,8 +100,15 @@ cudaError_t launch_wadg(int M, bool dbl, const void* params, int grid, cudaStrea
 #define BBW_CAT2(a, b) a##b
 #define BBW_CAT(a, b) BBW_CAT2(a, b)
 const KernelOps& BBW_CAT(ops_n, BBW_N)() {
-  static const KernelOps ops = {&tables_size, &build, &face_maps, &prepare,
-                                &launch_stage, &launch_wadg, kE, kT};
+  static const KernelOps ops = {&tables_size,
+                                &build,
+                                &face_maps,
+                                &prepare,
+                                &launch_stage,
+                                &launch_wadg,
+                                {Shape<float>::T, Shape<double>::T},
+                                {Shape<float>::V, Shape<double>::V},
+                                {Shape<float>::GC, Shape<double>::GC}};
   return ops;
 }
 
