@@ -325,7 +325,7 @@ def cpu_baseline(args):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     Ns = [int(x) for x in args.Ns.split(",")]
     code = (f"import sys, json; sys.path.insert(0, {ROOT!r}); import bench; "
-            f"d, s = bench._oracle_sample({args.cpu_hexes}, {Ns!r}, 1); print(json.dumps([d, s]))")
+            f"d, s = bench._oracle_sample({args.cpu_hexes}, {Ns!r}, {args.cpu_reps}); print(json.dumps([d, s]))")
     p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
                        timeout=1800)
     if p.returncode != 0:
@@ -334,7 +334,7 @@ def cpu_baseline(args):
     d, s = json.loads(p.stdout.strip().splitlines()[-1])
     K = 6 * args.cpu_hexes ** 3
     return {"value": d / s, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one FP64 oracle stage per degree N={Ns[0]}..{Ns[-1]} on the "
+            "sample": f"{args.cpu_reps} FP64 oracle stages per degree N={Ns[0]}..{Ns[-1]} on the "
                       f"{args.cpu_hexes}^3 x 6 = {K}-tet sub-cube of the same workload "
                       f"(same c2 field, source, pulse); {s:.1f} s of CPU work, 1 thread"}
 
@@ -379,6 +379,7 @@ def main():
     ap.add_argument("--hexes", type=int, default=inputs.SWEEP_CONFIG["hexes"])
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-hexes", type=int, default=5)
+    ap.add_argument("--cpu-reps", type=int, default=15)
     ap.add_argument("--ref-hexes", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -615,10 +615,10 @@ bbw_status bbw_create(int64_t nverts, const double* vxyz, int64_t K, const int64
     free_solver(s);
     return st;
   }
-  const int pi = precision == 64 ? 1 : 0;
-  s->V = s->ops->group_width[pi];
+  int team = 0, gpc = 1;
+  s->ops->launch_shape(M, precision == 64, &team, &s->V, &gpc);
   s->G = (K + s->V - 1) / s->V;
-  const int64_t tiles = (s->G + s->ops->groups_per_cta[pi] - 1) / s->ops->groups_per_cta[pi];
+  const int64_t tiles = (s->G + gpc - 1) / gpc;
   s->grid_stage = int(std::min<int64_t>(tiles, int64_t(std::max(1, s->op->per_sm_stage)) * num_sms()));
 
   const size_t rs = s->rsz();
@@ -939,8 +939,9 @@ bbw_status bbw_wadg_update(int N, int M, int precision, int64_t K, const void* r
   bbw_status st = get_tables(N, M, precision, &op);
   if (st != BBW_OK) return st;
   const bbw::KernelOps* ops = bbw::ops_for(N);
-  const int pi = precision == 64 ? 1 : 0;
-  const int64_t per_cta = int64_t(ops->group_width[pi]) * ops->groups_per_cta[pi];
+  int team = 0, width = 1, gpc = 1;
+  ops->launch_shape(M, precision == 64, &team, &width, &gpc);
+  const int64_t per_cta = int64_t(width) * gpc;
   const int64_t tiles = (K + per_cta - 1) / per_cta;
   const int grid = int(std::min<int64_t>(tiles, int64_t(std::max(1, op->per_sm_wadg)) * num_sms()));
   cudaStream_t s = static_cast<cudaStream_t>(stream);

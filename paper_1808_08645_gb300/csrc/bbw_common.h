@@ -65,6 +65,25 @@ BBW_HD constexpr uint32_t pack_stencil2(int base, int db, int w1, int w2) {
   return uint32_t(base) | (uint32_t(db) << 7) | (uint32_t(w1) << 11) | (uint32_t(w2) << 15);
 }
 
+// Nodes of the degree-N lattice with at least one coordinate equal to i:
+// these receive lift contributions at pyramid level i (face f contributes to
+// the nodes with alpha_f = i).
+constexpr int lift_level_nodes(int N, int i) {
+  int c = 0;
+  for (int l = 0; l <= N; ++l)
+    for (int k = 0; k <= N - l; ++k)
+      for (int j = 0; j <= N - l - k; ++j) {
+        const int a0 = N - j - k - l;
+        if (a0 == i || j == i || k == i || l == i) ++c;
+      }
+  return c;
+}
+constexpr int lift_level_off(int N, int i) {
+  int c = 0;
+  for (int x = 0; x < i; ++x) c += lift_level_nodes(N, x);
+  return c;
+}
+
 // Operator tables for one (N, M, real). Plain data, built on the host by
 // build_tables(), copied once to device memory and from there into each
 // CTA's shared memory.
@@ -87,7 +106,11 @@ struct Tables {
   uint16_t prod[NMp * Mp];      // index of gamma-beta in degree N, or Np if gamma !>= beta
   uint16_t fidx[4 * Nfp];       // own volume index of face node a of face f
   uint16_t nidx[24 * Nfp];      // neighbour volume index for (nface, perm, a)
-  uint16_t lidx[4 * Np];        // volume index of (face f, layer i, face coords b)
+  // lift scatter entries per pyramid level i = 0..N (offsets lift_level_off):
+  // x = node index | face mask << 9, y = face-local index of the node on each
+  // face in the mask (8 bits per face)
+  uint32_t lscat[2 * lift_level_off(N, N + 1)];
+  uint16_t lvl_off[N + 2];
 };
 
 template <int N, int M, typename real>
@@ -203,18 +226,27 @@ void build_tables(Tables<N, M, real>& t, const double* cj) {
         t.nidx[(f * 6 + p) * Tb::Nfp + a] = uint16_t(idx3(N, an[1], an[2], an[3]));
       }
     }
-    int off = 0;
-    for (int layer = 0; layer <= N; ++layer) {
-      const int n2 = N - layer;
-      for (int a = 0; a < np2(n2); ++a) {
-        int b[3];
-        mi2(n2, a, b);
-        int al[4] = {0, 0, 0, 0};
-        al[f] = layer;
-        for (int x = 0; x < 3; ++x) al[kFaceVerts[f][x]] = b[x];
-        t.lidx[f * Tb::Np + off + a] = uint16_t(idx3(N, al[1], al[2], al[3]));
+  }
+  // lift scatter entries, level by level
+  for (int lv = 0; lv <= N + 1; ++lv) t.lvl_off[lv] = uint16_t(lift_level_off(N, lv));
+  for (int lv = 0; lv <= N; ++lv) {
+    int c = 0;
+    for (int i = 0; i < Tb::Np; ++i) {
+      int a[4];
+      mi(N, i, a);
+      uint32_t mask = 0, locals = 0;
+      for (int f = 0; f < 4; ++f)
+        if (a[f] == lv) {
+          mask |= 1u << f;
+          int b[3];
+          for (int x = 0; x < 3; ++x) b[x] = a[kFaceVerts[f][x]];
+          locals |= uint32_t(idx2(N - lv, b[1], b[2])) << (8 * f);
+        }
+      if (mask) {
+        const int e = lift_level_off(N, lv) + c++;
+        t.lscat[2 * e] = uint32_t(i) | (mask << 9);
+        t.lscat[2 * e + 1] = locals;
       }
-      off += np2(n2);
     }
   }
 }

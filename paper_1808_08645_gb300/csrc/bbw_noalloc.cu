@@ -105,7 +105,9 @@ extern "C" bbw_status bbw_wadg_update_noalloc(int N, int M, int precision, int64
   err = cudaMemcpyAsync(g_scratch_ptr[dev], g_host_tables, bytes, cudaMemcpyHostToDevice, s);
   if (err != cudaSuccess) return fail(BBW_ERR_CUDA, "table upload", err);
 
-  const int64_t per_cta = int64_t(ops->group_width[dbl ? 1 : 0]) * ops->groups_per_cta[dbl ? 1 : 0];
+  int team = 0, width = 1, gpc = 1;
+  ops->launch_shape(M, dbl, &team, &width, &gpc);
+  const int64_t per_cta = int64_t(width) * gpc;
   const int64_t tiles = (K + per_cta - 1) / per_cta;
   const int grid = int(std::min<int64_t>(tiles, int64_t(per_sm) * g_num_sms[dev]));
   if (dbl) {

@@ -24,7 +24,7 @@ struct KernelOps {
   // launch the weight-adjusted update; params points to WadgParams<float|double>
   cudaError_t (*launch_wadg)(int M, bool dbl, const void* params, int grid, cudaStream_t s);
   // launch shape: lanes per group, elements per group, groups per CTA
-  int team[2], group_width[2], groups_per_cta[2];  // [0] float, [1] double
+  void (*launch_shape)(int M, bool dbl, int* team, int* group_width, int* groups_per_cta);
 };
 
 const KernelOps& ops_n1();

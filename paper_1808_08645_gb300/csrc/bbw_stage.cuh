@@ -72,21 +72,22 @@ struct WadgParams {
 };
 
 // Launch shape per degree and precision: T lanes per group, V elements per
-// group, GC groups per CTA.
+// group. The number of groups per CTA is derived in StageCfg: as many teams
+// as fit one CTA per SM (the operator tables are then held once per SM).
 template <int N, typename real>
 struct TileShape;
 template <int N>
 struct TileShape<N, float> {
-  static constexpr int T = N == 1 ? 4 : N == 2 ? 8 : N == 3 ? 16 : 32;
+  static constexpr int T = N == 1 ? 4 : N == 2 ? 8 : N == 3 ? 16 : N <= 7 ? 32 : 64;
   static constexpr int V = N <= 5 ? 4 : 2;
-  static constexpr int GC = N <= 2 ? 128 / T : N <= 4 ? 256 / T : N <= 6 ? 8 : 4;
 };
 template <int N>
 struct TileShape<N, double> {
   static constexpr int T = N == 1 ? 4 : N == 2 ? 8 : N == 3 ? 16 : 32;
   static constexpr int V = N <= 4 ? 2 : 1;
-  static constexpr int GC = N <= 4 ? 256 / T : N <= 6 ? 8 : 4;
 };
+
+constexpr int kSmemPerCta = 232448;  // 227 KB of dynamic shared memory per CTA (sm_100 family)
 
 // ---------------------------------------------------------------------------
 // V-wide vectors of real. Float vectors of even width are stored as float2
@@ -246,15 +247,36 @@ struct StageCfg {
   static constexpr int TEAMV = (8 * Np + S_SZ + 16 + Mp + CONNV) | 1;
   static constexpr int TAB = table_bytes<N, M, real>();
   static constexpr int SMEM = TAB + int(sizeof(real)) * V * GC * TEAMV;
+  static_assert(SMEM <= kSmemPerCta, "shared memory of the launch shape");
   static constexpr int RMAX = (Np + T - 1) / T;
   static constexpr int RK_IT = (4 * Np + T - 1) / T;  // RK vectors per lane
-  static_assert(T >= 4 && T <= 32 && 32 % T == 0, "team must divide a warp and cover the 4 faces");
+  static_assert(T >= 4 && (T <= 32 ? 32 % T == 0 : T % 32 == 0), "team: a divisor or a multiple of a warp");
+  static_assert(T <= 32 || GC <= 15, "one named barrier per multi-warp team");
   static_assert(V == 1 || V == 2 || V == 4, "group width");
 };
 
+// Barrier of one team: __syncwarp for teams within a warp, a named barrier
+// (ids 1..15, one per team of the CTA) for teams of several warps.
+// Teams per CTA. From N = 4 up: as many as fit the shared memory of one CTA
+// per SM and 512 threads (so that 128 registers per thread fit the register
+// file), which holds the operator tables once per SM. Below: 128-thread CTAs,
+// several per SM (the tables are small there).
+template <int N, int M, typename real, int T, int V>
+constexpr int fat_cta_groups() {
+  constexpr int team_bytes = int(sizeof(real)) * V * StageCfg<N, M, real, T, V, 1>::TEAMV;
+  constexpr int by_smem = (kSmemPerCta - table_bytes<N, M, real>()) / team_bytes;
+  constexpr int by_threads = (N <= 3 ? 128 : 512) / T;
+  constexpr int g = by_smem < by_threads ? by_smem : by_threads;
+  return T > 32 && g > 15 ? 15 : g;
+}
+
 template <int T>
 __device__ __forceinline__ void team_sync() {
-  if constexpr (T > 1) __syncwarp();
+  if constexpr (T > 32) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + int(threadIdx.x) / T), "r"(T) : "memory");
+  } else if constexpr (T > 1) {
+    __syncwarp();
+  }
 }
 
 struct Stencil3 {
@@ -299,10 +321,41 @@ __device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// One-degree reduction (E^{n}_{n-1})^T into degree n-1 (outputs i = t + r*T)
+// from X (degree n): every output of this lane is computed into out[] before
+// anything is stored, so the lane's loads are all in flight together.
+template <typename real, int V, int T, int R>
+__device__ __forceinline__ void reduce_lane(const uint32_t* __restrict__ words, int count, int n,
+                                            const real* X, int t, vec<real, V> (&out)[R]) {
+  const real inv = real(1) / real(n);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int i = t + r * T;
+    if (r * T < count && i < count) {
+      const Stencil3 s = unpack_stencil3(words[i]);
+      vec<real, V> v = vmuls(real(n + 3 - s.w1 - s.w2 - s.w3), vld<real, V>(X + s.base * V));
+      vfmas(v, real(s.w1), vld<real, V>(X + (s.base + 1) * V));
+      vfmas(v, real(s.w2), vld<real, V>(X + (s.base + s.dk) * V));
+      vfmas(v, real(s.w3), vld<real, V>(X + (s.base + s.dl) * V));
+      out[r] = vmuls(inv, v);
+    }
+  }
+}
+
+template <typename real, int V, int T, int R>
+__device__ __forceinline__ void store_lane(real* Y, int count, int t, const vec<real, V> (&v)[R]) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int i = t + r * T;
+    if (r * T < count && i < count) vst(Y + i * V, v[r]);
+  }
+}
+
 // Weight-adjusted update of one group (Sec. 5): out = P^{N+M}_N (c2 * r).
 // On entry A[0..Np) holds r * invfactN (A[Np] = 0) and bh the c2 coefficients
 // scaled by invfactM. The result for items i = t + r*T is left in lv[0][r].
-// A and B are vector buffers of BUF vectors each.
+// A and B are vector buffers of BUF vectors each. Each phase computes all of
+// a lane's outputs before storing them (loads in flight together).
 template <int N, int M, typename real, int T, int V, int RMAX>
 __device__ __forceinline__ void wadg_group(const Tables<N, M, real>& tab, real* A, real* B,
                                            const vec<real, V> (&bh)[np3(M)], bool active, int t,
@@ -311,13 +364,23 @@ __device__ __forceinline__ void wadg_group(const Tables<N, M, real>& tab, real* 
   constexpr int Np = np3(N);
   constexpr int Mp = np3(M);
   constexpr int NMp = np3(N + M);
+  constexpr int RP = (NMp + T - 1) / T;  // outputs per lane of the product and reductions
+  const int cnt = active ? 1 : 0;        // inactive teams produce nothing
   // product h_gamma = gamma!/C(N+M,N) sum_beta (b_beta/beta!) (a_{gamma-beta}/(gamma-beta)!)
-  for (int i = t; active && i < NMp; i += T) {
-    const uint16_t* pr = tab.prod + i * Mp;
-    vt h = vzero<real, V>();
+  {
+    vt h[RP];
 #pragma unroll
-    for (int b = 0; b < Mp; ++b) vfma(h, bh[b], vld<real, V>(A + pr[b] * V));
-    vst(B + i * V, vmuls(tab.factNM[i], h));
+    for (int r = 0; r < RP; ++r) {
+      const int i = t + r * T;
+      if (r * T < NMp && cnt && i < NMp) {
+        const uint16_t* pr = tab.prod + i * Mp;
+        vt acc = vzero<real, V>();
+#pragma unroll
+        for (int b = 0; b < Mp; ++b) vfma(acc, bh[b], vld<real, V>(A + pr[b] * V));
+        h[r] = vmuls(tab.factNM[i], acc);
+      }
+    }
+    store_lane<real, V, T, RP>(B, cnt * NMp, t, h);
   }
   team_sync<T>();
   // M one-degree reductions (E^{n}_{n-1})^T, n = N+M .. N+1 (right factors of Eq. 20)
@@ -326,15 +389,9 @@ __device__ __forceinline__ void wadg_group(const Tables<N, M, real>& tab, real* 
 #pragma unroll
   for (int r = 0; r < M; ++r) {
     const int n = N + M - r;
-    const real inv = real(1) / real(n);
-    for (int i = t; active && i < np3(n - 1); i += T) {
-      const Stencil3 s = unpack_stencil3(tab.red3[off3(n - 1) + i]);
-      vt v = vmuls(real(n + 3 - s.w1 - s.w2 - s.w3), vld<real, V>(X + s.base * V));
-      vfmas(v, real(s.w1), vld<real, V>(X + (s.base + 1) * V));
-      vfmas(v, real(s.w2), vld<real, V>(X + (s.base + s.dk) * V));
-      vfmas(v, real(s.w3), vld<real, V>(X + (s.base + s.dl) * V));
-      vst(Y + i * V, vmuls(inv, v));
-    }
+    vt out[RP];
+    reduce_lane<real, V, T, RP>(tab.red3 + off3(n - 1), cnt * np3(n - 1), n, X, t, out);
+    store_lane<real, V, T, RP>(Y, cnt * np3(n - 1), t, out);
     real* tmp = X;
     X = Y;
     Y = tmp;
@@ -350,21 +407,8 @@ __device__ __forceinline__ void wadg_group(const Tables<N, M, real>& tab, real* 
 #pragma unroll
   for (int jl = 1; jl <= N; ++jl) {
     const int n = N - jl + 1;
-    const real inv = real(1) / real(n);
-#pragma unroll
-    for (int r = 0; r < RMAX; ++r) {
-      const int i = t + r * T;
-      if (r * T < np3(n - 1) && active && i < np3(n - 1)) {
-        const Stencil3 s = unpack_stencil3(tab.red3[off3(n - 1) + i]);
-        vt v = vmuls(real(n + 3 - s.w1 - s.w2 - s.w3), vld<real, V>(X + s.base * V));
-        vfmas(v, real(s.w1), vld<real, V>(X + (s.base + 1) * V));
-        vfmas(v, real(s.w2), vld<real, V>(X + (s.base + s.dk) * V));
-        vfmas(v, real(s.w3), vld<real, V>(X + (s.base + s.dl) * V));
-        v = vmuls(inv, v);
-        lv[jl][r] = v;
-        vst(Y + i * V, v);
-      }
-    }
+    reduce_lane<real, V, T, RMAX>(tab.red3 + off3(n - 1), cnt * np3(n - 1), n, X, t, lv[jl]);
+    store_lane<real, V, T, RMAX>(Y, cnt * np3(n - 1), t, lv[jl]);
     real* tmp = X;
     X = Y;
     Y = tmp;
@@ -378,6 +422,7 @@ __device__ __forceinline__ void wadg_group(const Tables<N, M, real>& tab, real* 
     const int n = N - jl;
     const real inv = real(1) / real(n);
     const real c = tab.cj[jl];
+    vt w[RMAX];
 #pragma unroll
     for (int r = 0; r < RMAX; ++r) {
       const int i = t + r * T;
@@ -389,13 +434,16 @@ __device__ __forceinline__ void wadg_group(const Tables<N, M, real>& tab, real* 
         if (s.w1 > 0) vfmas(acc, real(s.w1), vld<real, V>(X + (s.base - 1) * V));
         if (s.w2 > 0) vfmas(acc, real(s.w2), vld<real, V>(X + (s.base - s.dk) * V));
         if (s.w3 > 0) vfmas(acc, real(s.w3), vld<real, V>(X + (s.base - s.dl) * V));
-        vt w = vmuls(c, lv[jl][r]);
-        vfmas(w, inv, acc);
-        if (jl > 0)
-          vst(Y + i * V, w);
-        else
-          lv[0][r] = w;
+        w[r] = vmuls(c, lv[jl][r]);
+        vfmas(w[r], inv, acc);
       }
+    }
+    if (jl > 0) {
+      store_lane<real, V, T, RMAX>(Y, cnt * np3(n), t, w);
+    } else {
+#pragma unroll
+      for (int r = 0; r < RMAX; ++r)
+        if (r * T < np3(n) && t + r * T < np3(n)) lv[0][r] = w[r];
     }
     real* tmp = X;
     X = Y;
@@ -573,107 +621,111 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
     }
     team_sync<T>();
 
-    // ---- L: lift L^f = E_L L0 per face, accumulated into rhs ----
+    // ---- L: lift L^f = E_L L0 of the four faces, level by level ----
+    // Pyramid level i of face f is ell_i (E^{N}_{N-i})^T L0 F_f restricted to
+    // the nodes with alpha_f = i. Levels of all four faces are built together
+    // in [p, u][face][Nfp] buffers (level 0 over the fluxes, in place); the
+    // nodes touched at level i are then updated once each from every face in
+    // their mask (a per-level node table), so no two lanes update one node.
     {
-      real* bufA = NB + 8 * Nfp * V;  // [p, u][Nfp], over the traces of fields 2, 3
-      real* bufB = bufA + 2 * Nfp * V;
-      const real third = real(1) / real(3);
-#pragma unroll 1
-      for (int f = 0; f < 4; ++f) {
-        const real* Fp = NB + f * Nfp * V;
-        const real* Fu = NB + (4 * Nfp + f * Nfp) * V;
-        const real* nr = NRM + 4 * f * V;
-        const vt nx = vld<real, V>(nr), ny = vld<real, V>(nr + V), nz = vld<real, V>(nr + 2 * V);
-        // t = E'^T F at degree N-1 (integer weights b_x + 1)
-        for (int i = t; i < np2(N - 1); i += T) {
-          const Stencil2 s = unpack_stencil2(tab.red2[off2(N - 1) + i]);
-          const real w0 = real(N + 2 - s.w1 - s.w2), w1 = real(s.w1), w2 = real(s.w2);
-          vt tp = vmuls(w0, vld<real, V>(Fp + s.base * V));
-          vfmas(tp, w1, vld<real, V>(Fp + (s.base + 1) * V));
-          vfmas(tp, w2, vld<real, V>(Fp + (s.base + s.db) * V));
-          vt tu = vmuls(w0, vld<real, V>(Fu + s.base * V));
-          vfmas(tu, w1, vld<real, V>(Fu + (s.base + 1) * V));
-          vfmas(tu, w2, vld<real, V>(Fu + (s.base + s.db) * V));
-          vst(bufB + i * V, tp);
-          vst(bufB + (Nfp + i) * V, tu);
-        }
-        team_sync<T>();
-        // g0 = L0 F = ((2N+3) F + E' t) / 3; layer 0 (ell_0 = 1)
-        for (int i = t; i < Nfp; i += T) {
-          const Stencil2 s = unpack_stencil2(tab.elev2[i]);
-          const int a0 = N - s.w1 - s.w2;
-          vt ep = vmuls(real(2 * N + 3), vld<real, V>(Fp + i * V));
-          vt eu = vmuls(real(2 * N + 3), vld<real, V>(Fu + i * V));
-          if (a0 > 0) {
-            vfmas(ep, real(a0), vld<real, V>(bufB + s.base * V));
-            vfmas(eu, real(a0), vld<real, V>(bufB + (Nfp + s.base) * V));
-          }
-          if (s.w1 > 0) {
-            vfmas(ep, real(s.w1), vld<real, V>(bufB + (s.base - 1) * V));
-            vfmas(eu, real(s.w1), vld<real, V>(bufB + (Nfp + s.base - 1) * V));
-          }
-          if (s.w2 > 0) {
-            vfmas(ep, real(s.w2), vld<real, V>(bufB + (s.base - s.db) * V));
-            vfmas(eu, real(s.w2), vld<real, V>(bufB + (Nfp + s.base - s.db) * V));
-          }
-          const vt gp = vmuls(third, ep);
-          const vt gu = vmuls(third, eu);
-          vst(bufA + i * V, gp);
-          vst(bufA + (Nfp + i) * V, gu);
-          real* r = R + tab.lidx[f * Np + i] * V;
-          vst(r, vaxpy(vld<real, V>(r), real(1), gp));
-          vt ru = vld<real, V>(r + Np * V);
-          vfma(ru, nx, gu);
-          vst(r + Np * V, ru);
-          vt rv = vld<real, V>(r + 2 * Np * V);
-          vfma(rv, ny, gu);
-          vst(r + 2 * Np * V, rv);
-          vt rw = vld<real, V>(r + 3 * Np * V);
-          vfma(rw, nz, gu);
-          vst(r + 3 * Np * V, rw);
-        }
-        team_sync<T>();
-        real* cur = bufA;
-        real* nxt = bufB;
-        int off = Nfp;
-#pragma unroll 1
-        for (int layer = 1; layer <= N; ++layer) {
-          const int n2 = N - layer;  // output degree; input degree n2 + 1
-          const real scale = real(1) / real(n2 + 1);
-          const real ell = tab.ell[layer] * scale;
-          const vt enx = vmuls(ell, nx), eny = vmuls(ell, ny), enz = vmuls(ell, nz);
-          for (int i = t; i < np2(n2); i += T) {
-            const Stencil2 s = unpack_stencil2(tab.red2[off2(n2) + i]);
-            const real w0 = real(n2 + 3 - s.w1 - s.w2), w1 = real(s.w1), w2 = real(s.w2);
-            vt gp = vmuls(w0, vld<real, V>(cur + s.base * V));
-            vfmas(gp, w1, vld<real, V>(cur + (s.base + 1) * V));
-            vfmas(gp, w2, vld<real, V>(cur + (s.base + s.db) * V));
-            vt gu = vmuls(w0, vld<real, V>(cur + (Nfp + s.base) * V));
-            vfmas(gu, w1, vld<real, V>(cur + (Nfp + s.base + 1) * V));
-            vfmas(gu, w2, vld<real, V>(cur + (Nfp + s.base + s.db) * V));
-            // gp, gu are (n2+1) times the reduced values: the next level
-            // stores them divided by n2+1, the scatter has 1/(n2+1) in ell
-            vst(nxt + i * V, vmuls(scale, gp));
-            vst(nxt + (Nfp + i) * V, vmuls(scale, gu));
-            real* r = R + tab.lidx[f * Np + off + i] * V;
-            vst(r, vaxpy(vld<real, V>(r), ell, gp));
-            vt ru = vld<real, V>(r + Np * V);
-            vfma(ru, enx, gu);
-            vst(r + Np * V, ru);
-            vt rv = vld<real, V>(r + 2 * Np * V);
-            vfma(rv, eny, gu);
-            vst(r + 2 * Np * V, rv);
-            vt rw = vld<real, V>(r + 3 * Np * V);
-            vfma(rw, enz, gu);
-            vst(r + 3 * Np * V, rw);
-          }
-          off += np2(n2);
-          real* tmp = cur;
-          cur = nxt;
-          nxt = tmp;
-          team_sync<T>();
+      real* bufA = NB;                 // fluxes, then even levels
+      real* bufB = NB + 8 * Nfp * V;   // t = E'^T F, then odd levels
+      auto LV = [&](real* buf, int k, int f, int a) { return buf + ((k * 4 + f) * Nfp + a) * V; };
+      vt nrm[4][3];
+#pragma unroll
+      for (int f = 0; f < 4; ++f)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) nrm[f][d] = vld<real, V>(NRM + (4 * f + d) * V);
+      // t = E'^T F at degree N-1 (integer weights b_x + 1), all faces
+      constexpr int CT = np2(N - 1);
+      for (int it = t; it < 4 * CT; it += T) {
+        const int f = it / CT;
+        const int i = it - f * CT;
+        const Stencil2 s = unpack_stencil2(tab.red2[off2(N - 1) + i]);
+        const real w0 = real(N + 2 - s.w1 - s.w2), w1 = real(s.w1), w2 = real(s.w2);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          vt x = vmuls(w0, vld<real, V>(LV(bufA, k, f, s.base)));
+          vfmas(x, w1, vld<real, V>(LV(bufA, k, f, s.base + 1)));
+          vfmas(x, w2, vld<real, V>(LV(bufA, k, f, s.base + s.db)));
+          vst(LV(bufB, k, f, i), x);
         }
       }
+      team_sync<T>();
+      // level 0: L0 F = ((2N+3) F + E' t) / 3, in place over F
+      const real third = real(1) / real(3);
+      for (int it = t; it < 4 * Nfp; it += T) {
+        const int f = it / Nfp;
+        const int i = it - f * Nfp;
+        const Stencil2 s = unpack_stencil2(tab.elev2[i]);
+        const int a0 = N - s.w1 - s.w2;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          vt x = vmuls(real(2 * N + 3), vld<real, V>(LV(bufA, k, f, i)));
+          if (a0 > 0) vfmas(x, real(a0), vld<real, V>(LV(bufB, k, f, s.base)));
+          if (s.w1 > 0) vfmas(x, real(s.w1), vld<real, V>(LV(bufB, k, f, s.base - 1)));
+          if (s.w2 > 0) vfmas(x, real(s.w2), vld<real, V>(LV(bufB, k, f, s.base - s.db)));
+          vst(LV(bufA, k, f, i), vmuls(third, x));
+        }
+      }
+      team_sync<T>();
+      // scatter of level lv from the pyramid buffer P into rhs
+      auto scatter = [&](int lv, const real* P) {
+        const int e0 = tab.lvl_off[lv], cnt = tab.lvl_off[lv + 1] - e0;
+        const real ell = tab.ell[lv];
+        for (int e = t; e < cnt; e += T) {
+          const uint32_t x = tab.lscat[2 * (e0 + e)];
+          const uint32_t y = tab.lscat[2 * (e0 + e) + 1];
+          const int node = int(x & 511u);
+          vt ap = vzero<real, V>(), ax = vzero<real, V>(), ay = vzero<real, V>(), az = vzero<real, V>();
+#pragma unroll
+          for (int f = 0; f < 4; ++f)
+            if ((x >> (9 + f)) & 1u) {
+              const int a = int((y >> (8 * f)) & 255u);
+              const vt gp = vld<real, V>(P + (f * Nfp + a) * V);
+              const vt gu = vld<real, V>(P + ((4 + f) * Nfp + a) * V);
+              ap = vaxpy(ap, real(1), gp);
+              vfma(ax, nrm[f][0], gu);
+              vfma(ay, nrm[f][1], gu);
+              vfma(az, nrm[f][2], gu);
+            }
+          real* r = R + node * V;
+          vst(r, vaxpy(vld<real, V>(r), ell, ap));
+          vst(r + Np * V, vaxpy(vld<real, V>(r + Np * V), ell, ax));
+          vst(r + 2 * Np * V, vaxpy(vld<real, V>(r + 2 * Np * V), ell, ay));
+          vst(r + 3 * Np * V, vaxpy(vld<real, V>(r + 3 * Np * V), ell, az));
+        }
+      };
+      real* cur = bufA;
+      real* nxt = bufB;
+#pragma unroll 1
+      for (int lv = 1; lv <= N; ++lv) {
+        scatter(lv - 1, cur);  // reads cur, updates rhs; the pyramid below writes nxt only
+        const int n2 = N - lv;  // output degree; input degree n2 + 1
+        const int cnt = np2(n2);
+        const real icnt = real(1) / real(cnt);
+        const real scale = real(1) / real(n2 + 1);
+        for (int it = t; it < 4 * cnt; it += T) {
+          const int f = int((real(it) + real(0.5)) * icnt);
+          const int i = it - f * cnt;
+          const Stencil2 s = unpack_stencil2(tab.red2[off2(n2) + i]);
+          const real w0 = real(n2 + 3 - s.w1 - s.w2) * scale, w1 = real(s.w1) * scale,
+                     w2 = real(s.w2) * scale;
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            vt x = vmuls(w0, vld<real, V>(LV(cur, k, f, s.base)));
+            vfmas(x, w1, vld<real, V>(LV(cur, k, f, s.base + 1)));
+            vfmas(x, w2, vld<real, V>(LV(cur, k, f, s.base + s.db)));
+            vst(LV(nxt, k, f, i), x);
+          }
+        }
+        team_sync<T>();
+        real* tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+      }
+      scatter(N, cur);
+      team_sync<T>();
     }
 
     // ---- W: weight-adjusted update of the p right-hand side ----

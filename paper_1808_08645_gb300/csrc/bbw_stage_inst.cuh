@@ -20,16 +20,20 @@ template <typename real>
 using Shape = TileShape<kN, real>;
 
 template <int M, typename real>
-using Cfg = StageCfg<kN, M, real, Shape<real>::T, Shape<real>::V, Shape<real>::GC>;
+constexpr int kGC = fat_cta_groups<kN, M, real, Shape<real>::T, Shape<real>::V>();
+
+template <int M, typename real>
+using Cfg = StageCfg<kN, M, real, Shape<real>::T, Shape<real>::V, kGC<M, real>>;
 
 template <int M, typename real>
 constexpr auto stage_fn() {
-  return stage_kernel<kN, M, real, Shape<real>::T, Shape<real>::V, Shape<real>::GC>;
+  return stage_kernel<kN, M, real, Shape<real>::T, Shape<real>::V, kGC<M, real>>;
 }
 template <int M, typename real>
 constexpr auto wadg_fn() {
-  return wadg_kernel<kN, M, real, Shape<real>::T, Shape<real>::V, Shape<real>::GC>;
+  return wadg_kernel<kN, M, real, Shape<real>::T, Shape<real>::V, kGC<M, real>>;
 }
+
 
 template <typename F>
 auto dispatch(int M, bool dbl, F&& f) {
@@ -39,6 +43,15 @@ auto dispatch(int M, bool dbl, F&& f) {
     case 2: return dbl ? f.template operator()<2, double>() : f.template operator()<2, float>();
     default: return dbl ? f.template operator()<3, double>() : f.template operator()<3, float>();
   }
+}
+
+void launch_shape(int M, bool dbl, int* team, int* width, int* groups) {
+  dispatch(M, dbl, [&]<int MM, typename real>() {
+    *team = Shape<real>::T;
+    *width = Shape<real>::V;
+    *groups = kGC<MM, real>;
+    return 0;
+  });
 }
 
 size_t tables_size(int M, bool dbl) {
@@ -100,15 +113,8 @@ cudaError_t launch_wadg(int M, bool dbl, const void* params, int grid, cudaStrea
 #define BBW_CAT2(a, b) a##b
 #define BBW_CAT(a, b) BBW_CAT2(a, b)
 const KernelOps& BBW_CAT(ops_n, BBW_N)() {
-  static const KernelOps ops = {&tables_size,
-                                &build,
-                                &face_maps,
-                                &prepare,
-                                &launch_stage,
-                                &launch_wadg,
-                                {Shape<float>::T, Shape<double>::T},
-                                {Shape<float>::V, Shape<double>::V},
-                                {Shape<float>::GC, Shape<double>::GC}};
+  static const KernelOps ops = {&tables_size, &build,        &face_maps,   &prepare,
+                                &launch_stage, &launch_wadg, &launch_shape};
   return ops;
 }
 
