@@ -197,14 +197,7 @@ def run_gpu(args):
                          "us_per_stage": t_stage * 1e6,
                          "achieved_gbs": algorithmic_bytes_per_element(N, M) * K / t_stage / 1e9}
     dofs_total = sum(5 * dof_stage[N] for N in Ns) * args.steps
-    value_local = dofs_total / (total_ms / 1e3)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        value = dofs_total * world / (total_ms / 1e3)
-    else:
-        value = value_local
+    total_ms, value = aggregate_ranks(total_ms, dofs_total, dist, device="cuda")
 
     # dominant kernel: the largest share of kernel time
     top = max(Ns, key=lambda N: statistics.median(kern_ms[N]))
@@ -256,6 +249,23 @@ def run_gpu(args):
     if dist is not None:
         dist.destroy_process_group()
     return out
+
+
+def aggregate_ranks(local_ms: float, local_units: float, dist=None, device="cpu"):
+    """Whole-job throughput of independent replicas: every rank processed
+    ``local_units`` in ``local_ms``; the job time is the maximum over ranks
+    and the value is the units of all ranks over that time. Returns
+    (job_ms, value). ``dist`` is torch.distributed (or None for one rank)."""
+    if dist is not None:
+        import torch
+        t = torch.tensor([float(local_ms), float(local_units)], dtype=torch.float64, device=device)
+        u = t[1:].clone()
+        dist.all_reduce(t[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        local_ms, units = float(t[0].item()), float(u[0].item())
+    else:
+        units = float(local_units)
+    return local_ms, units / (local_ms / 1e3)
 
 
 def run_e2e(solvers, host_q0, Ns, dts, K, steps, stream):
