@@ -103,7 +103,10 @@ struct Tables {
   uint32_t elev3[off3(N + 1)];  // elevation words, outputs of degree n = 0..N
   uint32_t red2[off2(N)];       // 2D reduction words, outputs of degree 0..N-1
   uint32_t elev2[np2(N)];       // 2D elevation words, outputs of degree N
-  uint16_t prod[NMp * Mp];      // index of gamma-beta in degree N, or Np if gamma !>= beta
+  static constexpr int MP2 = (Mp + 1) / 2;
+  // product gather: word [p][gamma] holds the degree-N indices of gamma-beta
+  // for beta = 2p (low 16 bits) and 2p+1 (high), Np where gamma !>= beta
+  uint32_t prod2[MP2 * NMp];
   uint16_t fidx[4 * Nfp];       // own volume index of face node a of face f
   uint16_t nidx[24 * Nfp];      // neighbour volume index for (nface, perm, a)
   // lift scatter entries per pyramid level i = 0..N (offsets lift_level_off):
@@ -201,8 +204,11 @@ void build_tables(Tables<N, M, real>& t, const double* cj) {
       mi(M, b, be);
       bool ok = true;
       for (int x = 0; x < 4; ++x) ok = ok && g[x] >= be[x];
-      t.prod[i * Tb::Mp + b] = uint16_t(ok ? idx3(N, g[1] - be[1], g[2] - be[2], g[3] - be[3]) : Tb::Np);
+      const uint32_t src = uint32_t(ok ? idx3(N, g[1] - be[1], g[2] - be[2], g[3] - be[3]) : Tb::Np);
+      uint32_t& w = t.prod2[(b / 2) * Tb::NMp + i];
+      w = (b & 1) ? (w & 0xffffu) | (src << 16) : src;
     }
+    if (Tb::Mp & 1) t.prod2[(Tb::Mp / 2) * Tb::NMp + i] |= uint32_t(Tb::Np) << 16;
   }
   for (int b = 0; b < Tb::Mp; ++b) {
     int be[4];

@@ -373,10 +373,13 @@ __device__ __forceinline__ void wadg_group(const Tables<N, M, real>& tab, real* 
     for (int r = 0; r < RP; ++r) {
       const int i = t + r * T;
       if (r * T < NMp && cnt && i < NMp) {
-        const uint16_t* pr = tab.prod + i * Mp;
         vt acc = vzero<real, V>();
 #pragma unroll
-        for (int b = 0; b < Mp; ++b) vfma(acc, bh[b], vld<real, V>(A + pr[b] * V));
+        for (int p = 0; p < (Mp + 1) / 2; ++p) {
+          const uint32_t w = tab.prod2[p * NMp + i];
+          vfma(acc, bh[2 * p], vld<real, V>(A + (w & 0xffffu) * V));
+          if (2 * p + 1 < Mp) vfma(acc, bh[2 * p + 1], vld<real, V>(A + (w >> 16) * V));
+        }
         h[r] = vmuls(tab.factNM[i], acc);
       }
     }
@@ -594,6 +597,11 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
       }
     }
     cp_async_wait_all();
+    vt nf[4][4];  // per face: nx, ny, nz, (1/2)|f|/|D|
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) nf[f][c] = vld<real, V>(NRM + (4 * f + c) * V);
     for (int it = t; it < 4 * Nfp; it += T) {
       const int f = it / Nfp;
       const int io = tab.fidx[it];
@@ -609,9 +617,15 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
           vp.set(v, vm.get(v));
           wp.set(v, wm.get(v));
         }
-      const real* nr = NRM + 4 * f * V;
-      const vt nx = vld<real, V>(nr), ny = vld<real, V>(nr + V), nz = vld<real, V>(nr + 2 * V),
-               hs = vld<real, V>(nr + 3 * V);
+      vt nx = nf[0][0], ny = nf[0][1], nz = nf[0][2], hs = nf[0][3];
+#pragma unroll
+      for (int ff = 1; ff < 4; ++ff)
+        if (f == ff) {
+          nx = nf[ff][0];
+          ny = nf[ff][1];
+          nz = nf[ff][2];
+          hs = nf[ff][3];
+        }
       const vt jp = vsub(pp, pm);
       vt ndu = vmul(nx, vsub(up, um));
       vfma(ndu, ny, vsub(vp, vm));
