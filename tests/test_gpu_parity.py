@@ -259,3 +259,108 @@ def test_full_size_sweep_mesh_sampled(N):
         got.append(rg[:, e])
         want.append(ro)
     assert rel_l2(np.array(got), np.array(want)) <= TOL_STAGE[prec]
+
+
+# -- edge cases of the grouped layout -----------------------------------------------
+
+@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("N", [1, 4, 7, 9])
+def test_stage_parity_element_counts_not_multiple_of_group(N, prec):
+    """K = 1 and K = 5: the last group of V elements is padded."""
+    M = 2
+    vxyz, etov, c2, q, res = random_case(1, N, M, prec, seed=30 + N)
+    for K in (1, 5):
+        sub = etov[:K]
+        verts, inv = np.unique(sub, return_inverse=True)
+        ev = inv.reshape(sub.shape)
+        vx = vxyz[verts]
+        orc = AcousticOracle(vx, ev, N, M, c2[:K])
+        solver = _solver(vx, ev, N, M, prec, c2[:K], q[:, :K], res[:, :K])
+        solver.stage(1, 1e-3)
+        qg, rg, _ = solver.get_state(with_res=True)
+        qo, ro = orc.stage(q[:, :K], res[:, :K], 1, 1e-3, 0.0)
+        assert rel_l2(rg, ro) <= TOL_STAGE[prec], (K, rel_l2(rg, ro))
+        assert rel_l2(qg, qo) <= TOL_STAGE[prec]
+        solver.close()
+
+
+@pytest.mark.parametrize("N,M", [(9, 3), (9, 0), (8, 3), (2, 0)])
+def test_stage_parity_extreme_shapes_fp64(N, M):
+    vxyz, etov, c2, q, res = random_case(1, N, M, 64, seed=40 + N + M)
+    orc = AcousticOracle(vxyz, etov, N, M, c2)
+    solver = _solver(vxyz, etov, N, M, 64, c2, q, res)
+    solver.stage(3, 5e-4)
+    _, rg, _ = solver.get_state(with_res=True)
+    _, ro = orc.stage(q, res, 3, 5e-4, 0.0)
+    assert rel_l2(rg, ro) <= TOL_STAGE[64]
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_host_state_roundtrip_through_grouped_layout(prec):
+    for N, K in ((1, 7), (6, 9), (9, 3)):
+        vxyz, etov, c2, q, res = random_case(2, N, 1, prec, seed=N)
+        sub = etov[:K]
+        verts, inv = np.unique(sub, return_inverse=True)
+        s = _solver(vxyz[verts], inv.reshape(sub.shape), N, 1, prec, c2[:K], q[:, :K], res[:, :K], t=0.25)
+        qg, rg, t = s.get_state(with_res=True)
+        assert np.array_equal(qg, q[:, :K]) and np.array_equal(rg, res[:, :K]) and t == 0.25
+        s.close()
+
+
+def test_solver_face_node_map_matches_mesh_analysis():
+    vxyz, etov, c2, q, res = random_case(2, 5, 2, 32, seed=12)
+    s = _solver(vxyz, etov, 5, 2, 32, c2, q, res)
+    ref = B.mesh_analyze(vxyz, etov, 5)
+    assert np.array_equal(s.face_node_map(), ref["nmap"])
+    etoe, etof, fperm = s.connectivity()
+    assert np.array_equal(etoe, ref["etoe"]) and np.array_equal(fperm, ref["fperm"])
+
+
+def test_wadg_update_single_element():
+    rng = np.random.default_rng(3)
+    for N, M in ((1, 2), (9, 2)):
+        Np, Mp = bb.np_count(N), bb.np_count(M)
+        r = rounded(rng.standard_normal((1, Np)), 32)
+        c2 = rounded(rng.uniform(0.5, 2, (1, Mp)), 32)
+        want = np.linalg.solve(bb.mass(N), np.einsum("kb,bij,kj->ki", c2, bb.weighted_mass_terms(N, M), r).T).T
+        dr = torch.tensor(r, dtype=torch.float32, device="cuda")
+        dc = torch.tensor(c2, dtype=torch.float32, device="cuda")
+        out = torch.full_like(dr, float("nan"))
+        B.wadg_update(N, M, 32, 1, dr, dc, out)
+        torch.cuda.synchronize()
+        assert rel_l2(out.double().cpu().numpy(), want) <= TOL_STAGE[32]
+
+
+# -- the GPU solver against the closed-form solution ------------------------------
+
+def test_gpu_standing_wave_converges():
+    """c2 = 1, p = 0 walls: p = sin(pi x) sin(pi y) sin(pi z) cos(sqrt(3) pi t);
+    the GPU solution converges at a rate near N + 1 = 4 (N = 3, FP64)."""
+    from oracle.quadrature import tet_rule
+    N, T = 3, 0.1
+    errs = []
+    for hexes in (2, 4):
+        vxyz, etov = inputs.cube_mesh(hexes)
+        K = len(etov)
+        lam, w = tet_rule(2 * N + 4)
+        X = np.asarray(vxyz)[etov]
+        xq = np.einsum("qa,kai->kqi", lam, X)
+        Vq = bb.evaluate(np.eye(bb.np_count(N)), N, lam)
+        Pq = np.linalg.solve(bb.mass(N), Vq * w)
+        s3 = np.sin(np.pi * xq)
+        c3 = np.cos(np.pi * xq)
+        q0 = np.zeros((4, K, bb.np_count(N)))
+        q0[0] = np.einsum("aq,kq->ka", Pq, s3[..., 0] * s3[..., 1] * s3[..., 2])
+        s = _solver(vxyz, etov, N, 0, 64, np.ones((K, 1)), q0, None)
+        s.advance(T, 0.25)
+        q, _ = s.get_state()
+        w3 = np.sqrt(3) * np.pi
+        pex = s3[..., 0] * s3[..., 1] * s3[..., 2] * np.cos(w3 * T)
+        uex = -np.pi * np.stack([c3[..., 0] * s3[..., 1] * s3[..., 2], s3[..., 0] * c3[..., 1] * s3[..., 2],
+                                 s3[..., 0] * s3[..., 1] * c3[..., 2]]) * np.sin(w3 * T) / w3
+        ph = np.einsum("aq,ka->kq", Vq, q[0])
+        uh = np.einsum("aq,ika->ikq", Vq, q[1:4])
+        vol = B.mesh_analyze(vxyz, etov, N)["vol"][:, None]
+        errs.append(np.sqrt(np.sum(vol * w * ((ph - pex) ** 2 + np.sum((uh - uex) ** 2, axis=0)))))
+        s.close()
+    assert errs[1] < 1e-3 and np.log2(errs[0] / errs[1]) > 3.3
