@@ -65,24 +65,10 @@ BBW_HD constexpr uint32_t pack_stencil2(int base, int db, int w1, int w2) {
   return uint32_t(base) | (uint32_t(db) << 7) | (uint32_t(w1) << 11) | (uint32_t(w2) << 15);
 }
 
-// Nodes of the degree-N lattice with at least one coordinate equal to i:
-// these receive lift contributions at pyramid level i (face f contributes to
-// the nodes with alpha_f = i).
-constexpr int lift_level_nodes(int N, int i) {
-  int c = 0;
-  for (int l = 0; l <= N; ++l)
-    for (int k = 0; k <= N - l; ++k)
-      for (int j = 0; j <= N - l - k; ++j) {
-        const int a0 = N - j - k - l;
-        if (a0 == i || j == i || k == i || l == i) ++c;
-      }
-  return c;
-}
-constexpr int lift_level_off(int N, int i) {
-  int c = 0;
-  for (int x = 0; x < i; ++x) c += lift_level_nodes(N, x);
-  return c;
-}
+// Offset of pyramid level i in the per-face lift buffer: level i holds the
+// np2(N - i) coefficients of degree N - i, levels stacked from i = 0, so that
+// the whole pyramid of one face fills np3(N) slots.
+BBW_HD constexpr int lift_level_base(int N, int i) { return np3(N) - np3(N - i); }
 
 // Operator tables for one (N, M, real). Plain data, built on the host by
 // build_tables(), copied once to device memory and from there into each
@@ -98,7 +84,10 @@ struct Tables {
   real factNM[NMp];       // gamma! / C(N+M,N)  (degree N+M)
   real invfactM[Mp];      // 1 / beta!          (degree M)
   real cj[N + 1];         // projection constants c_j of Theorem 5.3
-  real ell[N + 1];        // lift layer factors (-1)^i C(N,i) / (i+1)
+  // lift: level i of a face pyramid is stored scaled by ell_i = (-1)^i C(N,i)/(i+1);
+  // lscale[i] = ell_i / (ell_{i-1} (N - i + 1)) turns a 2D reduction of the
+  // stored level i - 1 (integer weights) into the stored level i (i >= 1)
+  real lscale[N + 1];
   uint32_t red3[off3(N + M)];   // reduction words, outputs of degree d = 0..N+M-1
   uint32_t elev3[off3(N + 1)];  // elevation words, outputs of degree n = 0..N
   uint32_t red2[off2(N)];       // 2D reduction words, outputs of degree 0..N-1
@@ -109,11 +98,10 @@ struct Tables {
   uint32_t prod2[MP2 * NMp];
   uint16_t fidx[4 * Nfp];       // own volume index of face node a of face f
   uint16_t nidx[24 * Nfp];      // neighbour volume index for (nface, perm, a)
-  // lift scatter entries per pyramid level i = 0..N (offsets lift_level_off):
-  // x = node index | face mask << 9, y = face-local index of the node on each
-  // face in the mask (8 bits per face)
-  uint32_t lscat[2 * lift_level_off(N, N + 1)];
-  uint16_t lvl_off[N + 2];
+  // lift gather: for node i, byte f is the slot of its coefficient in the
+  // pyramid of face f, lift_level_base(N, alpha_f) + idx2(N - alpha_f, .)
+  uint32_t lgat[Np];
+  static_assert(Np <= 256, "8-bit lift gather slots");
 };
 
 template <int N, int M, typename real>
@@ -215,9 +203,10 @@ void build_tables(Tables<N, M, real>& t, const double* cj) {
     mi(M, b, be);
     t.invfactM[b] = real(1.0 / (fact(be[0]) * fact(be[1]) * fact(be[2]) * fact(be[3])));
   }
+  auto ell = [&](int i) { return ((i & 1) ? -1.0 : 1.0) * binom(N, i) / (i + 1); };
   for (int j = 0; j <= N; ++j) {
     t.cj[j] = real(cj[j]);
-    t.ell[j] = real(((j & 1) ? -1.0 : 1.0) * binom(N, j) / (j + 1));
+    t.lscale[j] = j == 0 ? real(1) : real(ell(j) / (ell(j - 1) * (N - j + 1)));
   }
   for (int f = 0; f < 4; ++f) {
     for (int a = 0; a < Tb::Nfp; ++a) {
@@ -233,27 +222,17 @@ void build_tables(Tables<N, M, real>& t, const double* cj) {
       }
     }
   }
-  // lift scatter entries, level by level
-  for (int lv = 0; lv <= N + 1; ++lv) t.lvl_off[lv] = uint16_t(lift_level_off(N, lv));
-  for (int lv = 0; lv <= N; ++lv) {
-    int c = 0;
-    for (int i = 0; i < Tb::Np; ++i) {
-      int a[4];
-      mi(N, i, a);
-      uint32_t mask = 0, locals = 0;
-      for (int f = 0; f < 4; ++f)
-        if (a[f] == lv) {
-          mask |= 1u << f;
-          int b[3];
-          for (int x = 0; x < 3; ++x) b[x] = a[kFaceVerts[f][x]];
-          locals |= uint32_t(idx2(N - lv, b[1], b[2])) << (8 * f);
-        }
-      if (mask) {
-        const int e = lift_level_off(N, lv) + c++;
-        t.lscat[2 * e] = uint32_t(i) | (mask << 9);
-        t.lscat[2 * e + 1] = locals;
-      }
+  // lift gather slots
+  for (int i = 0; i < Tb::Np; ++i) {
+    int a[4];
+    mi(N, i, a);
+    uint32_t w = 0;
+    for (int f = 0; f < 4; ++f) {
+      int b[3];
+      for (int x = 0; x < 3; ++x) b[x] = a[kFaceVerts[f][x]];
+      w |= uint32_t(lift_level_base(N, a[f]) + idx2(N - a[f], b[1], b[2])) << (8 * f);
     }
+    t.lgat[i] = w;
   }
 }
 

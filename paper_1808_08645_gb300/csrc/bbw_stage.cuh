@@ -16,26 +16,29 @@
 // in its own shared region; the sparse Bernstein operators are gather stencils
 // on the multi-index lattice driven by one packed word per output item
 // (base index, lattice offsets, integer weights). Team phases are separated
-// by __syncwarp (teams never span warps).
+// by a team barrier: __syncwarp within a warp, a named barrier for teams of
+// two warps.
 //
 // Per group and stage:
-//   V1/V2  grad p and div u (Sec. 4): degree N-1 combinations
-//          w_beta = sum_m g_m a_{beta+e_m}, then one degree elevation
-//          (E^N_{N-1}, Eq. 12) with integer weights gamma_j.
-//   F      penalty fluxes of Eq. (2) on the 4 N_fp face coefficients, with the
-//          neighbour traces gathered from q_in (L2),
-//   L      then per face the lift L^f = E_L L0 (Sec. 4):
-//          L0 = ((2N+3)/3) I + (N^2/3) E E^T on the face, and layer i of the
-//          element receives ell_i (E^N_{N-i})^T L0 F,
-//          ell_i = (-1)^i C(N,i)/(i+1), by i successive 2D reductions.
+//   F1     neighbour traces of the four faces gathered from q_in (L2) with
+//          asynchronous copies, in flight during V1;
+//   V1     degree N-1 barycentric combinations for grad p and div u (Sec. 4):
+//          w_beta = sum_m g_m a_{beta+e_m};
+//   F2     penalty fluxes of Eq. (2) on the 4 N_fp face coefficients;
+//   L      per face the lift pyramid of L^f = E_L L0 (Sec. 4):
+//          L0 = ((2N+3)/3) I + (N^2/3) E E^T on the face, and level i,
+//          ell_i (E^N_{N-i})^T L0 F with ell_i = (-1)^i C(N,i)/(i+1), by i
+//          successive 2D reductions; every level of both fields is kept;
+//   V2+L   per node: one degree elevation of V1 (E^N_{N-1}, Eq. 12, integer
+//          weights) plus the node's four face contributions gathered from the
+//          pyramids. The velocity fields finish their RK update here;
 //   W      weight-adjusted update of the p right-hand side: Bernstein product
 //          with c^2_M (Eq. 11 as a convolution of factorial-scaled
 //          coefficients), M degree reductions, then P~_N of Eq. (20): a
 //          downward reduction sweep whose levels stay in registers and an
-//          upward elevation sweep scaled by c_j.
-//   RK     res = a res + dt rhs, q_out = q_in + b res over the group with vector
-//          loads and stores (stage 0 skips reading res, a_0 = 0); non-finite
-//          values raise a status bit.
+//          upward elevation sweep scaled by c_j;
+//   RK     res = a res + dt rhs, q_out = q_in + b res (stage 0 skips reading
+//          res, a_0 = 0); non-finite values raise a status bit.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -232,24 +235,27 @@ struct StageCfg {
   static constexpr int NMp = np3(N + M);
   static constexpr int THREADS = T * GC;
   static constexpr int BUF = NMp > Np + 1 ? NMp : Np + 1;
-  // scratch per group, in vectors: V1 (4 (N-1)_p), neighbour traces of the
-  // four faces, later the fluxes and two lift pyramid levels (16 N_fp), WADG
-  // ping-pong (2 BUF)
-  static constexpr int S_VOL = 4 * Nm1p;
-  static constexpr int S_LIFT = 16 * Nfp;
-  static constexpr int S_WADG = 2 * BUF;
-  static constexpr int S_SZ =
-      S_VOL > S_LIFT ? (S_VOL > S_WADG ? S_VOL : S_WADG) : (S_LIFT > S_WADG ? S_LIFT : S_WADG);
-  // per-team region, in vectors: Q [4][Np] | R [4][Np] | S | normals [4][4] |
-  // c2 [Mp] | connectivity words [4][V] (int32); odd, so that teams start in
+  // scratch per group, in vectors: the lift pyramids of p and u for the four
+  // faces ([k][f][Np], level i at lift_level_base(N, i); level 0 first holds
+  // the neighbour traces and fluxes), the degree N-1 combinations of V1
+  // ([4][Nm1p]), and, when they do not fit beside level 0 in the pyramid
+  // blocks (N < 3), the v and w neighbour traces ([2][4][Nfp]). The WADG
+  // ping-pong buffers (2 BUF) reuse the region afterwards.
+  static constexpr bool TR_IN_P = Np >= 2 * Nfp;
+  static constexpr int S_PYR = 8 * Np;
+  static constexpr int S_V1 = 4 * Nm1p;
+  static constexpr int S_TR = TR_IN_P ? 0 : 8 * Nfp;
+  static constexpr int S_LIFT = S_PYR + S_V1 + S_TR;
+  static constexpr int S_SZ = S_LIFT > 2 * BUF ? S_LIFT : 2 * BUF;
+  // per-team region, in vectors: Q [4][Np] | S | normals [4][4] | c2 [Mp] |
+  // connectivity words [4][V] (int32); odd, so that teams start in
   // different shared-memory banks
   static constexpr int CONNV = (16 + int(sizeof(real)) - 1) / int(sizeof(real));
-  static constexpr int TEAMV = (8 * Np + S_SZ + 16 + Mp + CONNV) | 1;
+  static constexpr int TEAMV = (4 * Np + S_SZ + 16 + Mp + CONNV) | 1;
   static constexpr int TAB = table_bytes<N, M, real>();
   static constexpr int SMEM = TAB + int(sizeof(real)) * V * GC * TEAMV;
   static_assert(SMEM <= kSmemPerCta, "shared memory of the launch shape");
-  static constexpr int RMAX = (Np + T - 1) / T;
-  static constexpr int RK_IT = (4 * Np + T - 1) / T;  // RK vectors per lane
+  static constexpr int RMAX = (Np + T - 1) / T;  // nodes per lane
   static_assert(T >= 4 && (T <= 32 ? 32 % T == 0 : T % 32 == 0), "team: a divisor or a multiple of a warp");
   static_assert(T <= 32 || GC <= 15, "one named barrier per multi-warp team");
   static_assert(V == 1 || V == 2 || V == 4, "group width");
@@ -471,11 +477,22 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
   const int team = threadIdx.x / T;
   const int t = threadIdx.x % T;
   real* Q = reinterpret_cast<real*>(smem + C::TAB) + team * C::TEAMV * V;  // [4][Np]
-  real* R = Q + QV * V;                                                   // [4][Np]
-  real* S = R + QV * V;                                                   // scratch
+  real* S = Q + QV * V;                                                   // scratch
   real* NRM = S + C::S_SZ * V;  // [4 faces][nx, ny, nz, (1/2)|f|/|D|]
   real* C2S = NRM + 16 * V;     // [Mp]
   int* CS = reinterpret_cast<int*>(C2S + Mp * V);  // [4][V]
+  real* V1B = S + C::S_PYR * V;                    // [4][Nm1p]
+  // slot of pyramid k (0: p, 1: u) of face f
+  auto pyr = [&](int k, int f, int slot) { return S + ((k * 4 + f) * Np + slot) * V; };
+  // neighbour trace of field fld at face node a of face f: p and u in level 0
+  // of their pyramids (the fluxes replace them in place), v and w beside them
+  auto trace = [&](int fld, int f, int a) -> real* {
+    if (fld < 2) return pyr(fld, f, a);
+    if constexpr (C::TR_IN_P)
+      return pyr(fld - 2, f, Nfp + a);
+    else
+      return V1B + (C::S_V1 + ((fld - 2) * 4 + f) * Nfp + a) * V;
+  };
   const int64_t G = P.G;
   const int64_t stride = int64_t(gridDim.x) * GC;
   const bool read_res = P.a != real(0);
@@ -532,7 +549,26 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
     cp_async_wait_all();
     team_sync<T>();
 
-    // ---- V1: barycentric combinations at degree N-1, S = [4][Nm1p] ----
+    // ---- F1: neighbour traces of all four faces (asynchronous 4- or 8-byte
+    // copies from q_in in L2), in flight while V1 runs ----
+    for (int it = t; it < 4 * Nfp; it += T) {
+      const int f = it / Nfp;
+      const int a = it - f * Nfp;
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const int c = CS[f * V + v];
+        if (c >= 0) {
+          const int64_t nb = int64_t(c >> 5);
+          const int ni = tab.nidx[(((c >> 3) & 3) * 6 + (c & 7)) * Nfp + a];
+          const int64_t gq = nb / V;
+          const real* src = P.qin + (size_t(gq) * QV + ni) * V + (nb - gq * V);
+#pragma unroll
+          for (int fld = 0; fld < 4; ++fld) cp_async<int(sizeof(real))>(trace(fld, f, a) + v, src + fld * Np * V);
+        }
+      }
+    }
+
+    // ---- V1: barycentric combinations at degree N-1, V1B = [4][Nm1p] ----
     for (int i = t; i < Nm1p; i += T) {
       const Stencil3 s = unpack_stencil3(tab.red3[off3(N - 1) + i]);
       const int im[4] = {s.base, s.base + 1, s.base + s.dk, s.base + s.dl};
@@ -547,110 +583,64 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
         vfma(dv, gm[m][1], vld<real, V>(Q + (2 * Np + im[m]) * V));
         vfma(dv, gm[m][2], vld<real, V>(Q + (3 * Np + im[m]) * V));
       }
-      vst(S + i * V, gx);
-      vst(S + (Nm1p + i) * V, gy);
-      vst(S + (2 * Nm1p + i) * V, gz);
-      vst(S + (3 * Nm1p + i) * V, dv);
-    }
-    team_sync<T>();
-    // ---- V2: elevate to degree N; rhs_u = -grad p, rhs_p = -div u ----
-    for (int i = t; i < Np; i += T) {
-      const Stencil3 s = unpack_stencil3(tab.elev3[off3(N) + i]);
-      const int a0 = N - s.w1 - s.w2 - s.w3;
-      vt ax = vzero<real, V>(), ay = vzero<real, V>(), az = vzero<real, V>(), ad = vzero<real, V>();
-      auto add = [&](int idx, int w) {
-        const real wt = real(-w);
-        vfmas(ax, wt, vld<real, V>(S + idx * V));
-        vfmas(ay, wt, vld<real, V>(S + (Nm1p + idx) * V));
-        vfmas(az, wt, vld<real, V>(S + (2 * Nm1p + idx) * V));
-        vfmas(ad, wt, vld<real, V>(S + (3 * Nm1p + idx) * V));
-      };
-      if (a0 > 0) add(s.base, a0);
-      if (s.w1 > 0) add(s.base - 1, s.w1);
-      if (s.w2 > 0) add(s.base - s.dk, s.w2);
-      if (s.w3 > 0) add(s.base - s.dl, s.w3);
-      vst(R + i * V, ad);
-      vst(R + (Np + i) * V, ax);
-      vst(R + (2 * Np + i) * V, ay);
-      vst(R + (3 * Np + i) * V, az);
-    }
-    team_sync<T>();
-
-    // ---- F: neighbour traces of all four faces into NB = [field][4 Nfp]
-    // (asynchronous 4-byte copies, many in flight), then the penalty fluxes
-    // of Eq. (2) in place: F_p over field 0 and F_u over field 1 ----
-    real* NB = S;
-    for (int it = t; it < 4 * Nfp; it += T) {
-      const int f = it / Nfp;
-      const int a = it - f * Nfp;
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        const int c = CS[f * V + v];
-        if (c >= 0) {
-          const int64_t nb = int64_t(c >> 5);
-          const int ni = tab.nidx[(((c >> 3) & 3) * 6 + (c & 7)) * Nfp + a];
-          const int64_t gq = nb / V;
-          const real* src = P.qin + (size_t(gq) * QV + ni) * V + (nb - gq * V);
-#pragma unroll
-          for (int fld = 0; fld < 4; ++fld) cp_async<int(sizeof(real))>(NB + (fld * 4 * Nfp + it) * V + v, src + fld * Np * V);
-        }
-      }
+      vst(V1B + i * V, gx);
+      vst(V1B + (Nm1p + i) * V, gy);
+      vst(V1B + (2 * Nm1p + i) * V, gz);
+      vst(V1B + (3 * Nm1p + i) * V, dv);
     }
     cp_async_wait_all();
-    vt nf[4][4];  // per face: nx, ny, nz, (1/2)|f|/|D|
-#pragma unroll
-    for (int f = 0; f < 4; ++f)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) nf[f][c] = vld<real, V>(NRM + (4 * f + c) * V);
-    for (int it = t; it < 4 * Nfp; it += T) {
-      const int f = it / Nfp;
-      const int io = tab.fidx[it];
-      const vt pm = vld<real, V>(Q + io * V), um = vld<real, V>(Q + (Np + io) * V),
-               vm = vld<real, V>(Q + (2 * Np + io) * V), wm = vld<real, V>(Q + (3 * Np + io) * V);
-      vt pp = vld<real, V>(NB + it * V), up = vld<real, V>(NB + (4 * Nfp + it) * V),
-         vp = vld<real, V>(NB + (8 * Nfp + it) * V), wp = vld<real, V>(NB + (12 * Nfp + it) * V);
-#pragma unroll
-      for (int v = 0; v < V; ++v)
-        if (CS[f * V + v] < 0) {  // p = 0 wall: mirror state
-          pp.set(v, -pm.get(v));
-          up.set(v, um.get(v));
-          vp.set(v, vm.get(v));
-          wp.set(v, wm.get(v));
-        }
-      vt nx = nf[0][0], ny = nf[0][1], nz = nf[0][2], hs = nf[0][3];
-#pragma unroll
-      for (int ff = 1; ff < 4; ++ff)
-        if (f == ff) {
-          nx = nf[ff][0];
-          ny = nf[ff][1];
-          nz = nf[ff][2];
-          hs = nf[ff][3];
-        }
-      const vt jp = vsub(pp, pm);
-      vt ndu = vmul(nx, vsub(up, um));
-      vfma(ndu, ny, vsub(vp, vm));
-      vfma(ndu, nz, vsub(wp, wm));
-      vst(NB + it * V, vmul(hs, vaxpy(vmuls(P.tau_p, jp), real(-1), ndu)));
-      vst(NB + (4 * Nfp + it) * V, vmul(hs, vaxpy(vmuls(P.tau_u, ndu), real(-1), jp)));
-    }
     team_sync<T>();
 
-    // ---- L: lift L^f = E_L L0 of the four faces, level by level ----
-    // Pyramid level i of face f is ell_i (E^{N}_{N-i})^T L0 F_f restricted to
-    // the nodes with alpha_f = i. Levels of all four faces are built together
-    // in [p, u][face][Nfp] buffers (level 0 over the fluxes, in place); the
-    // nodes touched at level i are then updated once each from every face in
-    // their mask (a per-level node table), so no two lanes update one node.
+    // ---- F2: penalty fluxes of Eq. (2), in place over the p and u traces:
+    // F_p into level 0 of the p pyramids, F_u into level 0 of the u pyramids ----
     {
-      real* bufA = NB;                 // fluxes, then even levels
-      real* bufB = NB + 8 * Nfp * V;   // t = E'^T F, then odd levels
-      auto LV = [&](real* buf, int k, int f, int a) { return buf + ((k * 4 + f) * Nfp + a) * V; };
-      vt nrm[4][3];
+      vt nf[4][4];  // per face: nx, ny, nz, (1/2)|f|/|D|
 #pragma unroll
       for (int f = 0; f < 4; ++f)
 #pragma unroll
-        for (int d = 0; d < 3; ++d) nrm[f][d] = vld<real, V>(NRM + (4 * f + d) * V);
-      // t = E'^T F at degree N-1 (integer weights b_x + 1), all faces
+        for (int c = 0; c < 4; ++c) nf[f][c] = vld<real, V>(NRM + (4 * f + c) * V);
+      for (int it = t; it < 4 * Nfp; it += T) {
+        const int f = it / Nfp;
+        const int a = it - f * Nfp;
+        const int io = tab.fidx[it];
+        const vt pm = vld<real, V>(Q + io * V), um = vld<real, V>(Q + (Np + io) * V),
+                 vm = vld<real, V>(Q + (2 * Np + io) * V), wm = vld<real, V>(Q + (3 * Np + io) * V);
+        vt pp = vld<real, V>(trace(0, f, a)), up = vld<real, V>(trace(1, f, a)),
+           vp = vld<real, V>(trace(2, f, a)), wp = vld<real, V>(trace(3, f, a));
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+          if (CS[f * V + v] < 0) {  // p = 0 wall: mirror state
+            pp.set(v, -pm.get(v));
+            up.set(v, um.get(v));
+            vp.set(v, vm.get(v));
+            wp.set(v, wm.get(v));
+          }
+        vt nx = nf[0][0], ny = nf[0][1], nz = nf[0][2], hs = nf[0][3];
+#pragma unroll
+        for (int ff = 1; ff < 4; ++ff)
+          if (f == ff) {
+            nx = nf[ff][0];
+            ny = nf[ff][1];
+            nz = nf[ff][2];
+            hs = nf[ff][3];
+          }
+        const vt jp = vsub(pp, pm);
+        vt ndu = vmul(nx, vsub(up, um));
+        vfma(ndu, ny, vsub(vp, vm));
+        vfma(ndu, nz, vsub(wp, wm));
+        vst(trace(0, f, a), vmul(hs, vaxpy(vmuls(P.tau_p, jp), real(-1), ndu)));
+        vst(trace(1, f, a), vmul(hs, vaxpy(vmuls(P.tau_u, ndu), real(-1), jp)));
+      }
+    }
+    team_sync<T>();
+
+    // ---- L: lift pyramids L^f = E_L L0 of the four faces (Sec. 4) ----
+    // Level i of face f is ell_i (E^{N}_{N-i})^T L0 F_f; it lifts onto the
+    // nodes with alpha_f = i. All levels of both fields are kept (stored
+    // already scaled by ell_i), so that each node later gathers its four face
+    // contributions once.
+    {
+      // t = E'^T F at degree N-1 (integer weights b_x + 1), beside level 0
       constexpr int CT = np2(N - 1);
       for (int it = t; it < 4 * CT; it += T) {
         const int f = it / CT;
@@ -659,10 +649,10 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
         const real w0 = real(N + 2 - s.w1 - s.w2), w1 = real(s.w1), w2 = real(s.w2);
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-          vt x = vmuls(w0, vld<real, V>(LV(bufA, k, f, s.base)));
-          vfmas(x, w1, vld<real, V>(LV(bufA, k, f, s.base + 1)));
-          vfmas(x, w2, vld<real, V>(LV(bufA, k, f, s.base + s.db)));
-          vst(LV(bufB, k, f, i), x);
+          vt x = vmuls(w0, vld<real, V>(pyr(k, f, s.base)));
+          vfmas(x, w1, vld<real, V>(pyr(k, f, s.base + 1)));
+          vfmas(x, w2, vld<real, V>(pyr(k, f, s.base + s.db)));
+          vst(pyr(k, f, Nfp + i), x);
         }
       }
       team_sync<T>();
@@ -675,50 +665,22 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
         const int a0 = N - s.w1 - s.w2;
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-          vt x = vmuls(real(2 * N + 3), vld<real, V>(LV(bufA, k, f, i)));
-          if (a0 > 0) vfmas(x, real(a0), vld<real, V>(LV(bufB, k, f, s.base)));
-          if (s.w1 > 0) vfmas(x, real(s.w1), vld<real, V>(LV(bufB, k, f, s.base - 1)));
-          if (s.w2 > 0) vfmas(x, real(s.w2), vld<real, V>(LV(bufB, k, f, s.base - s.db)));
-          vst(LV(bufA, k, f, i), vmuls(third, x));
+          vt x = vmuls(real(2 * N + 3), vld<real, V>(pyr(k, f, i)));
+          if (a0 > 0) vfmas(x, real(a0), vld<real, V>(pyr(k, f, Nfp + s.base)));
+          if (s.w1 > 0) vfmas(x, real(s.w1), vld<real, V>(pyr(k, f, Nfp + s.base - 1)));
+          if (s.w2 > 0) vfmas(x, real(s.w2), vld<real, V>(pyr(k, f, Nfp + s.base - s.db)));
+          vst(pyr(k, f, i), vmuls(third, x));
         }
       }
       team_sync<T>();
-      // scatter of level lv from the pyramid buffer P into rhs
-      auto scatter = [&](int lv, const real* P) {
-        const int e0 = tab.lvl_off[lv], cnt = tab.lvl_off[lv + 1] - e0;
-        const real ell = tab.ell[lv];
-        for (int e = t; e < cnt; e += T) {
-          const uint32_t x = tab.lscat[2 * (e0 + e)];
-          const uint32_t y = tab.lscat[2 * (e0 + e) + 1];
-          const int node = int(x & 511u);
-          vt ap = vzero<real, V>(), ax = vzero<real, V>(), ay = vzero<real, V>(), az = vzero<real, V>();
-#pragma unroll
-          for (int f = 0; f < 4; ++f)
-            if ((x >> (9 + f)) & 1u) {
-              const int a = int((y >> (8 * f)) & 255u);
-              const vt gp = vld<real, V>(P + (f * Nfp + a) * V);
-              const vt gu = vld<real, V>(P + ((4 + f) * Nfp + a) * V);
-              ap = vaxpy(ap, real(1), gp);
-              vfma(ax, nrm[f][0], gu);
-              vfma(ay, nrm[f][1], gu);
-              vfma(az, nrm[f][2], gu);
-            }
-          real* r = R + node * V;
-          vst(r, vaxpy(vld<real, V>(r), ell, ap));
-          vst(r + Np * V, vaxpy(vld<real, V>(r + Np * V), ell, ax));
-          vst(r + 2 * Np * V, vaxpy(vld<real, V>(r + 2 * Np * V), ell, ay));
-          vst(r + 3 * Np * V, vaxpy(vld<real, V>(r + 3 * Np * V), ell, az));
-        }
-      };
-      real* cur = bufA;
-      real* nxt = bufB;
+      // levels 1..N: one 2D reduction each, times ell_i / ell_{i-1}
 #pragma unroll 1
       for (int lv = 1; lv <= N; ++lv) {
-        scatter(lv - 1, cur);  // reads cur, updates rhs; the pyramid below writes nxt only
         const int n2 = N - lv;  // output degree; input degree n2 + 1
         const int cnt = np2(n2);
+        const int src = lift_level_base(N, lv - 1), dst = lift_level_base(N, lv);
         const real icnt = real(1) / real(cnt);
-        const real scale = real(1) / real(n2 + 1);
+        const real scale = tab.lscale[lv];
         for (int it = t; it < 4 * cnt; it += T) {
           const int f = int((real(it) + real(0.5)) * icnt);
           const int i = it - f * cnt;
@@ -727,34 +689,94 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
                      w2 = real(s.w2) * scale;
 #pragma unroll
           for (int k = 0; k < 2; ++k) {
-            vt x = vmuls(w0, vld<real, V>(LV(cur, k, f, s.base)));
-            vfmas(x, w1, vld<real, V>(LV(cur, k, f, s.base + 1)));
-            vfmas(x, w2, vld<real, V>(LV(cur, k, f, s.base + s.db)));
-            vst(LV(nxt, k, f, i), x);
+            vt x = vmuls(w0, vld<real, V>(pyr(k, f, src + s.base)));
+            vfmas(x, w1, vld<real, V>(pyr(k, f, src + s.base + 1)));
+            vfmas(x, w2, vld<real, V>(pyr(k, f, src + s.base + s.db)));
+            vst(pyr(k, f, dst + i), x);
           }
         }
         team_sync<T>();
-        real* tmp = cur;
-        cur = nxt;
-        nxt = tmp;
       }
-      scatter(N, cur);
-      team_sync<T>();
     }
 
-    // ---- W: weight-adjusted update of the p right-hand side ----
+    // ---- V2 + lift gather per node: rhs_u = -grad p + sum_f n_f L^f F_u,
+    // rhs_p = -div u + sum_f L^f F_p. The velocity fields finish their RK
+    // update here (res = a res + dt rhs, q_out = q_in + b res); the p
+    // right-hand side (plus the point source) goes on to the WADG update. ----
+    real* resg = P.res + size_t(g) * QV * V;
+    real* qog = P.qout + size_t(g) * QV * V;
+    vt ap[C::RMAX];  // p right-hand side times 1 / alpha!
+    {
+      const int src_lane = (P.src_elem >= 0 && P.src_elem / V == g) ? int(P.src_elem % V) : -1;
+      vt nrm[4][3];
+#pragma unroll
+      for (int f = 0; f < 4; ++f)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) nrm[f][d] = vld<real, V>(NRM + (4 * f + d) * V);
+      vt rold[C::RMAX][3];  // this lane's res loads, all in flight at once
+#pragma unroll
+      for (int r = 0; r < C::RMAX; ++r) {
+        const int i = t + r * T;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          rold[r][c] = (read_res && i < Np) ? vld<real, V>(resg + size_t((1 + c) * Np + i) * V) : vzero<real, V>();
+      }
+#pragma unroll
+      for (int r = 0; r < C::RMAX; ++r) {
+        const int i = t + r * T;
+        if (i < Np) {
+          const Stencil3 s = unpack_stencil3(tab.elev3[off3(N) + i]);
+          const int a0 = N - s.w1 - s.w2 - s.w3;
+          vt ad = vzero<real, V>(), rhs[3] = {vzero<real, V>(), vzero<real, V>(), vzero<real, V>()};
+          auto add = [&](int idx, int w) {
+            const real wt = real(-w);
+            vfmas(rhs[0], wt, vld<real, V>(V1B + idx * V));
+            vfmas(rhs[1], wt, vld<real, V>(V1B + (Nm1p + idx) * V));
+            vfmas(rhs[2], wt, vld<real, V>(V1B + (2 * Nm1p + idx) * V));
+            vfmas(ad, wt, vld<real, V>(V1B + (3 * Nm1p + idx) * V));
+          };
+          if (a0 > 0) add(s.base, a0);
+          if (s.w1 > 0) add(s.base - 1, s.w1);
+          if (s.w2 > 0) add(s.base - s.dk, s.w2);
+          if (s.w3 > 0) add(s.base - s.dl, s.w3);
+          const uint32_t lg = tab.lgat[i];
+#pragma unroll
+          for (int f = 0; f < 4; ++f) {
+            const int o = int((lg >> (8 * f)) & 255u);
+            const vt gu = vld<real, V>(pyr(1, f, o));
+            ad = vaxpy(ad, real(1), vld<real, V>(pyr(0, f, o)));
+#pragma unroll
+            for (int d = 0; d < 3; ++d) vfma(rhs[d], nrm[f][d], gu);
+          }
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            vt rn = vmuls(P.dt, rhs[c]);
+            vfmas(rn, P.a, rold[r][c]);
+            vst(resg + size_t((1 + c) * Np + i) * V, rn);
+            const vt qn = vaxpy(vld<real, V>(Q + ((1 + c) * Np + i) * V), P.b, rn);
+            vst(qog + size_t((1 + c) * Np + i) * V, qn);
+#pragma unroll
+            for (int v = 0; v < V; ++v) bad |= !isfinite(qn.get(v));
+          }
+          if (src_lane >= 0) {
+#pragma unroll
+            for (int l = 0; l < V; ++l)
+              if (l == src_lane) ad.set(l, ad.get(l) + P.src_amp * P.src_vec[i]);
+          }
+          ap[r] = vmuls(tab.invfactN[i], ad);
+        }
+      }
+    }
+    team_sync<T>();
+
+    // ---- W: weight-adjusted update of the p right-hand side, then its RK update ----
     {
       real* A = S;
       real* B = S + C::BUF * V;
-      const int src_lane = (P.src_elem >= 0 && P.src_elem / V == g) ? int(P.src_elem % V) : -1;
-      for (int i = t; i < Np; i += T) {
-        vt v = vld<real, V>(R + i * V);
-        if (src_lane >= 0) {
 #pragma unroll
-          for (int l = 0; l < V; ++l)
-            if (l == src_lane) v.set(l, v.get(l) + P.src_amp * P.src_vec[i]);
-        }
-        vst(A + i * V, vmuls(tab.invfactN[i], v));
+      for (int r = 0; r < C::RMAX; ++r) {
+        const int i = t + r * T;
+        if (i < Np) vst(A + i * V, ap[r]);
       }
       if (t == 0) vst(A + Np * V, vzero<real, V>());
       vt bh[Mp];
@@ -763,33 +785,21 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
       team_sync<T>();
       vt lv[N + 1][C::RMAX];
       wadg_group<N, M, real, T, V, C::RMAX>(tab, A, B, bh, true, t, lv);
+      vt rold[C::RMAX];
 #pragma unroll
       for (int r = 0; r < C::RMAX; ++r) {
         const int i = t + r * T;
-        if (i < Np) vst(R + i * V, lv[0][r]);
-      }
-    }
-    team_sync<T>();
-
-    // ---- RK: res = a res + dt rhs; q_out = q_in + b res ([4][Np] vectors, coalesced) ----
-    {
-      real* resg = P.res + size_t(g) * QV * V;
-      real* qog = P.qout + size_t(g) * QV * V;
-      vt rold[C::RK_IT];  // all of this lane's res loads in flight at once
-#pragma unroll
-      for (int r = 0; r < C::RK_IT; ++r) {
-        const int idx = t + r * T;
-        rold[r] = (read_res && idx < QV) ? vld<real, V>(resg + size_t(idx) * V) : vzero<real, V>();
+        rold[r] = (read_res && i < Np) ? vld<real, V>(resg + size_t(i) * V) : vzero<real, V>();
       }
 #pragma unroll
-      for (int r = 0; r < C::RK_IT; ++r) {
-        const int idx = t + r * T;
-        if (idx < QV) {
-          vt rn = vmuls(P.dt, vld<real, V>(R + idx * V));
+      for (int r = 0; r < C::RMAX; ++r) {
+        const int i = t + r * T;
+        if (i < Np) {
+          vt rn = vmuls(P.dt, lv[0][r]);
           vfmas(rn, P.a, rold[r]);
-          vst(resg + size_t(idx) * V, rn);
-          const vt qn = vaxpy(vld<real, V>(Q + idx * V), P.b, rn);
-          vst(qog + size_t(idx) * V, qn);
+          vst(resg + size_t(i) * V, rn);
+          const vt qn = vaxpy(vld<real, V>(Q + i * V), P.b, rn);
+          vst(qog + size_t(i) * V, qn);
 #pragma unroll
           for (int v = 0; v < V; ++v) bad |= !isfinite(qn.get(v));
         }
