@@ -236,6 +236,9 @@ def run_gpu(args):
             "roofline": {"bound": "hbm", "kernel": f"stage_kernel N={top} M={M} f32",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
+                         "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch "
+                                         "(RK stages 1-2, which read res) from the committed summary; "
+                                         "null once the kernel sources change",
                          "algorithmic_bytes_per_launch": algorithmic_bytes_per_element(top, M) * K,
                          "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"},
             "e2e": e2e,
@@ -291,15 +294,35 @@ def run_e2e(solvers, host_q0, Ns, dts, K, steps, stream):
                     "bbw_get_state (device -> host); bytes per step amortised over the run"}
 
 
+KERNEL_SOURCES = ("bbw_stage.cuh", "bbw_common.h", "bbw_stage_inst.cuh")
+
+
+def kernel_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1808_08645_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def load_traffic(N: int):
-    """DRAM bytes per launch of the stage kernel from the committed ncu summary, if any."""
-    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
-    try:
+    """DRAM bytes per launch of the degree-N stage kernel from a committed ncu
+    summary (profiles/stage_kernel_n<N>_*dram_traffic.md, its
+    ``machine-readable:`` line). None when there is no capture for N or when
+    the kernel sources changed since the counters were taken."""
+    import glob
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", f"stage_kernel_n{N}_*dram_traffic.md"))):
         with open(path) as fh:
-            data = json.load(fh)
-        return data.get(str(N))
-    except (OSError, ValueError):
-        return None
+            for line in fh:
+                if line.startswith("machine-readable:"):
+                    try:
+                        data = json.loads(line.split(":", 1)[1])
+                    except ValueError:
+                        continue
+                    if data.get("N") == N and data.get("kernel_sources_sha256") == kernel_sources_sha256():
+                        return float(data["traffic_bytes_per_launch"])
+    return None
 
 
 # ---------------------------------------------------------------------------
