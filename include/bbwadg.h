@@ -57,6 +57,7 @@ extern "C" {
 #endif
 
 typedef struct bbw_solver bbw_solver; /* opaque, library-owned */
+typedef struct bbw_batch bbw_batch;   /* opaque, library-owned */
 
 typedef enum bbw_status {
   BBW_OK = 0,
@@ -251,6 +252,86 @@ bbw_status bbw_wadg_update(int N, int M, int precision, int64_t K, const void* r
  */
 bbw_status bbw_wadg_update_noalloc(int N, int M, int precision, int64_t K, const void* rhs,
                                    const void* c2, void* out, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Batches: many independent instances advanced together.
+ *
+ * The paper solves one mesh at a time and has no batched form; these calls
+ * are a scheduling layer of this library over the same stage kernel. A batch
+ * holds n instances (mesh, c^2, state, optional point source each) of uneven
+ * size and degree N_i; all share M, the precision, the penalty parameters,
+ * the time and dt. The instances of one degree form one bucket, a solver over
+ * the disjoint union of their meshes (each instance starts on an element-group
+ * boundary; detached padding tetrahedra stay at rest), so one persistent
+ * launch per bucket and RK stage covers all of them. bbw_batch_step can
+ * capture one RK step of all buckets into a CUDA graph and replay it; buckets
+ * run as concurrent branches of that graph. Every instance evolves exactly as
+ * it would alone in a bbw_solver with the same inputs and dt (same kernel, same
+ * arithmetic, bitwise).
+ * ------------------------------------------------------------------------ */
+
+/*
+ * Create a batch. Instance i: nverts[i] vertices vxyz[i] [nverts][3], K[i]
+ * elements etov[i] [K][4] (conventions as bbw_create), degree N[i] in 1..9.
+ * c^2 starts at 1, the state at 0, no sources, time 0. stream: cudaStream_t on
+ * which all work of the batch is ordered (NULL: the batch creates its own,
+ * since graphs cannot be captured on the legacy default stream).
+ */
+bbw_status bbw_batch_create(int n, const int64_t* nverts, const double* const* vxyz,
+                            const int64_t* K, const int64_t* const* etov, const int* N, int M,
+                            int precision, void* stream, bbw_batch** out);
+void bbw_batch_destroy(bbw_batch* b);
+
+/* Number of instances, of buckets (distinct degrees), and of elements over all
+ * buckets including padding. Any pointer may be NULL. */
+bbw_status bbw_batch_info(const bbw_batch* b, int* n, int* nbuckets, int64_t* elements);
+
+/* Instance i: its degree, element count, N_p, bucket and first element in the
+ * bucket's union mesh. Any output pointer may be NULL. */
+bbw_status bbw_batch_member(const bbw_batch* b, int i, int* N, int64_t* K, int* Np, int* bucket,
+                            int64_t* first);
+
+/* c^2 of instance i, [K_i][M_p] (rules as bbw_set_c2). */
+bbw_status bbw_batch_set_c2(bbw_batch* b, int i, const double* c2);
+
+/* State of instance i, q and res [4][K_i][N_{p,i}] (res NULL: zero). */
+bbw_status bbw_batch_set_state(bbw_batch* b, int i, const double* q, const double* res);
+
+/* State of instance i after all enqueued work (waits; reports non-finite
+ * values like bbw_sync). q or res may be NULL. */
+bbw_status bbw_batch_get_state(bbw_batch* b, int i, double* q, double* res);
+
+/* Penalty parameters of every instance (as bbw_set_params). */
+bbw_status bbw_batch_set_params(bbw_batch* b, double tau_p, double tau_u);
+
+/* Ricker point source of instance i at xs (as bbw_set_point_source, searched
+ * within instance i); elem (may be NULL) receives its element in instance i.
+ * Setting it again moves the source. */
+bbw_status bbw_batch_set_point_source(bbw_batch* b, int i, const double* xs, double f0,
+                                      double t0, int64_t* elem);
+
+/* Remove every source of the batch. */
+bbw_status bbw_batch_clear_sources(bbw_batch* b);
+
+/* The smallest CFL time step over the instances (rule of bbw_cfl_dt). */
+bbw_status bbw_batch_cfl_dt(const bbw_batch* b, double cfl, double* dt);
+
+/* Set the common time (and reset the step counter). */
+bbw_status bbw_batch_set_time(bbw_batch* b, double t);
+
+/*
+ * nsteps RK steps of every instance with step dt, asynchronous on the batch
+ * stream. use_graph != 0: each step is one replay of a CUDA graph of the whole
+ * step (built on first use per state-buffer parity and rebuilt when dt or the
+ * penalty parameters change); 0: the same launches enqueued directly.
+ */
+bbw_status bbw_batch_step(bbw_batch* b, double dt, int64_t nsteps, int use_graph);
+
+/* Wait for the batch and surface non-finite values (as bbw_sync). */
+bbw_status bbw_batch_sync(bbw_batch* b);
+
+/* Time and number of steps since the last bbw_batch_set_time (or creation). */
+bbw_status bbw_batch_get_time(const bbw_batch* b, double* t, int64_t* steps);
 
 #ifdef __cplusplus
 }

@@ -14,7 +14,7 @@ import os
 
 import numpy as np
 
-__all__ = ["BBWError", "lib", "lib_path", "Solver", "mesh_analyze", "projection_coeffs",
+__all__ = ["BBWError", "lib", "lib_path", "Solver", "Batch", "mesh_analyze", "projection_coeffs",
            "lsrk_coeffs", "wadg_update", "wadg_update_noalloc", "EXPORTS", "F32", "F64"]
 
 F32, F64 = 32, 64
@@ -64,6 +64,22 @@ EXPORTS = {
     "bbw_lsrk_coeffs": (_int, [_dp, _dp, _dp]),
     "bbw_wadg_update": (_int, [_int, _int, _int, _i64, _p, _p, _p, _p]),
     "bbw_wadg_update_noalloc": (_int, [_int, _int, _int, _i64, _p, _p, _p, _p]),
+    "bbw_batch_create": (_int, [_int, _i64p, C.POINTER(_dp), _i64p, C.POINTER(_i64p), _ip, _int, _int, _p,
+                                C.POINTER(_p)]),
+    "bbw_batch_destroy": (None, [_p]),
+    "bbw_batch_info": (_int, [_p, _ip, _ip, _i64p]),
+    "bbw_batch_member": (_int, [_p, _int, _ip, _i64p, _ip, _ip, _i64p]),
+    "bbw_batch_set_c2": (_int, [_p, _int, _dp]),
+    "bbw_batch_set_state": (_int, [_p, _int, _dp, _dp]),
+    "bbw_batch_get_state": (_int, [_p, _int, _dp, _dp]),
+    "bbw_batch_set_params": (_int, [_p, _d, _d]),
+    "bbw_batch_set_point_source": (_int, [_p, _int, _dp, _d, _d, _i64p]),
+    "bbw_batch_clear_sources": (_int, [_p]),
+    "bbw_batch_cfl_dt": (_int, [_p, _d, _dp]),
+    "bbw_batch_set_time": (_int, [_p, _d]),
+    "bbw_batch_step": (_int, [_p, _d, _i64, _int]),
+    "bbw_batch_sync": (_int, [_p]),
+    "bbw_batch_get_time": (_int, [_p, _dp, _i64p]),
 }
 
 
@@ -286,4 +302,117 @@ class Solver:
         t = C.c_double()
         n = C.c_int64()
         _check(lib().bbw_get_time(self._h, C.byref(t), C.byref(n)), "bbw_get_time")
+        return t.value, n.value
+
+
+class Batch:
+    """Owner of one ``bbw_batch`` handle: n independent instances (meshes of
+    uneven size, degrees N_i) advanced together; methods map one-to-one to
+    the ABI, instance arrays as for ``Solver``."""
+
+    def __init__(self, meshes, Ns, M: int, precision: int = F32, stream=None):
+        meshes = [(_f64(v), np.ascontiguousarray(e, dtype=np.int64)) for v, e in meshes]
+        n = len(meshes)
+        if n != len(Ns):
+            raise ValueError("one degree per mesh")
+        self._keep = meshes
+        nverts = np.array([len(v) for v, _ in meshes], np.int64)
+        K = np.array([len(e) for _, e in meshes], np.int64)
+        vptr = (_dp * n)(*[_ptr(v, C.c_double) for v, _ in meshes])
+        eptr = (_i64p * n)(*[_ptr(e, C.c_int64) for _, e in meshes])
+        Nn = np.array(Ns, np.int32)
+        h = C.c_void_p()
+        _check(lib().bbw_batch_create(n, _ptr(nverts, C.c_int64), vptr, _ptr(K, C.c_int64), eptr,
+                                      _ptr(Nn, C.c_int), M, precision, _dev(stream), C.byref(h)),
+               "bbw_batch_create")
+        self._h = h
+        self._keep = None
+        self.n, self.M, self.precision = n, M, precision
+        self.Ns = [int(x) for x in Ns]
+        self.Ks = [int(x) for x in K]
+        self.Mp = (M + 1) * (M + 2) * (M + 3) // 6
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().bbw_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def np_(self, i: int) -> int:
+        N = self.Ns[i]
+        return (N + 1) * (N + 2) * (N + 3) // 6
+
+    def info(self):
+        n, nb, el = C.c_int(), C.c_int(), C.c_int64()
+        _check(lib().bbw_batch_info(self._h, C.byref(n), C.byref(nb), C.byref(el)), "bbw_batch_info")
+        return n.value, nb.value, el.value
+
+    def member(self, i: int):
+        N, K, Np, b, e0 = C.c_int(), C.c_int64(), C.c_int(), C.c_int(), C.c_int64()
+        _check(lib().bbw_batch_member(self._h, i, C.byref(N), C.byref(K), C.byref(Np), C.byref(b), C.byref(e0)),
+               "bbw_batch_member")
+        return dict(N=N.value, K=K.value, Np=Np.value, bucket=b.value, first=e0.value)
+
+    def set_c2(self, i: int, c2):
+        c2 = _f64(c2).reshape(self.Ks[i], self.Mp)
+        _check(lib().bbw_batch_set_c2(self._h, i, _ptr(c2, C.c_double)), "bbw_batch_set_c2")
+
+    def set_state(self, i: int, q, res=None):
+        shape = (4, self.Ks[i], self.np_(i))
+        q = _f64(q).reshape(shape)
+        r = None if res is None else _f64(res).reshape(shape)
+        _check(lib().bbw_batch_set_state(self._h, i, _ptr(q, C.c_double),
+                                         None if r is None else _ptr(r, C.c_double)), "bbw_batch_set_state")
+
+    def get_state(self, i: int, with_res: bool = False):
+        shape = (4, self.Ks[i], self.np_(i))
+        q = np.empty(shape)
+        r = np.empty(shape) if with_res else None
+        _check(lib().bbw_batch_get_state(self._h, i, _ptr(q, C.c_double),
+                                         None if r is None else _ptr(r, C.c_double)), "bbw_batch_get_state")
+        return (q, r) if with_res else q
+
+    def set_params(self, tau_p: float, tau_u: float):
+        _check(lib().bbw_batch_set_params(self._h, tau_p, tau_u), "bbw_batch_set_params")
+
+    def set_point_source(self, i: int, xs, f0: float = 10.0, t0: float | None = None) -> int:
+        xs = _f64(xs)
+        e = C.c_int64()
+        _check(lib().bbw_batch_set_point_source(self._h, i, _ptr(xs, C.c_double), f0,
+                                                1.0 / f0 if t0 is None else t0, C.byref(e)),
+               "bbw_batch_set_point_source")
+        return e.value
+
+    def clear_sources(self):
+        _check(lib().bbw_batch_clear_sources(self._h), "bbw_batch_clear_sources")
+
+    def cfl_dt(self, cfl: float) -> float:
+        dt = C.c_double()
+        _check(lib().bbw_batch_cfl_dt(self._h, cfl, C.byref(dt)), "bbw_batch_cfl_dt")
+        return dt.value
+
+    def set_time(self, t: float):
+        _check(lib().bbw_batch_set_time(self._h, t), "bbw_batch_set_time")
+
+    def step(self, dt: float, nsteps: int = 1, graph: bool = True):
+        _check(lib().bbw_batch_step(self._h, dt, nsteps, 1 if graph else 0), "bbw_batch_step")
+
+    def sync(self):
+        _check(lib().bbw_batch_sync(self._h), "bbw_batch_sync")
+
+    def time(self):
+        t = C.c_double()
+        n = C.c_int64()
+        _check(lib().bbw_batch_get_time(self._h, C.byref(t), C.byref(n)), "bbw_batch_get_time")
         return t.value, n.value

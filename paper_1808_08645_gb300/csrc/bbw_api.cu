@@ -18,22 +18,17 @@
 #include "bbw_ops.h"
 #include "bbw_stage.cuh"
 #include "bbwadg.h"
+#include "bbw_solver.h"
+
+using bbw::fail;
+using bbw::OpCache;
+using bbw::check_status;
+using bbw::ensure_pinned;
 
 namespace {
 
 thread_local std::string g_err;
 
-bbw_status fail(bbw_status s, const std::string& msg) {
-  g_err = msg;
-  return s;
-}
-
-#define BBW_CUDA(call)                                                                   \
-  do {                                                                                   \
-    cudaError_t e_ = (call);                                                             \
-    if (e_ != cudaSuccess)                                                               \
-      return fail(BBW_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));    \
-  } while (0)
 
 // ---------------------------------------------------------------------------
 // constants
@@ -82,11 +77,6 @@ std::array<double, 5> rk_stage_times() {
     c[s] = acc;
   }
   return c;
-}
-
-double ricker(double t, double f0, double t0) {
-  const double a = (M_PI * f0 * (t - t0)) * (M_PI * f0 * (t - t0));
-  return (1.0 - 2.0 * a) * std::exp(-a);
 }
 
 double factd(int n) {
@@ -214,12 +204,6 @@ cudaError_t copy_to_user(const void* src, int src_prec, void* dst, int dst_prec,
                         : state_to_user<float, float>(src, dst, K, Np, V, s);
 }
 
-// per-process cache of device tables and launch grids for the stateless
-// operator entry point (keyed by device, N, M, precision)
-struct OpCache {
-  void* tables = nullptr;
-  int per_sm_stage = 0, per_sm_wadg = 0;
-};
 std::mutex g_cache_mu;
 std::map<std::tuple<int, int, int, int>, OpCache> g_cache;
 
@@ -265,64 +249,20 @@ void set_last_error(const char* msg) { g_err = msg; }
 // ---------------------------------------------------------------------------
 // solver object
 
-struct bbw_solver {
-  int N = 0, M = 0, prec = 32;
-  int64_t K = 0;
-  int Np = 0, Nfp = 0, Mp = 0;
-  cudaStream_t stream = nullptr;
-  const bbw::KernelOps* ops = nullptr;
-  OpCache* op = nullptr;
-  int grid_stage = 1;
-  std::vector<double> vxyz;
-  std::vector<int64_t> etov;
-  std::vector<double> grad;  // [K][4][3]
-  std::vector<double> vol;   // [K]
-  std::vector<int32_t> etoe;
-  std::vector<int8_t> etof, fperm;
-  std::vector<double> c2;  // [K][Mp]
-  double cj[bbw::kMaxN + 1] = {};
-  void* q[2] = {nullptr, nullptr};
-  void* res = nullptr;
-  void* d_c2 = nullptr;
-  void* d_geom = nullptr;
-  int32_t* d_conn = nullptr;
-  void* d_src = nullptr;
-  unsigned int* d_status = nullptr;
-  void* pinned = nullptr;
-  size_t pinned_bytes = 0;
-  int cur = 0;
-  double t = 0.0;
-  int64_t stages = 0;
-  double tau_p = 1.0, tau_u = 1.0;
-  int64_t src_elem = -1;
-  double f0 = 0.0, t0 = 0.0;
-  int V = 1;        // elements per group of the kernel's layout
-  int64_t G = 0;   // number of groups, ceil(K / V)
-  size_t rsz() const { return prec == 64 ? 8 : 4; }
-  size_t nstate() const { return size_t(4) * size_t(K) * size_t(Np); }           // user layout
-  size_t nstate_internal() const { return size_t(4) * size_t(G) * V * Np; }      // grouped layout
-};
 
 namespace {
 
 void free_solver(bbw_solver* s) {
   if (!s) return;
   for (void* p : {s->q[0], s->q[1], s->res, s->d_c2, s->d_geom, static_cast<void*>(s->d_conn), s->d_src,
+                  static_cast<void*>(s->d_src_group), static_cast<void*>(s->d_src_slots),
+                  static_cast<void*>(s->d_src_wav),
                   static_cast<void*>(s->d_status)})
     if (p) cudaFree(p);
   if (s->pinned) cudaFreeHost(s->pinned);
   delete s;
 }
 
-bbw_status ensure_pinned(bbw_solver* s, size_t bytes) {
-  if (s->pinned_bytes >= bytes) return BBW_OK;
-  if (s->pinned) cudaFreeHost(s->pinned);
-  s->pinned = nullptr;
-  s->pinned_bytes = 0;
-  BBW_CUDA(cudaMallocHost(&s->pinned, bytes));
-  s->pinned_bytes = bytes;
-  return BBW_OK;
-}
 
 // host doubles -> device buffer of the solver precision, through pinned memory
 bbw_status upload(bbw_solver* s, const double* src, void* dst, size_t n) {
@@ -407,17 +347,6 @@ bbw_status upload_grouped(bbw_solver* s, const double* src, int W, double pad, v
   return BBW_OK;
 }
 
-bbw_status check_status(bbw_solver* s) {
-  BBW_CUDA(cudaStreamSynchronize(s->stream));
-  BBW_CUDA(cudaGetLastError());
-  unsigned int st = 0;
-  BBW_CUDA(cudaMemcpy(&st, s->d_status, sizeof(st), cudaMemcpyDeviceToHost));
-  if (st) {
-    BBW_CUDA(cudaMemset(s->d_status, 0, sizeof(unsigned int)));
-    return fail(BBW_ERR_NONFINITE, "the stage kernel produced a non-finite value");
-  }
-  return BBW_OK;
-}
 
 // connectivity by sorting face keys (sorted global vertex triples)
 bbw_status build_connectivity(bbw_solver* s) {
@@ -568,9 +497,14 @@ bbw_status launch_stage(bbw_solver* s, int stage, double dt) {
   P.dt = real(dt);
   P.tau_p = real(s->tau_p);
   P.tau_u = real(s->tau_u);
-  P.src_elem = s->src_elem;
+  P.n_src_groups = s->src_elem >= 0 ? 1 : 0;
+  P.src_groups = s->d_src_group;
+  P.src_slots = s->d_src_slots;
   P.src_vec = static_cast<const real*>(s->d_src);
-  P.src_amp = real(s->src_elem >= 0 ? ricker(s->t + c[stage] * dt, s->f0, s->t0) : 0.0);
+  P.src_wav = s->d_src_wav;
+  P.t_dev = nullptr;
+  P.t_step = s->t;
+  P.c_dt = c[stage] * dt;
   P.status = s->d_status;
   BBW_CUDA(s->ops->launch_stage(s->M, s->prec == 64, &P, s->grid_stage, s->stream));
   s->cur = 1 - s->cur;
@@ -580,6 +514,70 @@ bbw_status launch_stage(bbw_solver* s, int stage, double dt) {
 }
 
 }  // namespace
+
+namespace bbw {
+
+bbw_status ensure_pinned(bbw_solver* s, size_t bytes) {
+  if (s->pinned_bytes >= bytes) return BBW_OK;
+  if (s->pinned) cudaFreeHost(s->pinned);
+  s->pinned = nullptr;
+  s->pinned_bytes = 0;
+  BBW_CUDA(cudaMallocHost(&s->pinned, bytes));
+  s->pinned_bytes = bytes;
+  return BBW_OK;
+}
+
+}  // namespace bbw
+
+namespace bbw {
+
+bbw_status check_status(bbw_solver* s) {
+  BBW_CUDA(cudaStreamSynchronize(s->stream));
+  BBW_CUDA(cudaGetLastError());
+  unsigned int st = 0;
+  BBW_CUDA(cudaMemcpy(&st, s->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+  if (st) {
+    BBW_CUDA(cudaMemset(s->d_status, 0, sizeof(unsigned int)));
+    return fail(BBW_ERR_NONFINITE, "the stage kernel produced a non-finite value");
+  }
+  return BBW_OK;
+}
+
+}  // namespace bbw
+
+bbw_status bbw::point_source_vector(const bbw_solver* s, const double* xs, int64_t e_begin, int64_t e_end,
+                                    int64_t* elem, std::vector<double>* vec) {
+  int64_t found = -1;
+  double lam[4] = {0, 0, 0, 0};
+  for (int64_t e = e_begin; e < e_end && found < 0; ++e) {
+    const double* g = &s->grad[size_t(e) * 12];
+    const double* v0 = &s->vxyz[size_t(s->etov[size_t(e) * 4]) * 3];
+    double l[4];
+    bool inside = true;
+    for (int m = 0; m < 4; ++m) {
+      l[m] = (m == 0 ? 1.0 : 0.0);
+      for (int d = 0; d < 3; ++d) l[m] += g[3 * m + d] * (xs[d] - v0[d]);
+      inside = inside && l[m] >= -1e-12;
+    }
+    if (inside) {
+      found = e;
+      std::memcpy(lam, l, sizeof(lam));
+    }
+  }
+  if (found < 0) return fail(BBW_ERR_ARG, "source point lies outside the mesh");
+  const auto A = multi_indices(s->N);
+  std::vector<double>& b = *vec;
+  b.assign(A.size(), 0.0);
+  for (size_t i = 0; i < A.size(); ++i) {
+    double v = factd(s->N) / (factd(A[i][0]) * factd(A[i][1]) * factd(A[i][2]) * factd(A[i][3]));
+    for (int x = 0; x < 4; ++x) v *= std::pow(std::max(lam[x], 0.0), A[i][x]);
+    b[i] = v;
+  }
+  if (!mass_solve(s->N, b)) return fail(BBW_ERR_ARG, "mass matrix factorisation failed");
+  for (double& v : b) v /= s->vol[size_t(found)];
+  *elem = found;
+  return BBW_OK;
+}
 
 // ---------------------------------------------------------------------------
 // C ABI
@@ -807,6 +805,19 @@ bbw_status bbw_set_source(bbw_solver* s, int64_t elem, const double* coeffs, dou
   if (!std::isfinite(f0) || !std::isfinite(t0)) return fail(BBW_ERR_ARG, "non-finite wavelet parameter");
   bbw_status st = upload(s, coeffs, s->d_src, size_t(s->Np));
   if (st != BBW_OK) return st;
+  if (!s->d_src_group) BBW_CUDA(cudaMalloc(reinterpret_cast<void**>(&s->d_src_group), sizeof(int64_t)));
+  if (!s->d_src_slots) BBW_CUDA(cudaMalloc(reinterpret_cast<void**>(&s->d_src_slots), s->V * sizeof(int32_t)));
+  if (!s->d_src_wav) BBW_CUDA(cudaMalloc(reinterpret_cast<void**>(&s->d_src_wav), 2 * sizeof(double)));
+  // one source group: element elem is lane elem % V of group elem / V
+  const int64_t grp = elem / s->V;
+  std::vector<int32_t> slots(size_t(s->V), -1);
+  slots[size_t(elem % s->V)] = 0;
+  const double wav[2] = {f0, t0};
+  BBW_CUDA(cudaMemcpyAsync(s->d_src_group, &grp, sizeof(grp), cudaMemcpyHostToDevice, s->stream));
+  BBW_CUDA(cudaMemcpyAsync(s->d_src_slots, slots.data(), slots.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                           s->stream));
+  BBW_CUDA(cudaMemcpyAsync(s->d_src_wav, wav, sizeof(wav), cudaMemcpyHostToDevice, s->stream));
+  BBW_CUDA(cudaStreamSynchronize(s->stream));
   s->src_elem = elem;
   s->f0 = f0;
   s->t0 = t0;
@@ -816,32 +827,9 @@ bbw_status bbw_set_source(bbw_solver* s, int64_t elem, const double* coeffs, dou
 bbw_status bbw_set_point_source(bbw_solver* s, const double* xs, double f0, double t0, int64_t* elem) {
   if (!s || !xs) return fail(BBW_ERR_ARG, "NULL argument");
   int64_t found = -1;
-  double lam[4] = {0, 0, 0, 0};
-  for (int64_t e = 0; e < s->K && found < 0; ++e) {
-    const double* g = &s->grad[size_t(e) * 12];
-    const double* v0 = &s->vxyz[size_t(s->etov[size_t(e) * 4]) * 3];
-    double l[4];
-    bool inside = true;
-    for (int m = 0; m < 4; ++m) {
-      l[m] = (m == 0 ? 1.0 : 0.0);
-      for (int d = 0; d < 3; ++d) l[m] += g[3 * m + d] * (xs[d] - v0[d]);
-      inside = inside && l[m] >= -1e-12;
-    }
-    if (inside) {
-      found = e;
-      std::memcpy(lam, l, sizeof(lam));
-    }
-  }
-  if (found < 0) return fail(BBW_ERR_ARG, "source point lies outside the mesh");
-  const auto A = multi_indices(s->N);
-  std::vector<double> b(A.size());
-  for (size_t i = 0; i < A.size(); ++i) {
-    double v = factd(s->N) / (factd(A[i][0]) * factd(A[i][1]) * factd(A[i][2]) * factd(A[i][3]));
-    for (int x = 0; x < 4; ++x) v *= std::pow(std::max(lam[x], 0.0), A[i][x]);
-    b[i] = v;
-  }
-  if (!mass_solve(s->N, b)) return fail(BBW_ERR_ARG, "mass matrix factorisation failed");
-  for (double& v : b) v /= s->vol[size_t(found)];
+  std::vector<double> b;
+  bbw_status st = bbw::point_source_vector(s, xs, 0, s->K, &found, &b);
+  if (st != BBW_OK) return st;
   if (elem) *elem = found;
   return bbw_set_source(s, found, b.data(), f0, t0);
 }

@@ -1,0 +1,93 @@
+// bbw_solver.h -- internal to libbbwadg: the solver object and the host
+// helpers shared by the translation units of the C ABI (bbw_api.cu,
+// bbw_batch.cu). Not installed; callers see only include/bbwadg.h.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "bbw_common.h"
+#include "bbw_ops.h"
+#include "bbwadg.h"
+
+namespace bbw {
+
+// per-process cache of device tables and launch grids for the stateless
+// operator entry point (keyed by device, N, M, precision)
+struct OpCache {
+  void* tables = nullptr;
+  int per_sm_stage = 0, per_sm_wadg = 0;
+};
+
+// Record msg as the thread's last error and return s.
+inline bbw_status fail(bbw_status s, const std::string& msg) {
+  set_last_error(msg.c_str());
+  return s;
+}
+
+#define BBW_CUDA(call)                                                                    \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return bbw::fail(BBW_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+}  // namespace bbw
+
+struct bbw_solver {
+  int N = 0, M = 0, prec = 32;
+  int64_t K = 0;
+  int Np = 0, Nfp = 0, Mp = 0;
+  cudaStream_t stream = nullptr;
+  const bbw::KernelOps* ops = nullptr;
+  bbw::OpCache* op = nullptr;
+  int grid_stage = 1;
+  std::vector<double> vxyz;
+  std::vector<int64_t> etov;
+  std::vector<double> grad;  // [K][4][3]
+  std::vector<double> vol;   // [K]
+  std::vector<int32_t> etoe;
+  std::vector<int8_t> etof, fperm;
+  std::vector<double> c2;  // [K][Mp]
+  double cj[bbw::kMaxN + 1] = {};
+  void* q[2] = {nullptr, nullptr};
+  void* res = nullptr;
+  void* d_c2 = nullptr;
+  void* d_geom = nullptr;
+  int32_t* d_conn = nullptr;
+  void* d_src = nullptr;          // [Np] source vector
+  int64_t* d_src_group = nullptr;  // [1] group of src_elem
+  int32_t* d_src_slots = nullptr;  // [V] source slot per lane of that group (0 at src_elem, else -1)
+  double* d_src_wav = nullptr;    // [2] Ricker f0, t0
+  unsigned int* d_status = nullptr;
+  void* pinned = nullptr;
+  size_t pinned_bytes = 0;
+  int cur = 0;
+  double t = 0.0;
+  int64_t stages = 0;
+  double tau_p = 1.0, tau_u = 1.0;
+  int64_t src_elem = -1;
+  double f0 = 0.0, t0 = 0.0;
+  int V = 1;        // elements per group of the kernel's layout
+  int64_t G = 0;   // number of groups, ceil(K / V)
+  size_t rsz() const { return prec == 64 ? 8 : 4; }
+  size_t nstate() const { return size_t(4) * size_t(K) * size_t(Np); }           // user layout
+  size_t nstate_internal() const { return size_t(4) * size_t(G) * V * Np; }      // grouped layout
+};
+
+namespace bbw {
+
+// Grow the solver's pinned staging buffer to at least bytes.
+bbw_status ensure_pinned(bbw_solver* s, size_t bytes);
+// Wait for the solver's stream and surface the device status word.
+bbw_status check_status(bbw_solver* s);
+// Point source at xs searched among elements [e_begin, e_end) (lowest index
+// wins on shared faces): its element and the vector M^{-1} B(x_s) / |D| of
+// N_p Bernstein coefficients.
+bbw_status point_source_vector(const bbw_solver* s, const double* xs, int64_t e_begin, int64_t e_end,
+                               int64_t* elem, std::vector<double>* vec);
+
+}  // namespace bbw

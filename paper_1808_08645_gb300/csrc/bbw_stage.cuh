@@ -59,9 +59,21 @@ struct StageParams {
   int64_t G;                      // number of element groups
   real a, b, dt;
   real tau_p, tau_u;
-  int64_t src_elem;               // -1: no source
-  const real* __restrict__ src_vec;  // [Np]
-  real src_amp;
+  // point sources, listed by group: src_groups[j] (ascending) holds at least
+  // one source and src_slots[j][v] is the source of its element lane v (-1:
+  // none); n_src_groups == 0: no sources. Source k adds r_k(t_s) src_vec[k][.]
+  // to the p right-hand side, r_k the Ricker wavelet of (f0, t0) =
+  // src_wav[k][0..1] at the stage time t_s = t + c_dt, where t, the time at
+  // the start of the step, is *t_dev (device-resident, for replayed graphs)
+  // or t_step.
+  int64_t n_src_groups;
+  const int64_t* __restrict__ src_groups;  // [n_src_groups]
+  const int32_t* __restrict__ src_slots;   // [n_src_groups][V]
+  const real* __restrict__ src_vec;        // [nsrc][Np]
+  const double* __restrict__ src_wav;      // [nsrc][2]
+  const double* t_dev;
+  double t_step;
+  double c_dt;
   unsigned int* status;           // bit 0: non-finite output
 };
 
@@ -248,9 +260,10 @@ struct StageCfg {
   static constexpr int S_LIFT = S_PYR + S_V1 + S_TR;
   static constexpr int S_SZ = S_LIFT > 2 * BUF ? S_LIFT : 2 * BUF;
   // per-team region, in vectors: Q [4][Np] | S | normals [4][4] | c2 [Mp] |
-  // connectivity words [4][V] (int32); odd, so that teams start in
-  // different shared-memory banks
-  static constexpr int CONNV = (16 + int(sizeof(real)) - 1) / int(sizeof(real));
+  // source amplitudes [V] | connectivity words [4][V] and source slots [V]
+  // (int32, the slots written only for groups that hold a source); odd, so
+  // that teams start in different shared-memory banks
+  static constexpr int CONNV = 1 + (20 + int(sizeof(real)) - 1) / int(sizeof(real));
   static constexpr int TEAMV = (4 * Np + S_SZ + 16 + Mp + CONNV) | 1;
   static constexpr int TAB = table_bytes<N, M, real>();
   static constexpr int SMEM = TAB + int(sizeof(real)) * V * GC * TEAMV;
@@ -461,6 +474,14 @@ __device__ __forceinline__ void wadg_group(const Tables<N, M, real>& tab, real* 
   }
 }
 
+// Ricker amplitude of source sd at the stage time; out of line, since only
+// the groups that hold a source call it.
+template <typename real>
+__device__ __noinline__ double stage_wavelet(const StageParams<real>& P, int sd) {
+  const double t = (P.t_dev ? *P.t_dev : P.t_step) + P.c_dt;
+  return ricker_wavelet(t, P.src_wav[2 * sd], P.src_wav[2 * sd + 1]);
+}
+
 template <int N, int M, typename real, int T, int V, int GC>
 __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P) {
   using C = StageCfg<N, M, real, T, V, GC>;
@@ -480,7 +501,8 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
   real* S = Q + QV * V;                                                   // scratch
   real* NRM = S + C::S_SZ * V;  // [4 faces][nx, ny, nz, (1/2)|f|/|D|]
   real* C2S = NRM + 16 * V;     // [Mp]
-  int* CS = reinterpret_cast<int*>(C2S + Mp * V);  // [4][V]
+  real* AMP = C2S + Mp * V;                       // [V] source amplitude of this stage
+  int* CS = reinterpret_cast<int*>(AMP + V);       // [4][V] connectivity, [V] source slots
   real* V1B = S + C::S_PYR * V;                    // [4][Nm1p]
   // slot of pyramid k (0: p, 1: u) of face f
   auto pyr = [&](int k, int f, int slot) { return S + ((k * 4 + f) * Np + slot) * V; };
@@ -497,6 +519,23 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
   const int64_t stride = int64_t(gridDim.x) * GC;
   const bool read_res = P.a != real(0);
   bool bad = false;
+  // cursor into the source groups: the first one at or after this team's
+  // first group (the team's groups only increase; group indices fit 32 bits)
+  const int nsg = int(P.n_src_groups);
+  int js = 0;
+  {
+    int lo = 0, hi = nsg;
+    const int64_t g0 = int64_t(blockIdx.x) * GC + team;
+    while (lo < hi) {
+      const int mid = (lo + hi) / 2;
+      if (P.src_groups[mid] < g0)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    js = lo;
+  }
+  int next_src = js < nsg ? int(P.src_groups[js]) : INT32_MAX;
 
   for (int64_t g = int64_t(blockIdx.x) * GC + team; g < G; g += stride) {
     // the team's next group into L2
@@ -512,6 +551,13 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
       for (int idx = t; idx < QV; idx += T) cp_async<VB>(Q + idx * V, qg + size_t(idx) * V);
       for (int idx = t; idx < Mp; idx += T) cp_async<VB>(C2S + idx * V, P.c2 + (size_t(g) * Mp + idx) * V);
       for (int idx = t; idx < 4 * V; idx += T) cp_async<4>(CS + idx, P.conn + size_t(g) * 4 * V + idx);
+    }
+    // the group's sources: slot (-1: none) and wavelet amplitude per element lane
+    while (next_src < g) next_src = ++js < nsg ? int(P.src_groups[js]) : INT32_MAX;
+    if (t < V) {
+      const int sd = next_src == g ? P.src_slots[size_t(js) * V + t] : -1;
+      CS[4 * V + t] = sd;
+      if (sd >= 0) AMP[t] = real(stage_wavelet(P, sd));
     }
     vt gm[4][3];
 #pragma unroll
@@ -705,9 +751,8 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
     // right-hand side (plus the point source) goes on to the WADG update. ----
     real* resg = P.res + size_t(g) * QV * V;
     real* qog = P.qout + size_t(g) * QV * V;
-    vt ap[C::RMAX];  // p right-hand side times 1 / alpha!
+    vt ap[C::RMAX];  // p right-hand side without the source
     {
-      const int src_lane = (P.src_elem >= 0 && P.src_elem / V == g) ? int(P.src_elem % V) : -1;
       vt nrm[4][3];
 #pragma unroll
       for (int f = 0; f < 4; ++f)
@@ -758,12 +803,7 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
 #pragma unroll
             for (int v = 0; v < V; ++v) bad |= !isfinite(qn.get(v));
           }
-          if (src_lane >= 0) {
-#pragma unroll
-            for (int l = 0; l < V; ++l)
-              if (l == src_lane) ad.set(l, ad.get(l) + P.src_amp * P.src_vec[i]);
-          }
-          ap[r] = vmuls(tab.invfactN[i], ad);
+          ap[r] = ad;
         }
       }
     }
@@ -773,10 +813,24 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
     {
       real* A = S;
       real* B = S + C::BUF * V;
+      // plus the point sources, times 1 / alpha!
+      bool any_src = false;
+#pragma unroll
+      for (int l = 0; l < V; ++l) any_src |= CS[4 * V + l] >= 0;
 #pragma unroll
       for (int r = 0; r < C::RMAX; ++r) {
         const int i = t + r * T;
-        if (i < Np) vst(A + i * V, ap[r]);
+        if (i < Np) {
+          vt v = ap[r];
+          if (any_src) {
+#pragma unroll
+            for (int l = 0; l < V; ++l) {
+              const int sd = CS[4 * V + l];
+              if (sd >= 0) v.set(l, v.get(l) + AMP[l] * P.src_vec[size_t(sd) * Np + i]);
+            }
+          }
+          vst(A + i * V, vmuls(tab.invfactN[i], v));
+        }
       }
       if (t == 0) vst(A + Np * V, vzero<real, V>());
       vt bh[Mp];
