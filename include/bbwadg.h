@@ -327,6 +327,18 @@ bbw_status bbw_batch_set_time(bbw_batch* b, double t);
  */
 bbw_status bbw_batch_step(bbw_batch* b, double dt, int64_t nsteps, int use_graph);
 
+/*
+ * Choose the batch's launch schedule by timing: every candidate (buckets as
+ * concurrent graph branches or one after another; persistent grids of 1/2,
+ * 1 or 2 times the solo grid) runs `steps` graph-replayed steps and the
+ * fastest is kept for later bbw_batch_step calls. The trial steps use dt = 0,
+ * which leaves the state and the time unchanged (res is reset, as at any
+ * step's first stage). schedule (may be NULL) receives the chosen candidate
+ * (0 = default: concurrent branches, solo grids) and ms_per_step (may be
+ * NULL) its time per step. Waits for the batch.
+ */
+bbw_status bbw_batch_autotune(bbw_batch* b, int steps, int* schedule, double* ms_per_step);
+
 /* Wait for the batch and surface non-finite values (as bbw_sync). */
 bbw_status bbw_batch_sync(bbw_batch* b);
 

@@ -78,6 +78,7 @@ EXPORTS = {
     "bbw_batch_cfl_dt": (_int, [_p, _d, _dp]),
     "bbw_batch_set_time": (_int, [_p, _d]),
     "bbw_batch_step": (_int, [_p, _d, _i64, _int]),
+    "bbw_batch_autotune": (_int, [_p, _int, _ip, _dp]),
     "bbw_batch_sync": (_int, [_p]),
     "bbw_batch_get_time": (_int, [_p, _dp, _i64p]),
 }
@@ -407,6 +408,14 @@ class Batch:
 
     def step(self, dt: float, nsteps: int = 1, graph: bool = True):
         _check(lib().bbw_batch_step(self._h, dt, nsteps, 1 if graph else 0), "bbw_batch_step")
+
+    def autotune(self, steps: int = 3):
+        """Time the candidate launch schedules and keep the fastest; returns
+        (schedule index, ms per step)."""
+        c = C.c_int()
+        ms = C.c_double()
+        _check(lib().bbw_batch_autotune(self._h, steps, C.byref(c), C.byref(ms)), "bbw_batch_autotune")
+        return c.value, ms.value
 
     def sync(self):
         _check(lib().bbw_batch_sync(self._h), "bbw_batch_sync")

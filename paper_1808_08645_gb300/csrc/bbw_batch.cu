@@ -60,6 +60,7 @@ struct bbw_batch {
     void* d_vec = nullptr;               // [members][Np] source vectors
     double* d_wav = nullptr;             // [members][2] Ricker f0, t0
     std::vector<int64_t> src_elem;       // per member slot: element of its source or -1
+    int grid0 = 1;                       // persistent grid of the solo solver (CTAs)
   };
   int n = 0, M = 0, prec = 32;
   cudaStream_t stream = nullptr;
@@ -73,6 +74,12 @@ struct bbw_batch {
   cudaEvent_t fork = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   double graph_dt[2] = {NAN, NAN};
+  // launch schedule (bbw_batch_autotune): buckets as concurrent graph
+  // branches or one after another, and the persistent grid of every bucket
+  // as a fraction of its solo grid
+  bool serial = false;
+  double grid_factor = 1.0;
+  int schedule = 0;
 };
 
 namespace {
@@ -149,14 +156,22 @@ bbw_status launch_bucket_step(bbw_batch* b, bbw_batch::Bucket& k, double dt, cud
 // One RK step of every bucket, forked onto the bucket streams and joined back
 // onto the batch stream, then the device time advanced by dt.
 bbw_status enqueue_step(bbw_batch* b, double dt) {
-  BBW_CUDA(cudaEventRecord(b->fork, b->stream));
-  for (auto& k : b->buckets) {
-    BBW_CUDA(cudaStreamWaitEvent(k.side, b->fork, 0));
-    bbw_status r = b->prec == 64 ? launch_bucket_step<double>(b, k, dt, k.side)
-                                 : launch_bucket_step<float>(b, k, dt, k.side);
-    if (r != BBW_OK) return r;
-    BBW_CUDA(cudaEventRecord(k.done, k.side));
-    BBW_CUDA(cudaStreamWaitEvent(b->stream, k.done, 0));
+  if (b->serial) {
+    for (auto& k : b->buckets) {
+      bbw_status r = b->prec == 64 ? launch_bucket_step<double>(b, k, dt, b->stream)
+                                   : launch_bucket_step<float>(b, k, dt, b->stream);
+      if (r != BBW_OK) return r;
+    }
+  } else {
+    BBW_CUDA(cudaEventRecord(b->fork, b->stream));
+    for (auto& k : b->buckets) {
+      BBW_CUDA(cudaStreamWaitEvent(k.side, b->fork, 0));
+      bbw_status r = b->prec == 64 ? launch_bucket_step<double>(b, k, dt, k.side)
+                                   : launch_bucket_step<float>(b, k, dt, k.side);
+      if (r != BBW_OK) return r;
+      BBW_CUDA(cudaEventRecord(k.done, k.side));
+      BBW_CUDA(cudaStreamWaitEvent(b->stream, k.done, 0));
+    }
   }
   advance_time_kernel<<<1, 1, 0, b->stream>>>(b->d_t, dt);
   BBW_CUDA(cudaGetLastError());
@@ -339,6 +354,7 @@ bbw_status bbw_batch_create(int n, const int64_t* nverts, const double* const* v
                                &k.s);
     if (st != BBW_OK) return bail(st);
     k.src_elem.assign(ids.size(), -1);
+    k.grid0 = k.s->grid_stage;
     const bool ok = cudaStreamCreateWithFlags(&k.side, cudaStreamNonBlocking) == cudaSuccess &&
                     cudaEventCreateWithFlags(&k.done, cudaEventDisableTiming) == cudaSuccess &&
                     cudaMalloc(reinterpret_cast<void**>(&k.d_groups), ids.size() * sizeof(int64_t)) == cudaSuccess &&
@@ -545,6 +561,60 @@ bbw_status bbw_batch_step(bbw_batch* b, double dt, int64_t nsteps, int use_graph
     b->steps += 1;
   }
   return BBW_OK;
+}
+
+bbw_status bbw_batch_autotune(bbw_batch* b, int steps, int* schedule, double* ms_per_step) {
+  if (!b) return fail(BBW_ERR_ARG, "batch is NULL");
+  if (steps < 1) return fail(BBW_ERR_ARG, "steps must be >= 1");
+  // candidate schedules: (serial, grid factor); 0 is the default
+  static const struct {
+    bool serial;
+    double factor;
+  } cand[] = {{false, 1.0}, {true, 1.0}, {false, 0.5}, {false, 2.0}};
+  constexpr int ncand = int(sizeof(cand) / sizeof(cand[0]));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  BBW_CUDA(cudaEventCreate(&e0));
+  BBW_CUDA(cudaEventCreate(&e1));
+  auto apply = [&](int c) {
+    b->serial = cand[c].serial;
+    b->grid_factor = cand[c].factor;
+    b->schedule = c;
+    for (auto& k : b->buckets) k.s->grid_stage = std::max(1, int(std::lround(k.grid0 * cand[c].factor)));
+    invalidate_graphs(b);
+  };
+  // trial steps have dt = 0: stage 0 sets res = 0 (a_0 = 0) and every stage
+  // then writes q_out = q_in + b * 0, so the state and the time stay as they
+  // are while the kernels do their full work
+  const double saved_t = b->t;
+  const int64_t saved_steps = b->steps;
+  float best = INFINITY;
+  int best_c = 0;
+  bbw_status st = BBW_OK;
+  for (int c = 0; c < ncand && st == BBW_OK; ++c) {
+    apply(c);
+    st = bbw_batch_step(b, 0.0, 2, 1);  // build both parities' graphs, warm up
+    if (st != BBW_OK) break;
+    if (cudaEventRecord(e0, b->stream) != cudaSuccess) st = fail(BBW_ERR_CUDA, "event record failed");
+    if (st == BBW_OK) st = bbw_batch_step(b, 0.0, steps, 1);
+    if (st == BBW_OK && cudaEventRecord(e1, b->stream) != cudaSuccess) st = fail(BBW_ERR_CUDA, "event record failed");
+    if (st == BBW_OK && cudaEventSynchronize(e1) != cudaSuccess) st = fail(BBW_ERR_CUDA, "event wait failed");
+    float ms = 0.f;
+    if (st == BBW_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) st = fail(BBW_ERR_CUDA, "event timing failed");
+    if (st == BBW_OK && ms < best) {
+      best = ms;
+      best_c = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  apply(st == BBW_OK ? best_c : 0);
+  b->t = saved_t;
+  b->steps = saved_steps;
+  for (auto& k : b->buckets) k.s->t = saved_t;
+  if (st != BBW_OK) return st;
+  if (schedule) *schedule = best_c;
+  if (ms_per_step) *ms_per_step = double(best) / steps;
+  return bbw_batch_sync(b);
 }
 
 bbw_status bbw_batch_sync(bbw_batch* b) {

@@ -24,7 +24,7 @@ import numpy as np
 __all__ = [
     "cube_mesh", "multi_index_points", "sample_at_domain_points",
     "c2_smooth_random", "c2_config_small", "gaussian_pulse", "random_state",
-    "PARITY_CONFIG", "SWEEP_CONFIG",
+    "PARITY_CONFIG", "SWEEP_CONFIG", "BATCH_CONFIG", "batched_instances",
 ]
 
 #: the FP64 parity workload: 4^3 hexes x 6 = 384 tets, N=3, M=1, T=0.5
@@ -32,6 +32,26 @@ PARITY_CONFIG = dict(hexes=4, N=3, M=1, T=0.5, cfl=0.5)
 #: the FP32 throughput workload: 32^3 hexes x 6 = 196,608 tets, N=1..9, M=2
 SWEEP_CONFIG = dict(hexes=32, Ns=tuple(range(1, 10)), M=2, steps=100,
                     source=(0.5, 0.5, 0.5), f0=10.0)
+
+
+#: the batched workload: 256 instances, cube refinements of 2k-60k tets
+#: (7^3 x 6 = 2,058 .. 21^3 x 6 = 55,566), N in 3..7, M = 2, FP32, one seeded
+#: medium and Ricker source position per instance
+BATCH_CONFIG = dict(instances=256, hexes=(7, 21), Ns=(3, 7), M=2, f0=10.0, cfl=0.5)
+
+
+def batched_instances(n: int = BATCH_CONFIG["instances"], seed: int = 0):
+    """Seeded instance descriptions of the batched workload: for each, the
+    cube refinement (hexes per side), the degree N, the seed of its c^2
+    medium (``c2_smooth_random``) and its source position."""
+    rng = np.random.default_rng(seed)
+    lo, hi = BATCH_CONFIG["hexes"]
+    nlo, nhi = BATCH_CONFIG["Ns"]
+    out = []
+    for i in range(n):
+        out.append(dict(hexes=int(rng.integers(lo, hi + 1)), N=int(rng.integers(nlo, nhi + 1)),
+                        c2_seed=int(1000 + i), source=rng.uniform(0.25, 0.75, 3)))
+    return out
 
 
 def cube_mesh(n: int, jitter: float = 0.0, shuffle: bool = False, seed: int = 0,

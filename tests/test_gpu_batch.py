@@ -156,3 +156,25 @@ def test_batch_argument_errors():
     with pytest.raises(B.BBWError, match="BBW_ERR_ARG"):
         b.set_point_source(1, np.array([5.0, 5.0, 5.0]))
     b.close()
+
+
+def test_autotune_keeps_state_and_results():
+    """The autotuner's dt = 0 trial steps leave state and time unchanged, and
+    whichever schedule it keeps gives the solo solvers' results bitwise."""
+    insts = _instances(32, seed=11)
+    b = _batch(insts, 32)
+    b.step(1e-3, 2)
+    before = [b.get_state(i, with_res=False) for i in range(len(insts))]
+    t0 = b.time()
+    sched, ms = b.autotune(2)
+    assert 0 <= sched < 4 and ms > 0
+    assert b.time() == t0
+    for i in range(len(insts)):
+        assert np.array_equal(b.get_state(i), before[i])
+    b.step(1e-3, 3)
+    for i, d in enumerate(insts):
+        s = _solo(d, 32)
+        s.step(1e-3, 5)
+        assert np.array_equal(b.get_state(i), s.get_state()[0]), i
+        s.close()
+    b.close()
