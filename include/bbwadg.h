@@ -254,6 +254,45 @@ bbw_status bbw_wadg_update_noalloc(int N, int M, int precision, int64_t K, const
                                    const void* c2, void* out, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Receivers and the adjoint gradient with respect to c^2.
+ *
+ * The paper has no adjoint; these calls differentiate the discrete LSRK time
+ * stepping of this library exactly (discrete adjoint, up to rounding). The
+ * adjoint stage uses L(tau)^T = -M_w L(-tau) M_w^{-1} (M_w the weight-adjusted
+ * mass of Eq. (4)), so it runs the forward spatial kernel with negated
+ * penalties between element-local mass products.
+ * ------------------------------------------------------------------------ */
+
+/*
+ * Receivers: the pressure is sampled at nrec points xyz [nrec][3] after every
+ * recorded step (point evaluation of the degree-N Bernstein polynomial of the
+ * containing element, lowest element index on shared faces). elems (may be
+ * NULL) receives the elements [nrec]. BBW_ERR_ARG if a point is outside the
+ * mesh. Discards a recorded run.
+ */
+bbw_status bbw_set_receivers(bbw_solver* s, int64_t nrec, const double* xyz, int64_t* elems);
+
+/*
+ * Run nsteps RK steps with step dt from the current state and time (as
+ * bbw_step), keep the state every checkpoint_every steps on the device, and
+ * write the receiver traces after every step to traces [nsteps][nrec] (host,
+ * may be NULL). The run is kept for bbw_adjoint until the next bbw_record or
+ * bbw_set_receivers. Waits for the device.
+ */
+bbw_status bbw_record(bbw_solver* s, double dt, int64_t nsteps, int64_t checkpoint_every, double* traces);
+
+/*
+ * Gradient of J = sum_{n,r} trace_grad[n][r] * trace[n][r] over the recorded
+ * run: grad_c2 [K][M_p] with respect to the c^2 coefficients, grad_q0
+ * [4][K][N_p] with respect to the initial state (either may be NULL). With
+ * trace_grad = trace - data this is the gradient of the L2 misfit
+ * (1/2) sum (trace - data)^2. The c^2 and penalties used are the solver's
+ * current ones, which must be those of the recorded run. Recomputes each
+ * checkpoint segment; device work of the order of three forward runs.
+ */
+bbw_status bbw_adjoint(bbw_solver* s, const double* trace_grad, double* grad_c2, double* grad_q0);
+
+/* ------------------------------------------------------------------------
  * Batches: many independent instances advanced together.
  *
  * The paper solves one mesh at a time and has no batched form; these calls

@@ -169,6 +169,16 @@ class AcousticOracle:
         return own, nbr
 
     def rhs(self, q: np.ndarray, t: float = 0.0) -> np.ndarray:
+        """Semi-discrete right-hand side: velocity rows as they are, the
+        pressure bracket through the weight-adjusted update (Eq. 4)."""
+        out, bracket = self.spatial(q, t)
+        out[0] = self.wadg(bracket)
+        return out
+
+    def spatial(self, q: np.ndarray, t: float = 0.0):
+        """(out, bracket): out[1:4] the velocity right-hand sides, bracket the
+        pressure right-hand side before the weight-adjusted update (volume
+        term, lifted penalty fluxes of Eq. (2) and the point source)."""
         q = np.asarray(q, dtype=np.float64)
         p, u = q[0], q[1:4]
         g = self.geo["grad"]                                 # (K, 4, 3)
@@ -199,8 +209,8 @@ class AcousticOracle:
         if self.source is not None:
             e, vec = self.source[0], self.source[1]
             bracket[e] += self.source_amplitude(t) * vec
-        out[0] = self.wadg(bracket)
-        return out
+        out[0] = 0.0
+        return out, bracket
 
     def wadg(self, r: np.ndarray) -> np.ndarray:
         """M^{-1} M_{c2} r per element (the weight-adjusted update, Eq. 4)."""

@@ -64,6 +64,9 @@ EXPORTS = {
     "bbw_lsrk_coeffs": (_int, [_dp, _dp, _dp]),
     "bbw_wadg_update": (_int, [_int, _int, _int, _i64, _p, _p, _p, _p]),
     "bbw_wadg_update_noalloc": (_int, [_int, _int, _int, _i64, _p, _p, _p, _p]),
+    "bbw_set_receivers": (_int, [_p, _i64, _dp, _i64p]),
+    "bbw_record": (_int, [_p, _d, _i64, _i64, _dp]),
+    "bbw_adjoint": (_int, [_p, _dp, _dp, _dp]),
     "bbw_batch_create": (_int, [_int, _i64p, C.POINTER(_dp), _i64p, C.POINTER(_i64p), _ip, _int, _int, _p,
                                 C.POINTER(_p)]),
     "bbw_batch_destroy": (None, [_p]),
@@ -298,6 +301,32 @@ class Solver:
 
     def sync(self):
         _check(lib().bbw_sync(self._h), "bbw_sync")
+
+    # -- receivers and the adjoint ---------------------------------------------
+    def set_receivers(self, xyz):
+        xyz = _f64(xyz).reshape(-1, 3)
+        el = np.empty(len(xyz), np.int64)
+        _check(lib().bbw_set_receivers(self._h, len(xyz), _ptr(xyz, C.c_double), _ptr(el, C.c_int64)),
+               "bbw_set_receivers")
+        self.nrec = len(xyz)
+        return el
+
+    def record(self, dt: float, nsteps: int, checkpoint_every: int = 1):
+        """Run nsteps steps keeping checkpoints; returns the traces [nsteps][nrec]."""
+        tr = np.empty((nsteps, getattr(self, "nrec", 0)))
+        _check(lib().bbw_record(self._h, dt, nsteps, checkpoint_every,
+                                _ptr(tr, C.c_double) if tr.size else None), "bbw_record")
+        return tr
+
+    def adjoint(self, trace_grad, want_q0: bool = False):
+        """Gradients (grad_c2 [K][Mp], grad_q0 [4][K][Np] or None) of
+        sum(trace_grad * traces) over the recorded run."""
+        g = _f64(trace_grad)
+        gc = np.empty((self.K, self.Mp))
+        gq = np.empty((4, self.K, self.Np)) if want_q0 else None
+        _check(lib().bbw_adjoint(self._h, _ptr(g, C.c_double) if g.size else None, _ptr(gc, C.c_double),
+                                 None if gq is None else _ptr(gq, C.c_double)), "bbw_adjoint")
+        return gc, gq
 
     def time(self):
         t = C.c_double()

@@ -186,8 +186,8 @@ cudaError_t state_to_user(const void* src, void* dst, int64_t K, int Np, int V, 
   return cudaGetLastError();
 }
 
-cudaError_t copy_to_internal(const void* src, int src_prec, void* dst, int dst_prec, int64_t K, int Np, int V,
-                             cudaStream_t s) {
+cudaError_t copy_to_internal_impl(const void* src, int src_prec, void* dst, int dst_prec, int64_t K, int Np,
+                                  int V, cudaStream_t s) {
   if (src_prec == 64)
     return dst_prec == 64 ? state_to_internal<double, double>(src, dst, K, Np, V, s)
                           : state_to_internal<double, float>(src, dst, K, Np, V, s);
@@ -195,8 +195,8 @@ cudaError_t copy_to_internal(const void* src, int src_prec, void* dst, int dst_p
                         : state_to_internal<float, float>(src, dst, K, Np, V, s);
 }
 
-cudaError_t copy_to_user(const void* src, int src_prec, void* dst, int dst_prec, int64_t K, int Np, int V,
-                         cudaStream_t s) {
+cudaError_t copy_to_user_impl(const void* src, int src_prec, void* dst, int dst_prec, int64_t K, int Np, int V,
+                              cudaStream_t s) {
   if (src_prec == 64)
     return dst_prec == 64 ? state_to_user<double, double>(src, dst, K, Np, V, s)
                           : state_to_user<double, float>(src, dst, K, Np, V, s);
@@ -244,6 +244,17 @@ int num_sms() {
 
 namespace bbw {
 void set_last_error(const char* msg) { g_err = msg; }
+cudaError_t copy_to_internal(const void* src, int src_prec, void* dst, int dst_prec, int64_t K, int Np, int V,
+                             cudaStream_t s) {
+  return copy_to_internal_impl(src, src_prec, dst, dst_prec, K, Np, V, s);
+}
+double factorial(int n) { return factd(n); }
+std::vector<std::array<int, 4>> lattice(int n) { return multi_indices(n); }
+bool solve_mass(int n, std::vector<double>& b) { return mass_solve(n, b); }
+cudaError_t copy_to_user(const void* src, int src_prec, void* dst, int dst_prec, int64_t K, int Np, int V,
+                         cudaStream_t s) {
+  return copy_to_user_impl(src, src_prec, dst, dst_prec, K, Np, V, s);
+}
 }  // namespace bbw
 
 // ---------------------------------------------------------------------------
@@ -254,6 +265,7 @@ namespace {
 
 void free_solver(bbw_solver* s) {
   if (!s) return;
+  bbw::free_adjoint(s);
   for (void* p : {s->q[0], s->q[1], s->res, s->d_c2, s->d_geom, static_cast<void*>(s->d_conn), s->d_src,
                   static_cast<void*>(s->d_src_group), static_cast<void*>(s->d_src_slots),
                   static_cast<void*>(s->d_src_wav),
@@ -765,9 +777,9 @@ bbw_status bbw_set_state(bbw_solver* s, const double* q, const double* res, doub
 bbw_status bbw_set_state_device(bbw_solver* s, const void* q, const void* res, int dtype, double t) {
   if (!s || !q) return fail(BBW_ERR_ARG, "NULL argument");
   if (dtype != 32 && dtype != 64) return fail(BBW_ERR_ARG, "dtype must be 32 or 64");
-  BBW_CUDA(copy_to_internal(q, dtype, s->q[s->cur], s->prec, s->K, s->Np, s->V, s->stream));
+  BBW_CUDA(bbw::copy_to_internal(q, dtype, s->q[s->cur], s->prec, s->K, s->Np, s->V, s->stream));
   if (res)
-    BBW_CUDA(copy_to_internal(res, dtype, s->res, s->prec, s->K, s->Np, s->V, s->stream));
+    BBW_CUDA(bbw::copy_to_internal(res, dtype, s->res, s->prec, s->K, s->Np, s->V, s->stream));
   else
     BBW_CUDA(cudaMemsetAsync(s->res, 0, s->nstate_internal() * s->rsz(), s->stream));
   s->t = t;
@@ -794,8 +806,8 @@ bbw_status bbw_get_state(bbw_solver* s, double* q, double* res, double* t) {
 bbw_status bbw_get_state_device(bbw_solver* s, void* q, void* res, int dtype) {
   if (!s) return fail(BBW_ERR_ARG, "solver is NULL");
   if (dtype != 32 && dtype != 64) return fail(BBW_ERR_ARG, "dtype must be 32 or 64");
-  if (q) BBW_CUDA(copy_to_user(s->q[s->cur], s->prec, q, dtype, s->K, s->Np, s->V, s->stream));
-  if (res) BBW_CUDA(copy_to_user(s->res, s->prec, res, dtype, s->K, s->Np, s->V, s->stream));
+  if (q) BBW_CUDA(bbw::copy_to_user(s->q[s->cur], s->prec, q, dtype, s->K, s->Np, s->V, s->stream));
+  if (res) BBW_CUDA(bbw::copy_to_user(s->res, s->prec, res, dtype, s->K, s->Np, s->V, s->stream));
   return BBW_OK;
 }
 

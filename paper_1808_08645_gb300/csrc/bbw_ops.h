@@ -25,6 +25,8 @@ struct KernelOps {
   cudaError_t (*launch_wadg)(int M, bool dbl, const void* params, int grid, cudaStream_t s);
   // launch shape: lanes per group, elements per group, groups per CTA
   void (*launch_shape)(int M, bool dbl, int* team, int* group_width, int* groups_per_cta);
+  // launch the spatial operator alone (StageParams, output in qout)
+  cudaError_t (*launch_spatial)(int M, bool dbl, const void* params, int grid, cudaStream_t s);
 };
 
 const KernelOps& ops_n1();

@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 
+#include <array>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -36,6 +37,8 @@ inline bbw_status fail(bbw_status s, const std::string& msg) {
   } while (0)
 
 }  // namespace bbw
+
+struct AdjointData;  // bbw_adjoint.cu
 
 struct bbw_solver {
   int N = 0, M = 0, prec = 32;
@@ -71,6 +74,7 @@ struct bbw_solver {
   double tau_p = 1.0, tau_u = 1.0;
   int64_t src_elem = -1;
   double f0 = 0.0, t0 = 0.0;
+  AdjointData* adj = nullptr;  // receivers, recorded run, adjoint buffers (bbw_adjoint.cu)
   int V = 1;        // elements per group of the kernel's layout
   int64_t G = 0;   // number of groups, ceil(K / V)
   size_t rsz() const { return prec == 64 ? 8 : 4; }
@@ -80,6 +84,21 @@ struct bbw_solver {
 
 namespace bbw {
 
+// State layout conversions on the device: the ABI's [4][K][Np] ("user")
+// and the kernels' grouped [G][4][Np][V] ("internal"), each in FP32 or FP64
+// (prec 32 | 64); padding entries of the internal layout are set to zero.
+cudaError_t copy_to_internal(const void* src, int src_prec, void* dst, int dst_prec, int64_t K, int Np, int V,
+                             cudaStream_t s);
+cudaError_t copy_to_user(const void* src, int src_prec, void* dst, int dst_prec, int64_t K, int Np, int V,
+                         cudaStream_t s);
+// n!, the degree-n multi-indices (alpha_0..alpha_3) in the library order, and
+// a solve with the normalised degree-n Bernstein mass matrix (in place;
+// false if the factorisation fails).
+double factorial(int n);
+std::vector<std::array<int, 4>> lattice(int n);
+bool solve_mass(int n, std::vector<double>& b);
+// Release the adjoint data of a solver (bbw_adjoint.cu); no-op without any.
+void free_adjoint(bbw_solver* s);
 // Grow the solver's pinned staging buffer to at least bytes.
 bbw_status ensure_pinned(bbw_solver* s, size_t bytes);
 // Wait for the solver's stream and surface the device status word.

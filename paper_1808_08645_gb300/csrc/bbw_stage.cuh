@@ -482,7 +482,11 @@ __device__ __noinline__ double stage_wavelet(const StageParams<real>& P, int sd)
   return ricker_wavelet(t, P.src_wav[2 * sd], P.src_wav[2 * sd + 1]);
 }
 
-template <int N, int M, typename real, int T, int V, int GC>
+// SP = false: one LSRK stage (above). SP = true: the spatial operator alone,
+// for the adjoint: q_out receives [rhs_p before the weight-adjusted update
+// (plus the point sources), rhs_u, rhs_v, rhs_w]; res, a, b and dt are not
+// used.
+template <int N, int M, typename real, int T, int V, int GC, bool SP = false>
 __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P) {
   using C = StageCfg<N, M, real, T, V, GC>;
   using Tab = typename C::Tab;
@@ -764,7 +768,8 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
         const int i = t + r * T;
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-          rold[r][c] = (read_res && i < Np) ? vld<real, V>(resg + size_t((1 + c) * Np + i) * V) : vzero<real, V>();
+          rold[r][c] = (!SP && read_res && i < Np) ? vld<real, V>(resg + size_t((1 + c) * Np + i) * V)
+                                                   : vzero<real, V>();
       }
 #pragma unroll
       for (int r = 0; r < C::RMAX; ++r) {
@@ -795,13 +800,17 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
           }
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            vt rn = vmuls(P.dt, rhs[c]);
-            vfmas(rn, P.a, rold[r][c]);
-            vst(resg + size_t((1 + c) * Np + i) * V, rn);
-            const vt qn = vaxpy(vld<real, V>(Q + ((1 + c) * Np + i) * V), P.b, rn);
-            vst(qog + size_t((1 + c) * Np + i) * V, qn);
+            if constexpr (SP) {
+              vst(qog + size_t((1 + c) * Np + i) * V, rhs[c]);
+            } else {
+              vt rn = vmuls(P.dt, rhs[c]);
+              vfmas(rn, P.a, rold[r][c]);
+              vst(resg + size_t((1 + c) * Np + i) * V, rn);
+              const vt qn = vaxpy(vld<real, V>(Q + ((1 + c) * Np + i) * V), P.b, rn);
+              vst(qog + size_t((1 + c) * Np + i) * V, qn);
 #pragma unroll
-            for (int v = 0; v < V; ++v) bad |= !isfinite(qn.get(v));
+              for (int v = 0; v < V; ++v) bad |= !isfinite(qn.get(v));
+            }
           }
           ap[r] = ad;
         }
@@ -809,6 +818,26 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
     }
     team_sync<T>();
 
+    if constexpr (SP) {  // the p right-hand side before the weight-adjusted update
+      bool any_src = false;
+#pragma unroll
+      for (int l = 0; l < V; ++l) any_src |= CS[4 * V + l] >= 0;
+#pragma unroll
+      for (int r = 0; r < C::RMAX; ++r) {
+        const int i = t + r * T;
+        if (i < Np) {
+          vt v = ap[r];
+          if (any_src) {
+#pragma unroll
+            for (int l = 0; l < V; ++l) {
+              const int sd = CS[4 * V + l];
+              if (sd >= 0) v.set(l, v.get(l) + AMP[l] * P.src_vec[size_t(sd) * Np + i]);
+            }
+          }
+          vst(qog + size_t(i) * V, v);
+        }
+      }
+    } else {
     // ---- W: weight-adjusted update of the p right-hand side, then its RK update ----
     {
       real* A = S;
@@ -858,6 +887,7 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
           for (int v = 0; v < V; ++v) bad |= !isfinite(qn.get(v));
         }
       }
+    }
     }
     team_sync<T>();  // the next group reuses this team's shared region
   }

@@ -30,6 +30,10 @@ constexpr auto stage_fn() {
   return stage_kernel<kN, M, real, Shape<real>::T, Shape<real>::V, kGC<M, real>>;
 }
 template <int M, typename real>
+constexpr auto spatial_fn() {
+  return stage_kernel<kN, M, real, Shape<real>::T, Shape<real>::V, kGC<M, real>, true>;
+}
+template <int M, typename real>
 constexpr auto wadg_fn() {
   return wadg_kernel<kN, M, real, Shape<real>::T, Shape<real>::V, kGC<M, real>>;
 }
@@ -84,6 +88,8 @@ cudaError_t prepare(int M, bool dbl, int* per_sm_stage, int* per_sm_wadg) {
     if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute(kw, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (err != cudaSuccess) return err;
+    err = cudaFuncSetAttribute(spatial_fn<MM, real>(), cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (err != cudaSuccess) return err;
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm_stage, ks, C::THREADS, C::SMEM);
     if (err != cudaSuccess) return err;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm_wadg, kw, C::THREADS, C::SMEM);
@@ -94,6 +100,15 @@ cudaError_t launch_stage(int M, bool dbl, const void* params, int grid, cudaStre
   return dispatch(M, dbl, [&]<int MM, typename real>() {
     using C = Cfg<MM, real>;
     stage_fn<MM, real>()<<<grid, C::THREADS, C::SMEM, s>>>(
+        *static_cast<const StageParams<real>*>(params));
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_spatial(int M, bool dbl, const void* params, int grid, cudaStream_t s) {
+  return dispatch(M, dbl, [&]<int MM, typename real>() {
+    using C = Cfg<MM, real>;
+    spatial_fn<MM, real>()<<<grid, C::THREADS, C::SMEM, s>>>(
         *static_cast<const StageParams<real>*>(params));
     return cudaGetLastError();
   });
@@ -113,8 +128,8 @@ cudaError_t launch_wadg(int M, bool dbl, const void* params, int grid, cudaStrea
 #define BBW_CAT2(a, b) a##b
 #define BBW_CAT(a, b) BBW_CAT2(a, b)
 const KernelOps& BBW_CAT(ops_n, BBW_N)() {
-  static const KernelOps ops = {&tables_size, &build,        &face_maps,   &prepare,
-                                &launch_stage, &launch_wadg, &launch_shape};
+  static const KernelOps ops = {&tables_size, &build,       &face_maps,   &prepare,     &launch_stage,
+                                &launch_wadg, &launch_shape, &launch_spatial};
   return ops;
 }
 

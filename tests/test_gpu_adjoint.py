@@ -1,0 +1,104 @@
+"""GPU receiver-misfit gradient (bbw_set_receivers / bbw_record / bbw_adjoint)
+against the FP64 oracle adjoint and against finite differences of the GPU
+forward run; checkpoint spacing does not change the result."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import adjoint as adj
+from oracle import bernstein as bb
+from oracle.acoustic import AcousticOracle
+from paper_1808_08645_gb300 import binding as B
+from paper_1808_08645_gb300 import inputs
+from parity_util import rel_l2, rounded
+
+pytestmark = pytest.mark.gpu
+
+XR = np.array([[0.3, 0.4, 0.9], [0.7, 0.2, 0.5], [0.5, 0.5, 0.0], [0.15, 0.8, 0.6]])
+SRC = np.array([0.5, 0.5, 0.5])
+
+
+def _case(hexes, N, M, prec, seed=0, jitter=0.1):
+    vxyz, etov = inputs.cube_mesh(hexes, jitter=jitter, shuffle=True, seed=seed)
+    K = len(etov)
+    rng = np.random.default_rng(seed + 7)
+    c2 = rounded(rng.uniform(0.5, 2.0, (K, bb.np_count(M))), prec)
+    q0 = rounded(rng.standard_normal((4, K, bb.np_count(N))) * 0.1, prec)
+    return vxyz, etov, c2, q0, rng
+
+
+def _gpu(vxyz, etov, N, M, prec, c2, q0, source=True):
+    s = B.Solver(vxyz, etov, N, M, prec)
+    s.set_c2(c2)
+    s.set_state(q0)
+    if source:
+        s.set_point_source(SRC, f0=10.0, t0=0.05)
+    s.set_receivers(XR)
+    return s
+
+
+@pytest.mark.parametrize("prec,tol", [(64, 1e-9), (32, 2e-3)])
+@pytest.mark.parametrize("N,M", [(2, 1), (4, 2)])
+def test_gradient_matches_oracle_adjoint(N, M, prec, tol):
+    vxyz, etov, c2, q0, rng = _case(1, N, M, prec, seed=N)
+    dt, nsteps = 0.01, 3
+    s = _gpu(vxyz, etov, N, M, prec, c2, q0)
+    tr = s.record(dt, nsteps, checkpoint_every=2)
+    o = AcousticOracle(vxyz, etov, N, M, c2)
+    o.set_point_source(SRC, f0=10.0, t0=0.05)
+    R = adj.receiver_matrix(o, XR)
+    tro, _ = adj.record(o, q0, dt, nsteps, R)
+    assert rel_l2(tr, tro) <= (1e-11 if prec == 64 else 1e-4)
+    g = rng.standard_normal(tr.shape)
+    gc, gq = s.adjoint(g, want_q0=True)
+    gco, gqo = adj.misfit_gradient(o, q0, dt, nsteps, R, g)
+    assert rel_l2(gc, gco) <= tol
+    assert rel_l2(gq, gqo) <= tol
+    s.close()
+
+
+def test_checkpoint_spacing_does_not_change_the_gradient():
+    N, M = 3, 2
+    vxyz, etov, c2, q0, rng = _case(2, N, M, 32, seed=5)
+    g = rng.standard_normal((7, len(XR)))
+    out = []
+    for every in (1, 3, 7):
+        s = _gpu(vxyz, etov, N, M, 32, c2, q0)
+        s.record(2e-3, 7, checkpoint_every=every)
+        out.append(s.adjoint(g, want_q0=True))
+        s.close()
+    for gc, gq in out[1:]:
+        assert np.array_equal(gc, out[0][0]) and np.array_equal(gq, out[0][1])
+
+
+def test_gradient_matches_gpu_finite_differences():
+    """FP64 on a 2^3 x 6 mesh, N = 3, M = 2, 12 steps: directional derivative
+    of the L2 misfit against central differences of GPU forward runs."""
+    N, M = 3, 2
+    vxyz, etov, c2, q0, rng = _case(2, N, M, 64, seed=11)
+    dt, nsteps = 2e-3, 12
+    data = rng.standard_normal((nsteps, len(XR))) * 1e-3
+
+    def misfit(c2v):
+        s = _gpu(vxyz, etov, N, M, 64, c2v, q0)
+        tr = s.record(dt, nsteps, checkpoint_every=5)
+        return 0.5 * np.sum((tr - data) ** 2), tr, s
+
+    J0, tr, s = misfit(c2)
+    gc, _ = s.adjoint(tr - data)
+    s.close()
+    d = rng.uniform(-1.0, 1.0, c2.shape) * 0.1
+    eps = 1e-6
+    fd = (misfit(c2 + eps * d)[0] - misfit(c2 - eps * d)[0]) / (2 * eps)
+    assert abs(fd - np.sum(gc * d)) <= 1e-6 * abs(fd)
+
+
+def test_adjoint_needs_a_recorded_run():
+    vxyz, etov, c2, q0, _ = _case(1, 2, 1, 32)
+    s = _gpu(vxyz, etov, 2, 1, 32, c2, q0)
+    with pytest.raises(B.BBWError, match="BBW_ERR_ARG"):
+        s.adjoint(np.zeros((1, len(XR))))
+    with pytest.raises(B.BBWError, match="BBW_ERR_ARG"):
+        s.set_receivers(np.array([[3.0, 0.5, 0.5]]))
+    s.close()
