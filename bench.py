@@ -506,6 +506,79 @@ def run_batched(args):
     }
 
 
+def run_adjoint(args):
+    """Receiver-misfit gradient with respect to c^2 on the adjoint workload:
+    forward steps alone, the recorded forward run (checkpoints, traces) and
+    the adjoint sweep, timed on the solver's stream."""
+    import torch
+
+    from paper_1808_08645_gb300 import binding as B
+    from paper_1808_08645_gb300 import build as libbuild
+
+    libbuild.build()
+    cfg = inputs.ADJOINT_CONFIG
+    N, M = cfg["N"], cfg["M"]
+    nsteps = args.adjoint_steps
+    vxyz, etov = inputs.cube_mesh(cfg["hexes"])
+    K = len(etov)
+    c2_true = inputs.sample_at_domain_points(vxyz, etov, M, inputs.c2_smooth_random(seed=cfg["true_seed"]))
+    c2 = inputs.sample_at_domain_points(vxyz, etov, M, inputs.c2_smooth_random(seed=cfg["model_seed"]))
+    rec = inputs.top_face_receivers()
+    stream = torch.cuda.Stream()
+    s = B.Solver(vxyz, etov, N, M, B.F32, stream=stream.cuda_stream)
+    s.set_point_source(np.array(cfg["source"]), f0=cfg["f0"])
+    s.set_receivers(rec)
+    q0 = np.zeros((4, K, np3(N)))
+    s.set_c2(c2_true)
+    s.set_state(q0)
+    dt = s.cfl_dt(cfg["cfl"])
+    s.set_c2(c2)
+    dt = min(dt, s.cfl_dt(cfg["cfl"]))
+    every = max(1, int(round(np.sqrt(nsteps))))
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t, out
+
+    # data: traces of the true medium
+    s.set_c2(c2_true)
+    s.set_state(q0)
+    data = s.record(dt, nsteps, every)
+    # warm-up, then forward alone
+    s.set_c2(c2)
+    s.set_state(q0)
+    s.step(dt, 3)
+    s.set_state(q0)
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()
+    t_fwd, _ = timed(lambda: s.step(dt, nsteps))
+    s.set_state(q0)
+    t_rec, tr = timed(lambda: s.record(dt, nsteps, every))
+    resid = tr - data
+    t_adj, (gc, _) = timed(lambda: s.adjoint(resid))
+    clocks = clk.stop()
+    s.close()
+    dofs = 4 * K * np3(N) * 5 * nsteps
+    return {
+        "metric": "receiver-misfit gradient w.r.t. c2: time relative to the forward run", "impl": "ours",
+        "workload": "adjoint", "value": (t_rec + t_adj) / t_fwd, "unit": "x forward time", "n_gpus": 1,
+        "steps": nsteps, "warmup": 3, "ms_per_step": 1e3 * (t_rec + t_adj) / nsteps, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{cfg['hexes']}^3 hexes x 6 = {K} tets, N={N}, M={M}, {len(rec)} receivers on "
+                               f"the top face, {nsteps} steps, checkpoints every {every} steps, Ricker source "
+                               f"at {tuple(cfg['source'])}, data from the seed-{cfg['true_seed']} medium, "
+                               f"model the seed-{cfg['model_seed']} medium", "dt": dt},
+        "forward_s": t_fwd, "record_s": t_rec, "adjoint_s": t_adj,
+        "forward_dof_updates_per_s": dofs / t_fwd, "adjoint_dof_updates_per_s": dofs / t_adj,
+        "misfit": 0.5 * float(np.sum(resid ** 2)), "grad_norm": float(np.linalg.norm(gc)),
+        "timing": "wall clock around each call with device synchronisation (each call ends with a device wait)",
+        "clocks": clocks,
+    }
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -519,12 +592,17 @@ def main():
     ap.add_argument("--cpu-reps", type=int, default=15)
     ap.add_argument("--ref-hexes", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["sweep", "batched"], default="sweep")
+    ap.add_argument("--workload", choices=["sweep", "batched", "adjoint"], default="sweep")
+    ap.add_argument("--adjoint-steps", type=int, default=inputs.ADJOINT_CONFIG["steps"])
     ap.add_argument("--instances", type=int, default=inputs.BATCH_CONFIG["instances"])
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")
-    if args.workload == "batched":
+    if args.workload == "adjoint":
+        out = run_adjoint(args) if args.impl == "ours" else {
+            "impl": "reference", "workload": "adjoint",
+            "unavailable": "the FP64 oracle adjoint is dense (small meshes only); its check is in the tests"}
+    elif args.workload == "batched":
         out = run_batched(args) if args.impl == "ours" else {
             "impl": "reference", "workload": "batched",
             "unavailable": "the batched form has no oracle counterpart; its reference is plain one-by-one "

@@ -27,6 +27,12 @@
 // A recorded run keeps the state every C steps (checkpoints) and the start
 // time of every step; the backward pass recomputes one checkpoint segment at
 // a time (the states at its steps, then the five stage inputs of each step).
+//
+// The element-local mass products are plain dense matrix products over all
+// elements at once ([N_p x N_p] times [N_p x 4K], and the M_p weighted masses
+// as one strided batch), done by cuBLAS in the solver's precision (no
+// reduced-precision tensor-op modes).
+#include <cublas_v2.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -79,6 +85,8 @@ struct AdjointData {
   void* rs = nullptr;
   std::vector<void*> seg;
   double* d_g = nullptr;  // [nsteps][nrec] trace cotangents
+  void* u = nullptr;      // [Mp][K][Np] weighted-mass products T_beta v_p
+  cublasHandle_t blas = nullptr;
 };
 
 namespace {
@@ -106,24 +114,6 @@ __global__ void receiver_adjoint_kernel(real* __restrict__ qb, int64_t K, int64_
     for (int64_t r = 0; r < nrec; ++r) qb[el[r] * Np + i] += real(g[r]) * vec[r * Np + i];
 }
 
-// out[e][i] (+)= alpha scale[e] sum_j A[i][j] in[e][j], over nf fields of [nf][K][Np]
-template <typename real>
-__global__ void dense_kernel(const real* __restrict__ A, int Np, const real* __restrict__ in, real* __restrict__ out,
-                             int64_t K, int nf, const real* __restrict__ scale, real alpha, bool accumulate) {
-  const size_t n = size_t(nf) * K * Np;
-  for (size_t x = blockIdx.x * size_t(blockDim.x) + threadIdx.x; x < n; x += size_t(gridDim.x) * blockDim.x) {
-    const int i = int(x % Np);
-    const size_t row = x / Np;  // field * K + e
-    const int64_t e = int64_t(row % K);
-    const real* a = A + size_t(i) * Np;
-    const real* u = in + row * Np;
-    real acc = 0;
-    for (int j = 0; j < Np; ++j) acc += a[j] * u[j];
-    acc *= alpha * (scale ? scale[e] : real(1));
-    out[x] = accumulate ? out[x] + acc : acc;
-  }
-}
-
 // x = a x + b y (elementwise)
 template <typename real>
 __global__ void axpby_kernel(real* __restrict__ x, const real* __restrict__ y, real a, real b, size_t n) {
@@ -131,34 +121,59 @@ __global__ void axpby_kernel(real* __restrict__ x, const real* __restrict__ y, r
     x[i] = a * x[i] + (y ? b * y[i] : real(0));
 }
 
-// x[e][i] *= s[e]
+// x[row][i] *= s[row % K] over nrows rows of Np ([f][K][Np] layouts)
 template <typename real>
-__global__ void scale_rows_kernel(real* __restrict__ x, const real* __restrict__ s, int64_t K, int Np) {
-  const size_t n = size_t(K) * Np;
+__global__ void scale_rows_kernel(real* __restrict__ x, const real* __restrict__ s, int64_t nrows, int64_t K, int Np) {
+  const size_t n = size_t(nrows) * Np;
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
-    x[i] *= s[i / Np];
+    x[i] *= s[(i / Np) % K];
 }
 
-// gc[e][b] += alpha yt[e]^T T_b v[e]
+// gc[e][b] += alpha sum_i yt[e][i] u[b][e][i]   (u_b = T_b v_p)
 template <typename real>
-__global__ void grad_c2_kernel(const real* __restrict__ T, const real* __restrict__ yt, const real* __restrict__ v,
-                               real* __restrict__ gc, int64_t K, int Mp, int Np, real alpha) {
+__global__ void grad_c2_kernel(const real* __restrict__ u, const real* __restrict__ yt, real* __restrict__ gc,
+                               int64_t K, int Mp, int Np, real alpha) {
   const size_t n = size_t(K) * Mp;
   for (size_t x = blockIdx.x * size_t(blockDim.x) + threadIdx.x; x < n; x += size_t(gridDim.x) * blockDim.x) {
     const int b = int(x % Mp);
     const int64_t e = int64_t(x / Mp);
-    const real* tb = T + size_t(b) * Np * Np;
+    const real* ub = u + (size_t(b) * K + e) * Np;
     const real* ye = yt + size_t(e) * Np;
-    const real* ve = v + size_t(e) * Np;
     real acc = 0;
-    for (int i = 0; i < Np; ++i) {
-      real s = 0;
-      for (int j = 0; j < Np; ++j) s += tb[size_t(i) * Np + j] * ve[j];
-      acc += ye[i] * s;
-    }
+    for (int i = 0; i < Np; ++i) acc += ye[i] * ub[i];
     gc[x] += alpha * acc;
   }
 }
+
+// Y = alpha A X + beta Y for row-major A [Np][Np] and ncols element rows of
+// Np values (X, Y: [ncols][Np], i.e. column-major Np x ncols).
+cublasStatus_t gemm(cublasHandle_t h, const float* A, int Np, const float* X, float* Y, int64_t ncols, float alpha,
+                    float beta) {
+  return cublasSgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, Np, int(ncols), Np, &alpha, A, Np, X, Np, &beta, Y, Np);
+}
+cublasStatus_t gemm(cublasHandle_t h, const double* A, int Np, const double* X, double* Y, int64_t ncols,
+                    double alpha, double beta) {
+  return cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, Np, int(ncols), Np, &alpha, A, Np, X, Np, &beta, Y, Np);
+}
+// U_b = T_b X for b < Mp (T: [Mp][Np][Np] row-major; U: [Mp][ncols][Np])
+cublasStatus_t gemm_batch(cublasHandle_t h, const float* T, int Np, const float* X, float* U, int64_t ncols, int Mp) {
+  const float one = 1.f, zero = 0.f;
+  return cublasSgemmStridedBatched(h, CUBLAS_OP_T, CUBLAS_OP_N, Np, int(ncols), Np, &one, T, Np,
+                                   static_cast<long long>(Np) * Np, X, Np, 0, &zero, U, Np, static_cast<long long>(Np) * ncols, Mp);
+}
+cublasStatus_t gemm_batch(cublasHandle_t h, const double* T, int Np, const double* X, double* U, int64_t ncols,
+                          int Mp) {
+  const double one = 1.0, zero = 0.0;
+  return cublasDgemmStridedBatched(h, CUBLAS_OP_T, CUBLAS_OP_N, Np, int(ncols), Np, &one, T, Np,
+                                   static_cast<long long>(Np) * Np, X, Np, 0, &zero, U, Np, static_cast<long long>(Np) * ncols, Mp);
+}
+
+#define BBW_BLAS(call)                                                                        \
+  do {                                                                                        \
+    const cublasStatus_t b_ = (call);                                                         \
+    if (b_ != CUBLAS_STATUS_SUCCESS)                                                          \
+      return fail(BBW_ERR_CUDA, std::string(#call) + ": cuBLAS status " + std::to_string(int(b_))); \
+  } while (0)
 
 int blocks_for(size_t n) { return int(std::min<size_t>((n + 255) / 256, 152 * 32)); }
 
@@ -345,11 +360,11 @@ bbw_status adjoint_stage(bbw_solver* s, AdjointData* a, const void* qin, int sta
   // rt = rb + b_s qb (in rb)
   axpby_kernel<real><<<blocks_for(4 * nf), 256, 0, st>>>(rb, qb, real(1), real(cb[stage]), 4 * nf);
   // yt = M^{-1} rt_p; y_p = P~(c2 . yt) / |D|; y_u = M^{-1} rt_u / |D|
-  dense_kernel<real><<<blocks_for(nf), 256, 0, st>>>(minv, Np, rb, yt, K, 1, nullptr, real(1), false);
+  BBW_BLAS(gemm(a->blas, minv, Np, rb, yt, K, real(1), real(0)));
   bbw_status r = wadg_user<real>(s, yt, a->d_c2u, y);
   if (r != BBW_OK) return r;
-  scale_rows_kernel<real><<<blocks_for(nf), 256, 0, st>>>(y, ivol, K, Np);
-  dense_kernel<real><<<blocks_for(3 * nf), 256, 0, st>>>(minv, Np, rb + nf, y + nf, K, 3, ivol, real(1), false);
+  BBW_BLAS(gemm(a->blas, minv, Np, rb + nf, y + nf, 3 * K, real(1), real(0)));
+  scale_rows_kernel<real><<<blocks_for(4 * nf), 256, 0, st>>>(y, ivol, 4 * K, K, Np);
   BBW_CUDA(cudaGetLastError());
   // z = A_{-tau}(y), v = A_tau(q_s) + sources
   BBW_CUDA(bbw::copy_to_internal(y, p, a->yi, p, K, Np, V, st));
@@ -359,10 +374,12 @@ bbw_status adjoint_stage(bbw_solver* s, AdjointData* a, const void* qin, int sta
   r = spatial<real>(s, qin, a->zi, 1.0, true, stage, dt, t);
   if (r != BBW_OK) return r;
   BBW_CUDA(bbw::copy_to_user(a->zi, p, v, p, K, Np, V, st));
-  // qb -= dt |D| M z; gc += dt yt^T T v_p; rb = a_s rt
-  dense_kernel<real><<<blocks_for(4 * nf), 256, 0, st>>>(mass, Np, z, qb, K, 4, vol, real(-dt), true);
-  grad_c2_kernel<real><<<blocks_for(size_t(K) * Mp), 256, 0, st>>>(
-      static_cast<const real*>(a->d_tw), yt, v, static_cast<real*>(a->gc), K, Mp, Np, real(dt));
+  // qb -= dt M (|D| z); gc += dt yt^T T_b v_p; rb = a_s rt
+  scale_rows_kernel<real><<<blocks_for(4 * nf), 256, 0, st>>>(z, vol, 4 * K, K, Np);
+  BBW_BLAS(gemm(a->blas, mass, Np, z, qb, 4 * K, real(-dt), real(1)));
+  BBW_BLAS(gemm_batch(a->blas, static_cast<const real*>(a->d_tw), Np, v, static_cast<real*>(a->u), K, Mp));
+  grad_c2_kernel<real><<<blocks_for(size_t(K) * Mp), 256, 0, st>>>(static_cast<const real*>(a->u), yt,
+                                                                     static_cast<real*>(a->gc), K, Mp, Np, real(dt));
   axpby_kernel<real><<<blocks_for(4 * nf), 256, 0, st>>>(rb, nullptr, real(ca[stage]), real(0), 4 * nf);
   BBW_CUDA(cudaGetLastError());
   return BBW_OK;
@@ -424,6 +441,13 @@ bbw_status adjoint(bbw_solver* s, const double* g, double* grad_c2, double* grad
   }
   st = dalloc(&a->yt, nf * sizeof(real));
   if (st == BBW_OK) st = dalloc(&a->gc, size_t(K) * Mp * sizeof(real));
+  if (st == BBW_OK) st = dalloc(&a->u, size_t(Mp) * nf * sizeof(real));
+  if (st != BBW_OK) return st;
+  if (!a->blas) {
+    BBW_BLAS(cublasCreate(&a->blas));
+    BBW_BLAS(cublasSetMathMode(a->blas, CUBLAS_PEDANTIC_MATH));
+  }
+  BBW_BLAS(cublasSetStream(a->blas, s->stream));
   if (st == BBW_OK) st = upload_real<real>(s->c2, &a->d_c2u);  // the current c^2 of the solver
   if (st != BBW_OK) return st;
   a->seg.resize(size_t(a->every), nullptr);
@@ -506,8 +530,9 @@ void free_adjoint(bbw_solver* s) {
   free_run(a);
   for (void* p : {static_cast<void*>(a->d_rec_elem), a->d_rec_vec, a->d_minv, a->d_mass, a->d_tw, a->d_vol, a->d_ivol,
                   a->d_c2u, a->qb, a->rb, a->y, a->z, a->v, a->yt, a->gc, a->yi, a->zi, a->rs, a->qs[0], a->qs[1],
-                  a->qs[2], a->qs[3], a->qs[4], static_cast<void*>(a->d_g)})
+                  a->qs[2], a->qs[3], a->qs[4], static_cast<void*>(a->d_g), a->u})
     if (p) cudaFree(p);
+  if (a->blas) cublasDestroy(a->blas);
   delete a;
   s->adj = nullptr;
 }

@@ -24,7 +24,8 @@ import numpy as np
 __all__ = [
     "cube_mesh", "multi_index_points", "sample_at_domain_points",
     "c2_smooth_random", "c2_config_small", "gaussian_pulse", "random_state",
-    "PARITY_CONFIG", "SWEEP_CONFIG", "BATCH_CONFIG", "batched_instances",
+    "PARITY_CONFIG", "SWEEP_CONFIG", "BATCH_CONFIG", "batched_instances", "ADJOINT_CONFIG",
+    "top_face_receivers",
 ]
 
 #: the FP64 parity workload: 4^3 hexes x 6 = 384 tets, N=3, M=1, T=0.5
@@ -38,6 +39,20 @@ SWEEP_CONFIG = dict(hexes=32, Ns=tuple(range(1, 10)), M=2, steps=100,
 #: (7^3 x 6 = 2,058 .. 21^3 x 6 = 55,566), N in 3..7, M = 2, FP32, one seeded
 #: medium and Ricker source position per instance
 BATCH_CONFIG = dict(instances=256, hexes=(7, 21), Ns=(3, 7), M=2, f0=10.0, cfl=0.5)
+
+
+#: the adjoint workload: 16^3 hexes x 6 = 24,576 tets, N = 5, M = 2, FP32,
+#: 64 receivers on the top face (8 x 8 grid at z = 1), 2000 steps, data from
+#: the medium of seed 0, model medium of seed 1, Ricker source at (0.5, 0.5, 0.7)
+ADJOINT_CONFIG = dict(hexes=16, N=5, M=2, steps=2000, receivers=8, source=(0.5, 0.5, 0.7), f0=10.0,
+                      cfl=0.5, true_seed=0, model_seed=1)
+
+
+def top_face_receivers(n: int = ADJOINT_CONFIG["receivers"]) -> np.ndarray:
+    """n x n receiver points at the cell centres of a uniform grid on z = 1."""
+    x = (np.arange(n) + 0.5) / n
+    X, Y = np.meshgrid(x, x, indexing="ij")
+    return np.stack([X.ravel(), Y.ravel(), np.ones(n * n)], axis=1)
 
 
 def batched_instances(n: int = BATCH_CONFIG["instances"], seed: int = 0):

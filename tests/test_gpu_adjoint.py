@@ -102,3 +102,27 @@ def test_adjoint_needs_a_recorded_run():
     with pytest.raises(B.BBWError, match="BBW_ERR_ARG"):
         s.set_receivers(np.array([[3.0, 0.5, 0.5]]))
     s.close()
+
+
+def test_autograd_function_gradcheck_and_backward():
+    """torch.autograd.gradcheck (FP64 solver, double tensors) and
+    loss.backward() against bbw_adjoint."""
+    import torch
+
+    from paper_1808_08645_gb300.autograd import receiver_traces
+
+    N, M = 2, 1
+    vxyz, etov, c2, q0, rng = _case(1, N, M, 64, seed=21)
+    s = _gpu(vxyz, etov, N, M, 64, c2, q0)
+    c2t = torch.tensor(c2, dtype=torch.float64, requires_grad=True)
+    assert torch.autograd.gradcheck(lambda c: receiver_traces(s, c, q0, 0.01, 3, 2), (c2t,),
+                                    eps=1e-6, atol=1e-8, rtol=1e-5)
+    data = torch.tensor(rng.standard_normal((3, len(XR))) * 1e-2)
+    loss = 0.5 * ((receiver_traces(s, c2t, q0, 0.01, 3, 2) - data) ** 2).sum()
+    loss.backward()
+    s.set_c2(c2)  # the same run again
+    s.set_state(q0)
+    tr = s.record(0.01, 3, 2)
+    gc, _ = s.adjoint(tr - data.numpy())
+    assert np.allclose(c2t.grad.numpy(), gc, rtol=1e-12, atol=1e-14)
+    s.close()
