@@ -254,8 +254,15 @@ class Solver:
     def set_state_device(self, q, res=None, dtype: int = F32, t: float = 0.0):
         _check(lib().bbw_set_state_device(self._h, _dev(q), _dev(res), dtype, t), "bbw_set_state_device")
 
-    def get_state(self, with_res: bool = False):
-        q = np.empty((4, self.K, self.Np))
+    def get_state(self, with_res: bool = False, out=None):
+        """(q, t) or (q, res, t); ``out`` (a C-contiguous float64 array of
+        shape (4, K, Np), e.g. a view of pinned memory) receives q if given."""
+        if out is not None:
+            if out.dtype != np.float64 or not out.flags.c_contiguous or out.size != 4 * self.K * self.Np:
+                raise ValueError("out must be a C-contiguous float64 array of 4*K*Np values")
+            q = out.reshape(4, self.K, self.Np)
+        else:
+            q = np.empty((4, self.K, self.Np))
         r = np.empty((4, self.K, self.Np)) if with_res else None
         t = C.c_double()
         _check(lib().bbw_get_state(self._h, _ptr(q, C.c_double),

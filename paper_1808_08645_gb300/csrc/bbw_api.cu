@@ -268,7 +268,7 @@ void free_solver(bbw_solver* s) {
   bbw::free_adjoint(s);
   for (void* p : {s->q[0], s->q[1], s->res, s->d_c2, s->d_geom, static_cast<void*>(s->d_conn), s->d_src,
                   static_cast<void*>(s->d_src_group), static_cast<void*>(s->d_src_slots),
-                  static_cast<void*>(s->d_src_wav),
+                  static_cast<void*>(s->d_src_wav), s->d_stage,
                   static_cast<void*>(s->d_status)})
     if (p) cudaFree(p);
   if (s->pinned) cudaFreeHost(s->pinned);
@@ -291,50 +291,34 @@ bbw_status upload(bbw_solver* s, const double* src, void* dst, size_t n) {
   return BBW_OK;
 }
 
-// host [4][K][Np] doubles -> device grouped state of the solver precision
+bbw_status ensure_stage(bbw_solver* s) {
+  const size_t bytes = s->nstate() * sizeof(double);
+  if (s->d_stage_bytes >= bytes) return BBW_OK;
+  if (s->d_stage) cudaFree(s->d_stage);
+  s->d_stage = nullptr;
+  s->d_stage_bytes = 0;
+  BBW_CUDA(cudaMalloc(&s->d_stage, bytes));
+  s->d_stage_bytes = bytes;
+  return BBW_OK;
+}
+
+// host [4][K][Np] doubles -> device grouped state of the solver precision:
+// the array is copied as it is and regrouped (and rounded) on the device
 bbw_status upload_state(bbw_solver* s, const double* src, void* dst) {
-  const size_t n = s->nstate_internal();
-  bbw_status st = ensure_pinned(s, n * 8);
+  bbw_status st = ensure_stage(s);
   if (st != BBW_OK) return st;
-  const int64_t K = s->K;
-  const int Np = s->Np, V = s->V;
-  auto fill = [&](auto* p) {
-    using T = std::remove_pointer_t<decltype(p)>;
-    std::memset(p, 0, n * sizeof(T));
-    for (int f = 0; f < 4; ++f)
-      for (int64_t e = 0; e < K; ++e) {
-        const double* row = src + (size_t(f) * K + e) * Np;
-        for (int i = 0; i < Np; ++i) p[internal_index(e, i, f, Np, V)] = T(row[i]);
-      }
-  };
-  if (s->prec == 64)
-    fill(static_cast<double*>(s->pinned));
-  else
-    fill(static_cast<float*>(s->pinned));
-  BBW_CUDA(cudaMemcpyAsync(dst, s->pinned, n * s->rsz(), cudaMemcpyHostToDevice, s->stream));
+  BBW_CUDA(cudaMemcpyAsync(s->d_stage, src, s->nstate() * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+  BBW_CUDA(bbw::copy_to_internal(s->d_stage, 64, dst, s->prec, s->K, s->Np, s->V, s->stream));
   BBW_CUDA(cudaStreamSynchronize(s->stream));
   return BBW_OK;
 }
 
 bbw_status download_state(bbw_solver* s, const void* src, double* dst) {
-  const size_t n = s->nstate_internal();
-  bbw_status st = ensure_pinned(s, n * 8);
+  bbw_status st = ensure_stage(s);
   if (st != BBW_OK) return st;
-  BBW_CUDA(cudaMemcpyAsync(s->pinned, src, n * s->rsz(), cudaMemcpyDeviceToHost, s->stream));
+  BBW_CUDA(bbw::copy_to_user(src, s->prec, s->d_stage, 64, s->K, s->Np, s->V, s->stream));
+  BBW_CUDA(cudaMemcpyAsync(dst, s->d_stage, s->nstate() * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   BBW_CUDA(cudaStreamSynchronize(s->stream));
-  const int64_t K = s->K;
-  const int Np = s->Np, V = s->V;
-  auto take = [&](const auto* p) {
-    for (int f = 0; f < 4; ++f)
-      for (int64_t e = 0; e < K; ++e) {
-        double* row = dst + (size_t(f) * K + e) * Np;
-        for (int i = 0; i < Np; ++i) row[i] = double(p[internal_index(e, i, f, Np, V)]);
-      }
-  };
-  if (s->prec == 64)
-    take(static_cast<const double*>(s->pinned));
-  else
-    take(static_cast<const float*>(s->pinned));
   return BBW_OK;
 }
 

@@ -68,6 +68,8 @@ struct bbw_solver {
   unsigned int* d_status = nullptr;
   void* pinned = nullptr;
   size_t pinned_bytes = 0;
+  void* d_stage = nullptr;  // FP64 user-layout staging of host state transfers
+  size_t d_stage_bytes = 0;
   int cur = 0;
   double t = 0.0;
   int64_t stages = 0;

@@ -364,3 +364,19 @@ def test_gpu_standing_wave_converges():
         errs.append(np.sqrt(np.sum(vol * w * ((ph - pex) ** 2 + np.sum((uh - uex) ** 2, axis=0)))))
         s.close()
     assert errs[1] < 1e-3 and np.log2(errs[0] / errs[1]) > 3.3
+
+
+def test_get_state_into_pinned_output_array():
+    """bbw_get_state into a caller-given pinned float64 array equals the
+    allocating call; a wrong shape or dtype is rejected before any copy."""
+    N, M = 4, 2
+    vxyz, etov, c2, q, _ = random_case(1, N, M, 32, seed=31)
+    s = _solver(vxyz, etov, N, M, 32, c2, q, None)
+    s.step(1e-3, 2)
+    want, _ = s.get_state()
+    out = torch.empty(q.size, dtype=torch.float64, pin_memory=True).numpy()
+    got, _ = s.get_state(out=out)
+    assert np.array_equal(got, want) and np.shares_memory(got, out)
+    with pytest.raises(ValueError):
+        s.get_state(out=np.empty(q.size, np.float32))
+    s.close()
