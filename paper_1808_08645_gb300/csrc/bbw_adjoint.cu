@@ -19,7 +19,8 @@
 //
 // Adjoint of one LSRK stage s (res' = a_s res + dt (L q + s), q' = q + b_s res'),
 // from the cotangents (qb, rb) of (q', res'):
-//     rt = rb + b_s qb;   qb += dt L^T rt;   rb = a_s rt;
+//     rt = rb + b_s qb;   qb += dt L^T rt;   rb = a_s rt
+// (rb = a_s rt is folded into the next adjoint stage's rt = a_s rt + b_{s-1} qb);
 //     gc2[k][beta] += dt (M^{-1} rt_p)_k^T T_beta v_k,
 // with T_beta the mass matrix weighted by the degree-M Bernstein polynomial
 // beta and v = (A_tau q + source) the pressure bracket of the forward stage.
@@ -121,12 +122,34 @@ __global__ void axpby_kernel(real* __restrict__ x, const real* __restrict__ y, r
     x[i] = a * x[i] + (y ? b * y[i] : real(0));
 }
 
-// x[row][i] *= s[row % K] over nrows rows of Np ([f][K][Np] layouts)
+// user [nf][K][Np] -> internal [G][4][Np][V] (fields >= nf and padding zero),
+// times scale[e] if given
 template <typename real>
-__global__ void scale_rows_kernel(real* __restrict__ x, const real* __restrict__ s, int64_t nrows, int64_t K, int Np) {
-  const size_t n = size_t(nrows) * Np;
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
-    x[i] *= s[(i / Np) % K];
+__global__ void to_internal_scaled(const real* __restrict__ in, real* __restrict__ out, int64_t K, int Np, int V,
+                                   const real* __restrict__ scale, size_t n_internal) {
+  for (size_t x = blockIdx.x * size_t(blockDim.x) + threadIdx.x; x < n_internal; x += size_t(gridDim.x) * blockDim.x) {
+    const int v = int(x % V);
+    const size_t r = x / V;
+    const int i = int(r % Np);
+    const size_t r2 = r / Np;
+    const int f = int(r2 % 4);
+    const int64_t e = int64_t(r2 / 4) * V + v;
+    out[x] = e < K ? in[(size_t(f) * K + e) * Np + i] * (scale ? scale[e] : real(1)) : real(0);
+  }
+}
+
+// internal -> user, fields 0..nf-1, times scale[e] if given
+template <typename real>
+__global__ void to_user_scaled(const real* __restrict__ in, real* __restrict__ out, int64_t K, int Np, int V, int nf,
+                               const real* __restrict__ scale) {
+  const size_t n = size_t(nf) * K * Np;
+  for (size_t x = blockIdx.x * size_t(blockDim.x) + threadIdx.x; x < n; x += size_t(gridDim.x) * blockDim.x) {
+    const int i = int(x % Np);
+    const size_t r = x / Np;
+    const int64_t e = int64_t(r % K);
+    const int f = int(r / K);
+    out[x] = in[iidx(e, i, f, Np, V)] * (scale ? scale[e] : real(1));
+  }
 }
 
 // gc[e][b] += alpha sum_i yt[e][i] u[b][e][i]   (u_b = T_b v_p)
@@ -357,30 +380,31 @@ bbw_status adjoint_stage(bbw_solver* s, AdjointData* a, const void* qin, int sta
   const real* vol = static_cast<const real*>(a->d_vol);
   const real* ivol = static_cast<const real*>(a->d_ivol);
   cudaStream_t st = s->stream;
-  // rt = rb + b_s qb (in rb)
-  axpby_kernel<real><<<blocks_for(4 * nf), 256, 0, st>>>(rb, qb, real(1), real(cb[stage]), 4 * nf);
-  // yt = M^{-1} rt_p; y_p = P~(c2 . yt) / |D|; y_u = M^{-1} rt_u / |D|
+  // rt = a_{s+1} rt + b_s qb in rb (rb holds rt of the stage after; at the
+  // last stage of a step the incoming res cotangent is zero, a_0 = 0)
+  const real a_next = stage == 4 ? real(0) : real(ca[stage + 1]);
+  axpby_kernel<real><<<blocks_for(4 * nf), 256, 0, st>>>(rb, qb, a_next, real(cb[stage]), 4 * nf);
+  // yt = M^{-1} rt_p; y = [P~(c2 . yt); M^{-1} rt_u], scaled by 1/|D| into the grouped layout
   BBW_BLAS(gemm(a->blas, minv, Np, rb, yt, K, real(1), real(0)));
   bbw_status r = wadg_user<real>(s, yt, a->d_c2u, y);
   if (r != BBW_OK) return r;
   BBW_BLAS(gemm(a->blas, minv, Np, rb + nf, y + nf, 3 * K, real(1), real(0)));
-  scale_rows_kernel<real><<<blocks_for(4 * nf), 256, 0, st>>>(y, ivol, 4 * K, K, Np);
+  const size_t ni = s->nstate_internal();
+  to_internal_scaled<real><<<blocks_for(ni), 256, 0, st>>>(y, static_cast<real*>(a->yi), K, Np, V, ivol, ni);
   BBW_CUDA(cudaGetLastError());
-  // z = A_{-tau}(y), v = A_tau(q_s) + sources
-  BBW_CUDA(bbw::copy_to_internal(y, p, a->yi, p, K, Np, V, st));
+  // z = |D| A_{-tau}(y); v_p = (A_tau(q_s) + sources)_p
   r = spatial<real>(s, a->yi, a->zi, -1.0, false, stage, dt, t);
   if (r != BBW_OK) return r;
-  BBW_CUDA(bbw::copy_to_user(a->zi, p, z, p, K, Np, V, st));
+  to_user_scaled<real><<<blocks_for(4 * nf), 256, 0, st>>>(static_cast<const real*>(a->zi), z, K, Np, V, 4, vol);
   r = spatial<real>(s, qin, a->zi, 1.0, true, stage, dt, t);
   if (r != BBW_OK) return r;
-  BBW_CUDA(bbw::copy_to_user(a->zi, p, v, p, K, Np, V, st));
-  // qb -= dt M (|D| z); gc += dt yt^T T_b v_p; rb = a_s rt
-  scale_rows_kernel<real><<<blocks_for(4 * nf), 256, 0, st>>>(z, vol, 4 * K, K, Np);
+  to_user_scaled<real><<<blocks_for(nf), 256, 0, st>>>(static_cast<const real*>(a->zi), v, K, Np, V, 1, nullptr);
+  BBW_CUDA(cudaGetLastError());
+  // qb -= dt M z; gc += dt yt^T T_b v_p
   BBW_BLAS(gemm(a->blas, mass, Np, z, qb, 4 * K, real(-dt), real(1)));
   BBW_BLAS(gemm_batch(a->blas, static_cast<const real*>(a->d_tw), Np, v, static_cast<real*>(a->u), K, Mp));
   grad_c2_kernel<real><<<blocks_for(size_t(K) * Mp), 256, 0, st>>>(static_cast<const real*>(a->u), yt,
                                                                      static_cast<real*>(a->gc), K, Mp, Np, real(dt));
-  axpby_kernel<real><<<blocks_for(4 * nf), 256, 0, st>>>(rb, nullptr, real(ca[stage]), real(0), 4 * nf);
   BBW_CUDA(cudaGetLastError());
   return BBW_OK;
 }
@@ -499,9 +523,8 @@ bbw_status adjoint(bbw_solver* s, const double* g, double* grad_c2, double* grad
         st = adjoint_stage<real>(s, a, a->qs[sg], sg, dt, a->t_step[size_t(n)]);
         if (st != BBW_OK) return st;
       }
-      // the step's res enters only through stage 0 (a_0 = 0): the incoming
-      // cotangent of res is zero at every step boundary
-      BBW_CUDA(cudaMemsetAsync(a->rb, 0, ns, sm));
+      // the step's res enters only through stage 0 (a_0 = 0): the res
+      // cotangent is zero at every step boundary (a_next = 0 at stage 4)
     }
   }
   BBW_CUDA(cudaStreamSynchronize(sm));
