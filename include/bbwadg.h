@@ -288,7 +288,10 @@ bbw_status bbw_record(bbw_solver* s, double dt, int64_t nsteps, int64_t checkpoi
  * trace_grad = trace - data this is the gradient of the L2 misfit
  * (1/2) sum (trace - data)^2. The c^2 and penalties used are the solver's
  * current ones, which must be those of the recorded run. Recomputes each
- * checkpoint segment; device work of the order of three forward runs.
+ * checkpoint segment once, keeping the five stage inputs of its steps:
+ * device memory of ceil(nsteps / C) + 5 C states (C = checkpoint_every) plus
+ * a few work arrays; device work of one more forward run plus the adjoint
+ * stages.
  */
 bbw_status bbw_adjoint(bbw_solver* s, const double* trace_grad, double* grad_c2, double* grad_q0);
 

@@ -27,7 +27,8 @@
 //
 // A recorded run keeps the state every C steps (checkpoints) and the start
 // time of every step; the backward pass recomputes one checkpoint segment at
-// a time (the states at its steps, then the five stage inputs of each step).
+// a time, keeping the five stage inputs of each of its steps (memory: the
+// checkpoints plus 5 C states).
 //
 // The element-local mass products are plain dense matrix products over all
 // elements at once ([N_p x N_p] times [N_p x 4K], and the M_p weighted masses
@@ -459,7 +460,7 @@ bbw_status adjoint(bbw_solver* s, const double* g, double* grad_c2, double* grad
     st = dalloc(b, ns);
     if (st != BBW_OK) return st;
   }
-  for (void** b : {&a->yi, &a->zi, &a->rs, &a->qs[0], &a->qs[1], &a->qs[2], &a->qs[3], &a->qs[4]}) {
+  for (void** b : {&a->yi, &a->zi, &a->rs}) {
     st = dalloc(b, bytes);
     if (st != BBW_OK) return st;
   }
@@ -474,7 +475,7 @@ bbw_status adjoint(bbw_solver* s, const double* g, double* grad_c2, double* grad
   BBW_BLAS(cublasSetStream(a->blas, s->stream));
   if (st == BBW_OK) st = upload_real<real>(s->c2, &a->d_c2u);  // the current c^2 of the solver
   if (st != BBW_OK) return st;
-  a->seg.resize(size_t(a->every), nullptr);
+  a->seg.resize(size_t(a->every) * 5, nullptr);  // the five stage inputs of each step of a segment
   for (auto& b : a->seg) {
     st = dalloc(&b, bytes);
     if (st != BBW_OK) return st;
@@ -494,14 +495,14 @@ bbw_status adjoint(bbw_solver* s, const double* g, double* grad_c2, double* grad
   const int64_t nseg = int64_t(a->ckpt.size());
   for (int64_t k = nseg - 1; k >= 0; --k) {
     const int64_t n0 = k * a->every, n1 = std::min(a->nsteps, n0 + a->every);
-    // states at the steps of the segment
+    // the stage inputs of every step of the segment, from its checkpoint
     BBW_CUDA(cudaMemcpyAsync(a->seg[0], a->ckpt[size_t(k)], bytes, cudaMemcpyDeviceToDevice, sm));
-    for (int64_t n = n0; n + 1 < n1; ++n) {
-      const void* src = a->seg[size_t(n - n0)];
-      BBW_CUDA(cudaMemcpyAsync(a->qs[0], src, bytes, cudaMemcpyDeviceToDevice, sm));
+    for (int64_t n = n0; n < n1; ++n) {
+      const size_t b5 = size_t(n - n0) * 5;
       for (int sg = 0; sg < 5; ++sg) {
-        void* out = sg < 4 ? a->qs[sg + 1] : a->seg[size_t(n - n0 + 1)];
-        st = forward_stage<real>(s, a->qs[sg], out, a->rs, sg, dt, a->t_step[size_t(n)]);
+        if (sg == 4 && n + 1 == n1) break;  // the segment's final state is not needed
+        void* out = sg < 4 ? a->seg[b5 + sg + 1] : a->seg[b5 + 5];
+        st = forward_stage<real>(s, a->seg[b5 + sg], out, a->rs, sg, dt, a->t_step[size_t(n)]);
         if (st != BBW_OK) return st;
       }
     }
@@ -513,14 +514,9 @@ bbw_status adjoint(bbw_solver* s, const double* g, double* grad_c2, double* grad
                                                          a->d_g + size_t(n) * a->nrec, Np);
         BBW_CUDA(cudaGetLastError());
       }
-      // stage inputs of step n
-      BBW_CUDA(cudaMemcpyAsync(a->qs[0], a->seg[size_t(n - n0)], bytes, cudaMemcpyDeviceToDevice, sm));
-      for (int sg = 0; sg < 4; ++sg) {
-        st = forward_stage<real>(s, a->qs[sg], a->qs[sg + 1], a->rs, sg, dt, a->t_step[size_t(n)]);
-        if (st != BBW_OK) return st;
-      }
+      const size_t b5 = size_t(n - n0) * 5;
       for (int sg = 4; sg >= 0; --sg) {
-        st = adjoint_stage<real>(s, a, a->qs[sg], sg, dt, a->t_step[size_t(n)]);
+        st = adjoint_stage<real>(s, a, a->seg[b5 + sg], sg, dt, a->t_step[size_t(n)]);
         if (st != BBW_OK) return st;
       }
       // the step's res enters only through stage 0 (a_0 = 0): the res
