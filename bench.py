@@ -310,7 +310,9 @@ def run_e2e(solvers, host_q0, Ns, dts, K, steps, stream):
                     "bytes per step amortised over the run"}
 
 
-KERNEL_SOURCES = ("bbw_stage.cuh", "bbw_common.h", "bbw_stage_inst.cuh")
+# the sources that decide the stage kernel's memory traffic: the kernel and
+# its tables, and the host code that lays out and orders the elements
+KERNEL_SOURCES = ("bbw_stage.cuh", "bbw_common.h", "bbw_stage_inst.cuh", "bbw_api.cu")
 
 
 def kernel_sources_sha256() -> str:

@@ -71,8 +71,9 @@ struct AdjointData {
   void* d_tw = nullptr;
   void* d_vol = nullptr;    // [K] element volumes
   void* d_ivol = nullptr;   // [K] 1 / volume
-  void* d_c2u = nullptr;    // [K][Mp] c^2 in the ABI layout (for the WADG kernel)
-  // work buffers: user layout [4][K][Np] (qb, rb, y, z, v), [K][Np] (yt), [K][Mp] (gc)
+  void* d_c2u = nullptr;    // [K][Mp] c^2 (for the WADG kernel)
+  // work buffers in the ABI's field-major layout but the solver's internal
+  // element order: [4][K][Np] (qb, rb, y, z, v), [K][Np] (yt), [K][Mp] (gc)
   void* qb = nullptr;
   void* rb = nullptr;
   void* y = nullptr;
@@ -248,8 +249,12 @@ bbw_status build_tables(bbw_solver* s, AdjointData* a) {
     if (!bbw::solve_mass(N, col)) return fail(BBW_ERR_ARG, "mass matrix factorisation failed");
     for (int i = 0; i < Np; ++i) minv[size_t(i) * Np + j] = col[size_t(i)];
   }
-  std::vector<double> vol(s->vol.begin(), s->vol.end()), ivol(vol.size());
-  for (size_t e = 0; e < vol.size(); ++e) ivol[e] = 1.0 / vol[e];
+  // element arrays in the solver's internal element order
+  std::vector<double> vol(s->vol.size()), ivol(s->vol.size());
+  for (size_t e = 0; e < vol.size(); ++e) {
+    vol[e] = s->vol[size_t(s->user(int64_t(e)))];
+    ivol[e] = 1.0 / vol[e];
+  }
   bbw_status st = upload_real<real>(mass, &a->d_mass);
   if (st == BBW_OK) st = upload_real<real>(minv, &a->d_minv);
   if (st == BBW_OK) st = upload_real<real>(tw, &a->d_tw);
@@ -473,8 +478,14 @@ bbw_status adjoint(bbw_solver* s, const double* g, double* grad_c2, double* grad
     BBW_BLAS(cublasSetMathMode(a->blas, CUBLAS_PEDANTIC_MATH));
   }
   BBW_BLAS(cublasSetStream(a->blas, s->stream));
-  if (st == BBW_OK) st = upload_real<real>(s->c2, &a->d_c2u);  // the current c^2 of the solver
   if (st != BBW_OK) return st;
+  {  // the current c^2 of the solver, [K][Mp] in the internal element order
+    std::vector<double> c2u(s->c2.size());
+    for (int64_t e = 0; e < K; ++e)
+      for (int b = 0; b < Mp; ++b) c2u[size_t(e) * Mp + b] = s->c2[size_t(s->user(e)) * Mp + b];
+    st = upload_real<real>(c2u, &a->d_c2u);
+    if (st != BBW_OK) return st;
+  }
   a->seg.resize(size_t(a->every) * 5, nullptr);  // the five stage inputs of each step of a segment
   for (auto& b : a->seg) {
     st = dalloc(&b, bytes);
@@ -526,15 +537,20 @@ bbw_status adjoint(bbw_solver* s, const double* g, double* grad_c2, double* grad
   BBW_CUDA(cudaStreamSynchronize(sm));
   st = bbw::check_status(s);
   if (st != BBW_OK) return st;
+  // back to the caller's element order
   if (grad_c2) {
     std::vector<real> h(size_t(K) * Mp);
     BBW_CUDA(cudaMemcpy(h.data(), a->gc, h.size() * sizeof(real), cudaMemcpyDeviceToHost));
-    for (size_t i = 0; i < h.size(); ++i) grad_c2[i] = double(h[i]);
+    for (int64_t e = 0; e < K; ++e)
+      for (int b = 0; b < Mp; ++b) grad_c2[size_t(s->user(e)) * Mp + b] = double(h[size_t(e) * Mp + b]);
   }
   if (grad_q0) {
     std::vector<real> h(4 * nf);
     BBW_CUDA(cudaMemcpy(h.data(), a->qb, h.size() * sizeof(real), cudaMemcpyDeviceToHost));
-    for (size_t i = 0; i < h.size(); ++i) grad_q0[i] = double(h[i]);
+    for (int f = 0; f < 4; ++f)
+      for (int64_t e = 0; e < K; ++e)
+        for (int i = 0; i < Np; ++i)
+          grad_q0[(size_t(f) * K + size_t(s->user(e))) * Np + i] = double(h[(size_t(f) * K + e) * Np + i]);
   }
   return BBW_OK;
 }
@@ -605,7 +621,9 @@ bbw_status bbw_set_receivers(bbw_solver* s, int64_t nrec, const double* xyz, int
   free_run(a);
   if (nrec > 0) {
     BBW_CUDA(cudaMalloc(reinterpret_cast<void**>(&a->d_rec_elem), size_t(nrec) * sizeof(int64_t)));
-    BBW_CUDA(cudaMemcpy(a->d_rec_elem, el.data(), size_t(nrec) * sizeof(int64_t), cudaMemcpyHostToDevice));
+    std::vector<int64_t> slots(el.size());
+    for (size_t r = 0; r < el.size(); ++r) slots[r] = s->slot(el[r]);  // internal element order
+    BBW_CUDA(cudaMemcpy(a->d_rec_elem, slots.data(), size_t(nrec) * sizeof(int64_t), cudaMemcpyHostToDevice));
     bbw_status st = s->prec == 64 ? upload_real<double>(vec, &a->d_rec_vec) : upload_real<float>(vec, &a->d_rec_vec);
     if (st != BBW_OK) return st;
   }

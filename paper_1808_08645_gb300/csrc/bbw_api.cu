@@ -143,9 +143,11 @@ __host__ __device__ inline size_t internal_index(int64_t e, int i, int f, int Np
   return ((size_t(e / V) * 4 + f) * Np + i) * V + size_t(e % V);
 }
 
+// Internal element slot e holds the caller's element perm[e] (perm NULL:
+// the identity); inv is the inverse permutation.
 template <typename From, typename To>
 __global__ void to_internal_kernel(const From* __restrict__ src, To* __restrict__ dst, int64_t K, int Np, int V,
-                                   size_t n_internal) {
+                                   const int32_t* __restrict__ perm, size_t n_internal) {
   for (size_t x = blockIdx.x * size_t(blockDim.x) + threadIdx.x; x < n_internal; x += size_t(gridDim.x) * blockDim.x) {
     // x enumerates the internal layout: decode (g, f, i, v)
     const int v = int(x % V);
@@ -154,54 +156,58 @@ __global__ void to_internal_kernel(const From* __restrict__ src, To* __restrict_
     const size_t r2 = r / Np;
     const int f = int(r2 % 4);
     const int64_t e = int64_t(r2 / 4) * V + v;
-    dst[x] = e < K ? To(src[(size_t(f) * K + e) * Np + i]) : To(0);
+    dst[x] = e < K ? To(src[(size_t(f) * K + (perm ? perm[e] : e)) * Np + i]) : To(0);
   }
 }
 
 template <typename From, typename To>
-__global__ void to_user_kernel(const From* __restrict__ src, To* __restrict__ dst, int64_t K, int Np, int V) {
+__global__ void to_user_kernel(const From* __restrict__ src, To* __restrict__ dst, int64_t K, int Np, int V,
+                               const int32_t* __restrict__ inv) {
   const size_t n = size_t(4) * K * Np;
   for (size_t x = blockIdx.x * size_t(blockDim.x) + threadIdx.x; x < n; x += size_t(gridDim.x) * blockDim.x) {
     const int i = int(x % Np);
     const size_t r = x / Np;
     const int64_t e = int64_t(r % K);
     const int f = int(r / K);
-    dst[x] = To(src[internal_index(e, i, f, Np, V)]);
+    dst[x] = To(src[internal_index(inv ? inv[e] : e, i, f, Np, V)]);
   }
 }
 
 template <typename From, typename To>
-cudaError_t state_to_internal(const void* src, void* dst, int64_t K, int Np, int V, cudaStream_t s) {
+cudaError_t state_to_internal(const void* src, void* dst, int64_t K, int Np, int V, const int32_t* perm,
+                              cudaStream_t s) {
   const size_t n = size_t((K + V - 1) / V) * V * Np * 4;
   const int blocks = int(std::min<size_t>((n + 255) / 256, 152 * 16));
-  to_internal_kernel<From, To><<<blocks, 256, 0, s>>>(static_cast<const From*>(src), static_cast<To*>(dst), K, Np, V, n);
+  to_internal_kernel<From, To><<<blocks, 256, 0, s>>>(static_cast<const From*>(src), static_cast<To*>(dst), K, Np, V,
+                                                      perm, n);
   return cudaGetLastError();
 }
 
 template <typename From, typename To>
-cudaError_t state_to_user(const void* src, void* dst, int64_t K, int Np, int V, cudaStream_t s) {
+cudaError_t state_to_user(const void* src, void* dst, int64_t K, int Np, int V, const int32_t* inv, cudaStream_t s) {
   const size_t n = size_t(4) * K * Np;
   const int blocks = int(std::min<size_t>((n + 255) / 256, 152 * 16));
-  to_user_kernel<From, To><<<blocks, 256, 0, s>>>(static_cast<const From*>(src), static_cast<To*>(dst), K, Np, V);
+  to_user_kernel<From, To><<<blocks, 256, 0, s>>>(static_cast<const From*>(src), static_cast<To*>(dst), K, Np, V,
+                                                  inv);
   return cudaGetLastError();
 }
 
 cudaError_t copy_to_internal_impl(const void* src, int src_prec, void* dst, int dst_prec, int64_t K, int Np,
-                                  int V, cudaStream_t s) {
+                                  int V, const int32_t* perm, cudaStream_t s) {
   if (src_prec == 64)
-    return dst_prec == 64 ? state_to_internal<double, double>(src, dst, K, Np, V, s)
-                          : state_to_internal<double, float>(src, dst, K, Np, V, s);
-  return dst_prec == 64 ? state_to_internal<float, double>(src, dst, K, Np, V, s)
-                        : state_to_internal<float, float>(src, dst, K, Np, V, s);
+    return dst_prec == 64 ? state_to_internal<double, double>(src, dst, K, Np, V, perm, s)
+                          : state_to_internal<double, float>(src, dst, K, Np, V, perm, s);
+  return dst_prec == 64 ? state_to_internal<float, double>(src, dst, K, Np, V, perm, s)
+                        : state_to_internal<float, float>(src, dst, K, Np, V, perm, s);
 }
 
 cudaError_t copy_to_user_impl(const void* src, int src_prec, void* dst, int dst_prec, int64_t K, int Np, int V,
-                              cudaStream_t s) {
+                              const int32_t* inv, cudaStream_t s) {
   if (src_prec == 64)
-    return dst_prec == 64 ? state_to_user<double, double>(src, dst, K, Np, V, s)
-                          : state_to_user<double, float>(src, dst, K, Np, V, s);
-  return dst_prec == 64 ? state_to_user<float, double>(src, dst, K, Np, V, s)
-                        : state_to_user<float, float>(src, dst, K, Np, V, s);
+    return dst_prec == 64 ? state_to_user<double, double>(src, dst, K, Np, V, inv, s)
+                          : state_to_user<double, float>(src, dst, K, Np, V, inv, s);
+  return dst_prec == 64 ? state_to_user<float, double>(src, dst, K, Np, V, inv, s)
+                        : state_to_user<float, float>(src, dst, K, Np, V, inv, s);
 }
 
 std::mutex g_cache_mu;
@@ -245,15 +251,15 @@ int num_sms() {
 namespace bbw {
 void set_last_error(const char* msg) { g_err = msg; }
 cudaError_t copy_to_internal(const void* src, int src_prec, void* dst, int dst_prec, int64_t K, int Np, int V,
-                             cudaStream_t s) {
-  return copy_to_internal_impl(src, src_prec, dst, dst_prec, K, Np, V, s);
+                             const int32_t* perm, cudaStream_t s) {
+  return copy_to_internal_impl(src, src_prec, dst, dst_prec, K, Np, V, perm, s);
 }
 double factorial(int n) { return factd(n); }
 std::vector<std::array<int, 4>> lattice(int n) { return multi_indices(n); }
 bool solve_mass(int n, std::vector<double>& b) { return mass_solve(n, b); }
 cudaError_t copy_to_user(const void* src, int src_prec, void* dst, int dst_prec, int64_t K, int Np, int V,
-                         cudaStream_t s) {
-  return copy_to_user_impl(src, src_prec, dst, dst_prec, K, Np, V, s);
+                         const int32_t* inv, cudaStream_t s) {
+  return copy_to_user_impl(src, src_prec, dst, dst_prec, K, Np, V, inv, s);
 }
 }  // namespace bbw
 
@@ -268,7 +274,8 @@ void free_solver(bbw_solver* s) {
   bbw::free_adjoint(s);
   for (void* p : {s->q[0], s->q[1], s->res, s->d_c2, s->d_geom, static_cast<void*>(s->d_conn), s->d_src,
                   static_cast<void*>(s->d_src_group), static_cast<void*>(s->d_src_slots),
-                  static_cast<void*>(s->d_src_wav), s->d_stage,
+                  static_cast<void*>(s->d_src_wav), s->d_stage, static_cast<void*>(s->d_perm),
+                  static_cast<void*>(s->d_inv),
                   static_cast<void*>(s->d_status)})
     if (p) cudaFree(p);
   if (s->pinned) cudaFreeHost(s->pinned);
@@ -308,7 +315,7 @@ bbw_status upload_state(bbw_solver* s, const double* src, void* dst) {
   bbw_status st = ensure_stage(s);
   if (st != BBW_OK) return st;
   BBW_CUDA(cudaMemcpyAsync(s->d_stage, src, s->nstate() * sizeof(double), cudaMemcpyHostToDevice, s->stream));
-  BBW_CUDA(bbw::copy_to_internal(s->d_stage, 64, dst, s->prec, s->K, s->Np, s->V, s->stream));
+  BBW_CUDA(bbw::copy_to_internal(s->d_stage, 64, dst, s->prec, s->K, s->Np, s->V, s->d_perm, s->stream));
   BBW_CUDA(cudaStreamSynchronize(s->stream));
   return BBW_OK;
 }
@@ -316,7 +323,7 @@ bbw_status upload_state(bbw_solver* s, const double* src, void* dst) {
 bbw_status download_state(bbw_solver* s, const void* src, double* dst) {
   bbw_status st = ensure_stage(s);
   if (st != BBW_OK) return st;
-  BBW_CUDA(bbw::copy_to_user(src, s->prec, s->d_stage, 64, s->K, s->Np, s->V, s->stream));
+  BBW_CUDA(bbw::copy_to_user(src, s->prec, s->d_stage, 64, s->K, s->Np, s->V, s->d_inv, s->stream));
   BBW_CUDA(cudaMemcpyAsync(dst, s->d_stage, s->nstate() * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   BBW_CUDA(cudaStreamSynchronize(s->stream));
   return BBW_OK;
@@ -332,7 +339,7 @@ bbw_status upload_grouped(bbw_solver* s, const double* src, int W, double pad, v
     using T = std::remove_pointer_t<decltype(p)>;
     for (int64_t e = 0; e < s->G * V; ++e)
       for (int w = 0; w < W; ++w)
-        p[(size_t(e / V) * W + w) * V + size_t(e % V)] = T(e < s->K ? src[size_t(e) * W + w] : pad);
+        p[(size_t(e / V) * W + w) * V + size_t(e % V)] = T(e < s->K ? src[size_t(s->user(e)) * W + w] : pad);
   };
   if (s->prec == 64)
     fill(static_cast<double*>(s->pinned));
@@ -471,7 +478,7 @@ bbw_status upload_geometry(bbw_solver* s) {
   for (int64_t e = 0; e < s->G * V; ++e)
     for (int c = 0; c < 9; ++c)
       geom[(size_t(e / V) * 9 + c) * V + size_t(e % V)] =
-          real(e < s->K ? s->grad[size_t(e) * 12 + 3 + c] : (c % 4 == 0 ? 1.0 : 0.0));
+          real(e < s->K ? s->grad[size_t(s->user(e)) * 12 + 3 + c] : (c % 4 == 0 ? 1.0 : 0.0));
   BBW_CUDA(cudaMemcpy(s->d_geom, geom.data(), geom.size() * sizeof(real), cudaMemcpyHostToDevice));
   return BBW_OK;
 }
@@ -506,6 +513,53 @@ bbw_status launch_stage(bbw_solver* s, int stage, double dt) {
   s->cur = 1 - s->cur;
   s->stages += 1;
   if (stage == 4) s->t += dt;
+  return BBW_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// Internal element order for locality: elements sorted by the Morton key of
+// their centroids (10 bits per axis over the mesh's bounding box; ties keep
+// the caller's order), so that face neighbours are close in memory and their
+// traces are more often still in L2 when gathered.
+bbw_status renumber_elements(bbw_solver* s) {
+  const int64_t K = s->K;
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  std::vector<double> cen(size_t(K) * 3, 0.0);
+  for (int64_t e = 0; e < K; ++e)
+    for (int v = 0; v < 4; ++v)
+      for (int d = 0; d < 3; ++d) {
+        const double x = s->vxyz[size_t(s->etov[size_t(e) * 4 + v]) * 3 + d];
+        cen[size_t(e) * 3 + d] += 0.25 * x;
+        lo[d] = std::min(lo[d], x);
+        hi[d] = std::max(hi[d], x);
+      }
+  auto spread = [](uint64_t v) {
+    uint64_t r = 0;
+    for (int b = 0; b < 10; ++b) r |= ((v >> b) & 1u) << (3 * b);
+    return r;
+  };
+  std::vector<uint64_t> key(static_cast<size_t>(K), 0);
+  for (int64_t e = 0; e < K; ++e) {
+    uint64_t k = 0;
+    for (int d = 0; d < 3; ++d) {
+      const double w = hi[d] > lo[d] ? (cen[size_t(e) * 3 + d] - lo[d]) / (hi[d] - lo[d]) : 0.0;
+      const uint64_t q = uint64_t(std::min(1023.0, std::max(0.0, std::floor(w * 1024.0))));
+      k |= spread(q) << d;
+    }
+    key[size_t(e)] = k;
+  }
+  s->perm.resize(size_t(K));
+  for (int64_t e = 0; e < K; ++e) s->perm[size_t(e)] = int32_t(e);
+  std::stable_sort(s->perm.begin(), s->perm.end(), [&](int32_t a, int32_t b) { return key[size_t(a)] < key[size_t(b)]; });
+  s->inv.resize(size_t(K));
+  for (int64_t e = 0; e < K; ++e) s->inv[size_t(s->perm[size_t(e)])] = int32_t(e);
+  BBW_CUDA(cudaMalloc(reinterpret_cast<void**>(&s->d_perm), size_t(K) * sizeof(int32_t)));
+  BBW_CUDA(cudaMalloc(reinterpret_cast<void**>(&s->d_inv), size_t(K) * sizeof(int32_t)));
+  BBW_CUDA(cudaMemcpy(s->d_perm, s->perm.data(), size_t(K) * sizeof(int32_t), cudaMemcpyHostToDevice));
+  BBW_CUDA(cudaMemcpy(s->d_inv, s->inv.data(), size_t(K) * sizeof(int32_t), cudaMemcpyHostToDevice));
   return BBW_OK;
 }
 
@@ -586,6 +640,13 @@ const char* bbw_last_error(void) { return g_err.c_str(); }
 
 bbw_status bbw_create(int64_t nverts, const double* vxyz, int64_t K, const int64_t* etov, int N, int M,
                       int precision, void* cuda_stream, bbw_solver** out) {
+  return bbw::create_solver(nverts, vxyz, K, etov, N, M, precision, cuda_stream, true, out);
+}
+
+}  // extern "C"
+
+bbw_status bbw::create_solver(int64_t nverts, const double* vxyz, int64_t K, const int64_t* etov, int N, int M,
+                              int precision, void* cuda_stream, bool renumber, bbw_solver** out) {
   if (!out) return fail(BBW_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (!vxyz || !etov || nverts <= 0 || K <= 0) return fail(BBW_ERR_ARG, "empty mesh or NULL array");
@@ -602,6 +663,13 @@ bbw_status bbw_create(int64_t nverts, const double* vxyz, int64_t K, const int64
   if (st != BBW_OK) {
     free_solver(s);
     return st;
+  }
+  if (renumber) {
+    st = renumber_elements(s);
+    if (st != BBW_OK) {
+      free_solver(s);
+      return st;
+    }
   }
   projection_coeffs(N, M, s->cj);
   st = get_tables(N, M, precision, &s->op);
@@ -635,11 +703,12 @@ bbw_status bbw_create(int64_t nverts, const double* vxyz, int64_t K, const int64
     // [G][4][V]; padding elements have walls on all faces
     const int V = s->V;
     std::vector<int32_t> conn(ng * 4, -1);
-    for (int64_t e = 0; e < K; ++e)
+    for (int64_t e = 0; e < K; ++e)  // internal slot e, caller's element s->user(e)
       for (int f = 0; f < 4; ++f) {
-        const size_t i = size_t(e) * 4 + f;
+        const size_t i = size_t(s->user(e)) * 4 + f;
         conn[(size_t(e / V) * 4 + f) * V + size_t(e % V)] =
-            s->etoe[i] < 0 ? -1 : (s->etoe[i] << 5) | (int32_t(s->etof[i]) << 3) | int32_t(s->fperm[i]);
+            s->etoe[i] < 0 ? -1
+                           : (int32_t(s->slot(s->etoe[i])) << 5) | (int32_t(s->etof[i]) << 3) | int32_t(s->fperm[i]);
       }
     if (cudaMemcpy(s->d_conn, conn.data(), conn.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
       st = fail(BBW_ERR_CUDA, "connectivity upload failed");
@@ -655,6 +724,8 @@ bbw_status bbw_create(int64_t nverts, const double* vxyz, int64_t K, const int64
   *out = s;
   return BBW_OK;
 }
+
+extern "C" {
 
 void bbw_destroy(bbw_solver* s) {
   if (s && s->stream) cudaStreamSynchronize(s->stream);
@@ -761,9 +832,9 @@ bbw_status bbw_set_state(bbw_solver* s, const double* q, const double* res, doub
 bbw_status bbw_set_state_device(bbw_solver* s, const void* q, const void* res, int dtype, double t) {
   if (!s || !q) return fail(BBW_ERR_ARG, "NULL argument");
   if (dtype != 32 && dtype != 64) return fail(BBW_ERR_ARG, "dtype must be 32 or 64");
-  BBW_CUDA(bbw::copy_to_internal(q, dtype, s->q[s->cur], s->prec, s->K, s->Np, s->V, s->stream));
+  BBW_CUDA(bbw::copy_to_internal(q, dtype, s->q[s->cur], s->prec, s->K, s->Np, s->V, s->d_perm, s->stream));
   if (res)
-    BBW_CUDA(bbw::copy_to_internal(res, dtype, s->res, s->prec, s->K, s->Np, s->V, s->stream));
+    BBW_CUDA(bbw::copy_to_internal(res, dtype, s->res, s->prec, s->K, s->Np, s->V, s->d_perm, s->stream));
   else
     BBW_CUDA(cudaMemsetAsync(s->res, 0, s->nstate_internal() * s->rsz(), s->stream));
   s->t = t;
@@ -790,8 +861,8 @@ bbw_status bbw_get_state(bbw_solver* s, double* q, double* res, double* t) {
 bbw_status bbw_get_state_device(bbw_solver* s, void* q, void* res, int dtype) {
   if (!s) return fail(BBW_ERR_ARG, "solver is NULL");
   if (dtype != 32 && dtype != 64) return fail(BBW_ERR_ARG, "dtype must be 32 or 64");
-  if (q) BBW_CUDA(bbw::copy_to_user(s->q[s->cur], s->prec, q, dtype, s->K, s->Np, s->V, s->stream));
-  if (res) BBW_CUDA(bbw::copy_to_user(s->res, s->prec, res, dtype, s->K, s->Np, s->V, s->stream));
+  if (q) BBW_CUDA(bbw::copy_to_user(s->q[s->cur], s->prec, q, dtype, s->K, s->Np, s->V, s->d_inv, s->stream));
+  if (res) BBW_CUDA(bbw::copy_to_user(s->res, s->prec, res, dtype, s->K, s->Np, s->V, s->d_inv, s->stream));
   return BBW_OK;
 }
 
@@ -804,10 +875,11 @@ bbw_status bbw_set_source(bbw_solver* s, int64_t elem, const double* coeffs, dou
   if (!s->d_src_group) BBW_CUDA(cudaMalloc(reinterpret_cast<void**>(&s->d_src_group), sizeof(int64_t)));
   if (!s->d_src_slots) BBW_CUDA(cudaMalloc(reinterpret_cast<void**>(&s->d_src_slots), s->V * sizeof(int32_t)));
   if (!s->d_src_wav) BBW_CUDA(cudaMalloc(reinterpret_cast<void**>(&s->d_src_wav), 2 * sizeof(double)));
-  // one source group: element elem is lane elem % V of group elem / V
-  const int64_t grp = elem / s->V;
+  // one source group: internal slot e of elem is lane e % V of group e / V
+  const int64_t ie = s->slot(elem);
+  const int64_t grp = ie / s->V;
   std::vector<int32_t> slots(size_t(s->V), -1);
-  slots[size_t(elem % s->V)] = 0;
+  slots[size_t(ie % s->V)] = 0;
   const double wav[2] = {f0, t0};
   BBW_CUDA(cudaMemcpyAsync(s->d_src_group, &grp, sizeof(grp), cudaMemcpyHostToDevice, s->stream));
   BBW_CUDA(cudaMemcpyAsync(s->d_src_slots, slots.data(), slots.size() * sizeof(int32_t), cudaMemcpyHostToDevice,

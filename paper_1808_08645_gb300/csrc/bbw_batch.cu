@@ -350,8 +350,9 @@ bbw_status bbw_batch_create(int n, const int64_t* nverts, const double* const* v
       }
     }
     if (e >= bbw::kMaxElements) return bail(fail(BBW_ERR_ARG, "too many elements of one degree (limit 2^26)"));
-    bbw_status st = bbw_create(int64_t(xyz.size() / 3), xyz.data(), e, tets.data(), deg, M, precision, b->stream,
-                               &k.s);
+    // the caller's element order is kept: each instance stays one contiguous range
+    bbw_status st = bbw::create_solver(int64_t(xyz.size() / 3), xyz.data(), e, tets.data(), deg, M, precision,
+                                       b->stream, false, &k.s);
     if (st != BBW_OK) return bail(st);
     k.src_elem.assign(ids.size(), -1);
     k.grid0 = k.s->grid_stage;

@@ -77,6 +77,13 @@ struct bbw_solver {
   int64_t src_elem = -1;
   double f0 = 0.0, t0 = 0.0;
   AdjointData* adj = nullptr;  // receivers, recorded run, adjoint buffers (bbw_adjoint.cu)
+  // element renumbering for locality: internal slot e holds the caller's
+  // element perm[e], inv[perm[e]] = e (empty / NULL: the identity)
+  std::vector<int32_t> perm, inv;
+  int32_t* d_perm = nullptr;
+  int32_t* d_inv = nullptr;
+  int64_t slot(int64_t e) const { return inv.empty() ? e : inv[size_t(e)]; }    // caller -> internal
+  int64_t user(int64_t e) const { return perm.empty() ? e : perm[size_t(e)]; }  // internal -> caller
   int V = 1;        // elements per group of the kernel's layout
   int64_t G = 0;   // number of groups, ceil(K / V)
   size_t rsz() const { return prec == 64 ? 8 : 4; }
@@ -89,10 +96,16 @@ namespace bbw {
 // State layout conversions on the device: the ABI's [4][K][Np] ("user")
 // and the kernels' grouped [G][4][Np][V] ("internal"), each in FP32 or FP64
 // (prec 32 | 64); padding entries of the internal layout are set to zero.
+// Internal slot e holds the caller's element perm[e]; inv is the inverse
+// (NULL: the identity).
 cudaError_t copy_to_internal(const void* src, int src_prec, void* dst, int dst_prec, int64_t K, int Np, int V,
-                             cudaStream_t s);
+                             const int32_t* perm, cudaStream_t s);
 cudaError_t copy_to_user(const void* src, int src_prec, void* dst, int dst_prec, int64_t K, int Np, int V,
-                         cudaStream_t s);
+                         const int32_t* inv, cudaStream_t s);
+// Create a solver (as bbw_create); renumber: order the elements internally
+// by a Morton key of their centroids (false: keep the caller's order).
+bbw_status create_solver(int64_t nverts, const double* vxyz, int64_t K, const int64_t* etov, int N, int M,
+                         int precision, void* cuda_stream, bool renumber, bbw_solver** out);
 // n!, the degree-n multi-indices (alpha_0..alpha_3) in the library order, and
 // a solve with the normalised degree-n Bernstein mass matrix (in place;
 // false if the factorisation fails).
