@@ -558,10 +558,14 @@ def run_adjoint(args):
     s.set_c2(c2_true)
     s.set_state(q0)
     data = s.record(dt, nsteps, every)
-    # warm-up, then forward alone
+    # warm-up (one checkpoint segment of record + adjoint: first-use set-up of
+    # the adjoint's buffers and of cuBLAS), then forward alone
     s.set_c2(c2)
     s.set_state(q0)
     s.step(dt, 3)
+    s.set_state(q0)
+    s.record(dt, every, every)
+    s.adjoint(np.zeros((every, len(rec))))
     s.set_state(q0)
     clk = ClockSampler(torch.cuda.current_device())
     clk.start()

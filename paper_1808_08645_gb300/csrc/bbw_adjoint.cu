@@ -268,13 +268,17 @@ AdjointData* adj_of(bbw_solver* s) {
   return s->adj;
 }
 
-void free_run(AdjointData* a) {
-  for (void* p : a->ckpt)
-    if (p) cudaFree(p);
-  a->ckpt.clear();
-  for (void* p : a->seg)
-    if (p) cudaFree(p);
-  a->seg.clear();
+// Forget the recorded run. Buffers stay allocated for the next run unless
+// release is set.
+void free_run(AdjointData* a, bool release = false) {
+  if (release) {
+    for (void* p : a->ckpt)
+      if (p) cudaFree(p);
+    a->ckpt.clear();
+    for (void* p : a->seg)
+      if (p) cudaFree(p);
+    a->seg.clear();
+  }
   if (a->d_traces) cudaFree(a->d_traces);
   a->d_traces = nullptr;
   a->recorded = false;
@@ -424,8 +428,12 @@ bbw_status record(bbw_solver* s, double dt, int64_t nsteps, int64_t every, doubl
   a->nsteps = nsteps;
   a->every = every;
   a->t_step.assign(size_t(nsteps), 0.0);
-  const int64_t nck = (nsteps + every - 1) / every;
-  a->ckpt.assign(size_t(std::max<int64_t>(nck, 1)), nullptr);
+  const int64_t nck = std::max<int64_t>((nsteps + every - 1) / every, 1);
+  while (int64_t(a->ckpt.size()) > nck) {  // keep the buffers of earlier runs, drop extras
+    if (a->ckpt.back()) cudaFree(a->ckpt.back());
+    a->ckpt.pop_back();
+  }
+  a->ckpt.resize(size_t(nck), nullptr);
   for (auto& c : a->ckpt) {
     bbw_status st = dalloc(&c, bytes);
     if (st != BBW_OK) return st;
@@ -486,7 +494,11 @@ bbw_status adjoint(bbw_solver* s, const double* g, double* grad_c2, double* grad
     st = upload_real<real>(c2u, &a->d_c2u);
     if (st != BBW_OK) return st;
   }
-  a->seg.resize(size_t(a->every) * 5, nullptr);  // the five stage inputs of each step of a segment
+  while (a->seg.size() > size_t(a->every) * 5) {  // the five stage inputs of each step of a segment
+    if (a->seg.back()) cudaFree(a->seg.back());
+    a->seg.pop_back();
+  }
+  a->seg.resize(size_t(a->every) * 5, nullptr);
   for (auto& b : a->seg) {
     st = dalloc(&b, bytes);
     if (st != BBW_OK) return st;
@@ -562,7 +574,7 @@ namespace bbw {
 void free_adjoint(bbw_solver* s) {
   AdjointData* a = s->adj;
   if (!a) return;
-  free_run(a);
+  free_run(a, true);
   for (void* p : {static_cast<void*>(a->d_rec_elem), a->d_rec_vec, a->d_minv, a->d_mass, a->d_tw, a->d_vol, a->d_ivol,
                   a->d_c2u, a->qb, a->rb, a->y, a->z, a->v, a->yt, a->gc, a->yi, a->zi, a->rs, a->qs[0], a->qs[1],
                   a->qs[2], a->qs[3], a->qs[4], static_cast<void*>(a->d_g), a->u})
