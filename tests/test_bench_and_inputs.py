@@ -1,0 +1,79 @@
+"""Host-side checks of the measurement script and the seeded input
+generators (CPU only): the reference arm's JSON line, the traffic lookup's
+source check, and the batched / adjoint workload recipes."""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from paper_1808_08645_gb300 import inputs  # noqa: E402
+
+REQUIRED = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+            "scaling", "vs_baseline", "dtype", "data", "config")
+
+
+def test_reference_arm_line_has_the_contract_keys():
+    args = argparse.Namespace(Ns="1,3", ref_hexes=1, steps=1, warmup=0, gpus=1)
+    out = bench.run_reference(args)
+    json.dumps(out)
+    for k in REQUIRED:
+        assert k in out, k
+    assert out["impl"] == "reference" and out["value"] > 0
+    assert out["cpu_baseline"]["kind"] == "oracle" and out["cpu_baseline"]["value"] == out["value"]
+    assert out["e2e"]["h2d_bytes_per_step"] == 0 and out["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_traffic_lookup_tracks_the_kernel_sources(tmp_path, monkeypatch):
+    """A committed traffic figure is reported only for the sources it was
+    measured on."""
+    assert bench.load_traffic(9) is None or bench.load_traffic(9) > 0
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    line = {"N": 4, "traffic_bytes_per_launch": 123.0, "kernel_sources_sha256": bench.kernel_sources_sha256()}
+    (prof / "stage_kernel_n4_test_dram_traffic.md").write_text("x\nmachine-readable: " + json.dumps(line) + "\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    # the sources are read from the real tree
+    monkeypatch.setattr(bench, "kernel_sources_sha256", lambda: line["kernel_sources_sha256"])
+    assert bench.load_traffic(4) == 123.0
+    monkeypatch.setattr(bench, "kernel_sources_sha256", lambda: "0" * 64)
+    assert bench.load_traffic(4) is None
+    assert bench.load_traffic(5) is None
+
+
+def test_algorithmic_bytes_formula():
+    # q_in read, q_out and res written, res read on 4 of 5 stages, c2, geometry, connectivity
+    N, M = 9, 2
+    np3 = lambda n: (n + 1) * (n + 2) * (n + 3) // 6
+    want = 4 * ((12 + 16 / 5) * np3(N) + np3(M) + 9) + 16
+    assert abs(bench.algorithmic_bytes_per_element(N, M) - want) < 1e-9
+
+
+def test_batched_instances_recipe():
+    a = inputs.batched_instances()
+    b = inputs.batched_instances()
+    assert all(x["hexes"] == y["hexes"] and x["N"] == y["N"] and x["c2_seed"] == y["c2_seed"]
+               and np.array_equal(x["source"], y["source"]) for x, y in zip(a, b))
+    cfg = inputs.BATCH_CONFIG
+    assert len(a) == cfg["instances"]
+    tets = [6 * d["hexes"] ** 3 for d in a]
+    assert 2000 <= min(tets) and max(tets) <= 60000
+    assert {d["N"] for d in a} <= set(range(cfg["Ns"][0], cfg["Ns"][1] + 1))
+    assert len({d["c2_seed"] for d in a}) == len(a)
+    for d in a:
+        assert np.all((d["source"] >= 0.25) & (d["source"] <= 0.75))
+
+
+def test_top_face_receivers():
+    r = inputs.top_face_receivers(8)
+    assert r.shape == (64, 3)
+    assert np.all(r[:, 2] == 1.0)
+    assert np.all((r[:, :2] > 0) & (r[:, :2] < 1))
+    assert len({tuple(x) for x in r}) == 64
