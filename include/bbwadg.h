@@ -217,6 +217,16 @@ bbw_status bbw_projection_coeffs(int N, int M, double* c);
 bbw_status bbw_lsrk_coeffs(double* a, double* b, double* c);
 
 /*
+ * Host-only self-check of the operator tables the kernels use for (N, M,
+ * precision): every stencil word (one-degree reductions and elevations of
+ * Eq. (12) in 3D and on faces), product gather index (Eq. 11), face map and
+ * lift gather slot is recomputed by brute force over the multi-index lattice
+ * and range-checked. BBW_OK, or BBW_ERR_ARG naming the first mismatch.
+ * Touches no GPU.
+ */
+bbw_status bbw_validate_tables(int N, int M, int precision);
+
+/*
  * The weight-adjusted update alone (the paper's timed "update kernel" minus
  * the RK part): out = P^{N+M}_N (c2_M * rhs) per element, by the product of
  * Eq. (11) and the telescoped projection of Eq. (20).

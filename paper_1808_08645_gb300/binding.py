@@ -15,7 +15,7 @@ import os
 import numpy as np
 
 __all__ = ["BBWError", "lib", "lib_path", "Solver", "Batch", "mesh_analyze", "projection_coeffs",
-           "lsrk_coeffs", "wadg_update", "wadg_update_noalloc", "EXPORTS", "F32", "F64"]
+           "lsrk_coeffs", "validate_tables", "wadg_update", "wadg_update_noalloc", "EXPORTS", "F32", "F64"]
 
 F32, F64 = 32, 64
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -62,6 +62,7 @@ EXPORTS = {
     "bbw_get_time": (_int, [_p, _dp, _i64p]),
     "bbw_projection_coeffs": (_int, [_int, _int, _dp]),
     "bbw_lsrk_coeffs": (_int, [_dp, _dp, _dp]),
+    "bbw_validate_tables": (_int, [_int, _int, _int]),
     "bbw_wadg_update": (_int, [_int, _int, _int, _i64, _p, _p, _p, _p]),
     "bbw_wadg_update_noalloc": (_int, [_int, _int, _int, _i64, _p, _p, _p, _p]),
     "bbw_set_receivers": (_int, [_p, _i64, _dp, _i64p]),
@@ -140,6 +141,11 @@ def projection_coeffs(N: int, M: int) -> np.ndarray:
     out = np.zeros(N + 1)
     _check(lib().bbw_projection_coeffs(N, M, _ptr(out, C.c_double)), "bbw_projection_coeffs")
     return out
+
+
+def validate_tables(N: int, M: int, precision: int = F32):
+    """bbw_validate_tables: raises BBWError naming the first table mismatch."""
+    _check(lib().bbw_validate_tables(N, M, precision), "bbw_validate_tables")
 
 
 def lsrk_coeffs():

@@ -973,6 +973,16 @@ bbw_status bbw_projection_coeffs(int N, int M, double* c) {
   return BBW_OK;
 }
 
+bbw_status bbw_validate_tables(int N, int M, int precision) {
+  if (N < 1 || N > bbw::kMaxN || M < 0 || M > bbw::kMaxM) return fail(BBW_ERR_UNSUPPORTED, "N or M out of range");
+  if (precision != 32 && precision != 64) return fail(BBW_ERR_ARG, "precision must be 32 or 64");
+  double cj[bbw::kMaxN + 1];
+  projection_coeffs(N, M, cj);
+  const char* msg = bbw::ops_for(N)->check_tables(M, precision == 64, cj);
+  if (msg) return fail(BBW_ERR_ARG, std::string("operator table check failed: ") + msg);
+  return BBW_OK;
+}
+
 bbw_status bbw_lsrk_coeffs(double* a, double* b, double* c) {
   const auto cs = rk_stage_times();
   for (int i = 0; i < 5; ++i) {

@@ -245,4 +245,134 @@ void build_tables(Tables<N, M, real>& t, const double* cj) {
   }
 }
 
+// Host-side check of a built table set against brute force: every stencil
+// word, product index, face map and lift slot is recomputed from the lattice
+// enumeration (not from idx3 / idx2) and range-checked. Returns nullptr if
+// all entries agree, else a description of the first mismatch.
+template <int N, int M, typename real>
+const char* validate_tables(const Tables<N, M, real>& t) {
+  using Tb = Tables<N, M, real>;
+  // position of multi-index (j, k, l) of degree n, by enumeration
+  auto pos3 = [](int n, int j, int k, int l) {
+    if (j < 0 || k < 0 || l < 0 || j + k + l > n) return -1;
+    int c = 0;
+    for (int ll = 0; ll <= n; ++ll)
+      for (int kk = 0; kk <= n - ll; ++kk)
+        for (int jj = 0; jj <= n - ll - kk; ++jj, ++c)
+          if (jj == j && kk == k && ll == l) return c;
+    return -1;
+  };
+  auto pos2 = [](int n, int b1, int b2) {
+    if (b1 < 0 || b2 < 0 || b1 + b2 > n) return -1;
+    int c = 0;
+    for (int bb2 = 0; bb2 <= n; ++bb2)
+      for (int bb1 = 0; bb1 <= n - bb2; ++bb1, ++c)
+        if (bb1 == b1 && bb2 == b2) return c;
+    return -1;
+  };
+  auto s3 = [](uint32_t w, int f) {
+    const int v[6] = {int(w & 511u), int((w >> 9) & 15u), int((w >> 13) & 127u), int((w >> 20) & 15u),
+                      int((w >> 24) & 15u), int(w >> 28)};
+    return v[f];
+  };
+  auto s2 = [](uint32_t w, int f) {
+    const int v[4] = {int(w & 127u), int((w >> 7) & 15u), int((w >> 11) & 15u), int((w >> 15) & 15u)};
+    return v[f];
+  };
+  // one-degree reductions into degree d: inputs beta + e_m of degree d + 1
+  for (int d = 0; d < N + M; ++d) {
+    const int n = d + 1;
+    int c = 0;
+    for (int l = 0; l <= d; ++l)
+      for (int k = 0; k <= d - l; ++k)
+        for (int j = 0; j <= d - l - k; ++j, ++c) {
+          const uint32_t w = t.red3[off3(d) + c];
+          const int b = s3(w, 0);
+          if (b != pos3(n, j, k, l) || b + 1 != pos3(n, j + 1, k, l) || b + s3(w, 1) != pos3(n, j, k + 1, l) ||
+              b + s3(w, 2) != pos3(n, j, k, l + 1))
+            return "reduction stencil offsets";
+          if (s3(w, 3) != j + 1 || s3(w, 4) != k + 1 || s3(w, 5) != l + 1) return "reduction stencil weights";
+        }
+  }
+  // one-degree elevations into degree n: inputs gamma - e_m of degree n - 1
+  for (int n = 1; n <= N; ++n) {
+    int c = 0;
+    for (int l = 0; l <= n; ++l)
+      for (int k = 0; k <= n - l; ++k)
+        for (int j = 0; j <= n - l - k; ++j, ++c) {
+          const uint32_t w = t.elev3[off3(n) + c];
+          const int b = s3(w, 0), g0 = n - j - k - l;
+          if (s3(w, 3) != j || s3(w, 4) != k || s3(w, 5) != l) return "elevation stencil weights";
+          if ((g0 > 0 && b != pos3(n - 1, j, k, l)) || (j > 0 && b - 1 != pos3(n - 1, j - 1, k, l)) ||
+              (k > 0 && b - s3(w, 1) != pos3(n - 1, j, k - 1, l)) ||
+              (l > 0 && b - s3(w, 2) != pos3(n - 1, j, k, l - 1)))
+            return "elevation stencil offsets";
+        }
+  }
+  for (int d = 0; d < N; ++d) {
+    const int n = d + 1;
+    int c = 0;
+    for (int b2 = 0; b2 <= d; ++b2)
+      for (int b1 = 0; b1 <= d - b2; ++b1, ++c) {
+        const uint32_t w = t.red2[off2(d) + c];
+        const int b = s2(w, 0);
+        if (b != pos2(n, b1, b2) || b + 1 != pos2(n, b1 + 1, b2) || b + s2(w, 1) != pos2(n, b1, b2 + 1))
+          return "2D reduction stencil offsets";
+        if (s2(w, 2) != b1 + 1 || s2(w, 3) != b2 + 1) return "2D reduction stencil weights";
+      }
+  }
+  {
+    int c = 0;
+    for (int a2 = 0; a2 <= N; ++a2)
+      for (int a1 = 0; a1 <= N - a2; ++a1, ++c) {
+        const uint32_t w = t.elev2[c];
+        const int b = s2(w, 0), a0 = N - a1 - a2;
+        if (s2(w, 2) != a1 || s2(w, 3) != a2) return "2D elevation stencil weights";
+        if ((a0 > 0 && b != pos2(N - 1, a1, a2)) || (a1 > 0 && b - 1 != pos2(N - 1, a1 - 1, a2)) ||
+            (a2 > 0 && b - s2(w, 1) != pos2(N - 1, a1, a2 - 1)))
+          return "2D elevation stencil offsets";
+      }
+  }
+  // product gather: gamma - beta in the degree-N lattice, Np where gamma !>= beta
+  {
+    int c = 0;
+    for (int l = 0; l <= N + M; ++l)
+      for (int k = 0; k <= N + M - l; ++k)
+        for (int j = 0; j <= N + M - l - k; ++j, ++c) {
+          int b = 0;
+          for (int bl = 0; bl <= M; ++bl)
+            for (int bk = 0; bk <= M - bl; ++bk)
+              for (int bj = 0; bj <= M - bl - bk; ++bj, ++b) {
+                const int g0 = N + M - j - k - l, b0 = M - bj - bk - bl;
+                int want = g0 >= b0 ? pos3(N, j - bj, k - bk, l - bl) : -1;
+                if (want < 0) want = Tb::Np;
+                const uint32_t w = t.prod2[(b / 2) * Tb::NMp + c];
+                const int got = int((b & 1) ? (w >> 16) : (w & 0xffffu));
+                if (got != want) return "product gather index";
+              }
+        }
+  }
+  // face maps and lift gather slots
+  for (int i = 0; i < 4 * Tb::Nfp; ++i)
+    if (t.fidx[i] >= Tb::Np) return "own face index out of range";
+  for (int i = 0; i < 24 * Tb::Nfp; ++i)
+    if (t.nidx[i] >= Tb::Np) return "neighbour face index out of range";
+  {
+    int c = 0;
+    for (int l = 0; l <= N; ++l)
+      for (int k = 0; k <= N - l; ++k)
+        for (int j = 0; j <= N - l - k; ++j, ++c) {
+          const int a[4] = {N - j - k - l, j, k, l};
+          for (int f = 0; f < 4; ++f) {
+            const int slot = int((t.lgat[c] >> (8 * f)) & 255u);
+            if (slot < lift_level_base(N, a[f]) || slot >= lift_level_base(N, a[f] + 1))
+              return "lift gather slot outside its level";
+          }
+        }
+  }
+  for (int i = 0; i <= N; ++i)
+    if (!(t.cj[i] == t.cj[i]) || !(t.lscale[i] != real(0))) return "projection or lift constants";
+  return nullptr;
+}
+
 }  // namespace bbw

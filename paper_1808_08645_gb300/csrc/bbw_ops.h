@@ -27,6 +27,8 @@ struct KernelOps {
   void (*launch_shape)(int M, bool dbl, int* team, int* group_width, int* groups_per_cta);
   // launch the spatial operator alone (StageParams, output in qout)
   cudaError_t (*launch_spatial)(int M, bool dbl, const void* params, int grid, cudaStream_t s);
+  // host-only: build the tables and check them against brute force (nullptr: all agree)
+  const char* (*check_tables)(int M, bool dbl, const double* cj);
 };
 
 const KernelOps& ops_n1();

@@ -70,6 +70,16 @@ void build(int M, bool dbl, const double* cj, void* buf) {
   });
 }
 
+const char* check_tables(int M, bool dbl, const double* cj) {
+  return dispatch(M, dbl, [&]<int MM, typename real>() -> const char* {
+    auto* t = new Tables<kN, MM, real>();
+    build_tables<kN, MM, real>(*t, cj);
+    const char* msg = validate_tables<kN, MM, real>(*t);
+    delete t;
+    return msg;
+  });
+}
+
 void face_maps(int* fidx, int* nidx) {
   auto* t = new Tables<kN, 0, double>();
   const double cj[kN + 1] = {};
@@ -128,8 +138,8 @@ cudaError_t launch_wadg(int M, bool dbl, const void* params, int grid, cudaStrea
 #define BBW_CAT2(a, b) a##b
 #define BBW_CAT(a, b) BBW_CAT2(a, b)
 const KernelOps& BBW_CAT(ops_n, BBW_N)() {
-  static const KernelOps ops = {&tables_size, &build,       &face_maps,   &prepare,     &launch_stage,
-                                &launch_wadg, &launch_shape, &launch_spatial};
+  static const KernelOps ops = {&tables_size, &build,       &face_maps,      &prepare,     &launch_stage,
+                                &launch_wadg, &launch_shape, &launch_spatial, &check_tables};
   return ops;
 }
 

@@ -135,3 +135,20 @@ def test_no_cpu_fallback_when_library_missing(monkeypatch, tmp_path):
     monkeypatch.setattr(B, "lib_path", lambda: str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         B.projection_coeffs(2, 1)
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("M", [0, 1, 2, 3])
+def test_operator_tables_agree_with_brute_force(M, prec):
+    """Every stencil word, product index, face map and lift slot the kernels
+    use, for all N, recomputed by enumeration of the multi-index lattice
+    (host only)."""
+    for N in range(1, 10):
+        B.validate_tables(N, M, prec)
+
+
+def test_table_validation_rejects_bad_arguments():
+    with pytest.raises(B.BBWError, match="BBW_ERR_UNSUPPORTED"):
+        B.validate_tables(10, 2, 32)
+    with pytest.raises(B.BBWError, match="BBW_ERR_ARG"):
+        B.validate_tables(3, 2, 16)
