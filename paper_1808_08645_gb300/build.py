@@ -5,7 +5,11 @@ Compiles every ``csrc/*.cu`` translation unit with nvcc in parallel (one
 ``paper_1808_08645_gb300/_lib/libbbwadg.so``. Objects go to ``_build/``.
 Only rebuilds objects whose sources or headers are newer.
 
-Usage: ``python -m paper_1808_08645_gb300.build [--force] [--jobs J]``
+``--checked`` builds the range-checked variant instead
+(``_lib/libbbwadg_checked.so``, kernels compiled with ``BBW_CHECKED``), used
+by the tests as a stand-in for a memory checker.
+
+Usage: ``python -m paper_1808_08645_gb300.build [--force] [--jobs J] [--checked]``
 """
 from __future__ import annotations
 
@@ -49,8 +53,8 @@ def _stale(obj: str, src: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in [src, *deps])
 
 
-def _compile(src: str, obj: str, verbose: bool) -> str:
-    cmd = [nvcc(), *ARCH, *FLAGS, "-c", src, "-o", obj]
+def _compile(src: str, obj: str, verbose: bool, defines=()) -> str:
+    cmd = [nvcc(), *ARCH, *FLAGS, *[f"-D{d}" for d in defines], "-c", src, "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     p = subprocess.run(cmd, capture_output=True, text=True)
@@ -59,29 +63,32 @@ def _compile(src: str, obj: str, verbose: bool) -> str:
     return p.stderr
 
 
-def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, jobs: int | None = None, verbose: bool = False, checked: bool = False) -> str:
+    build_dir = BUILD + ("_checked" if checked else "")
+    lib = LIB.replace(".so", "_checked.so") if checked else LIB
+    defines = ("BBW_CHECKED",) if checked else ()
+    os.makedirs(build_dir, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     deps = _headers()
-    objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    objs = [os.path.join(build_dir, os.path.basename(s)[:-3] + ".o") for s in srcs]
     todo = [(s, o) for s, o in zip(srcs, objs) if force or _stale(o, s, deps)]
     if todo:
         jobs = jobs or min(len(todo), os.cpu_count() or 4)
         with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
-            futs = {ex.submit(_compile, s, o, verbose): s for s, o in todo}
+            futs = {ex.submit(_compile, s, o, verbose, defines): s for s, o in todo}
             for f in cf.as_completed(futs):
                 log = f.result()
                 if verbose and log:
                     sys.stderr.write(log)
-    if todo or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
-        tmp = LIB + ".tmp"
+    if todo or not os.path.exists(lib) or any(os.path.getmtime(o) > os.path.getmtime(lib) for o in objs):
+        tmp = lib + ".tmp"
         cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcublas"]
         p = subprocess.run(cmd, capture_output=True, text=True)
         if p.returncode != 0:
             raise RuntimeError(f"link failed:\n{p.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
@@ -89,5 +96,6 @@ if __name__ == "__main__":
     ap.add_argument("--force", action="store_true")
     ap.add_argument("--jobs", type=int, default=None)
     ap.add_argument("--verbose", action="store_true")
+    ap.add_argument("--checked", action="store_true")
     a = ap.parse_args()
-    print(build(a.force, a.jobs, a.verbose))
+    print(build(a.force, a.jobs, a.verbose, a.checked))

@@ -588,6 +588,7 @@ bbw_status check_status(bbw_solver* s) {
   BBW_CUDA(cudaMemcpy(&st, s->d_status, sizeof(st), cudaMemcpyDeviceToHost));
   if (st) {
     BBW_CUDA(cudaMemset(s->d_status, 0, sizeof(unsigned int)));
+    if (st & 2u) return fail(BBW_ERR_MESH, "the checked stage kernel met a neighbour or table index out of range");
     return fail(BBW_ERR_NONFINITE, "the stage kernel produced a non-finite value");
   }
   return BBW_OK;

@@ -298,6 +298,16 @@ __device__ __forceinline__ void team_sync() {
   }
 }
 
+// Checked build (BBW_CHECKED defined): indices that come from run-time data
+// (the packed neighbour words) or from a table are range-checked before use;
+// a failing check skips the access and raises status bit 1 (value 2). The
+// normal build compiles none of it.
+#ifdef BBW_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+
 struct Stencil3 {
   int base, dk, dl, w1, w2, w3;
 };
@@ -523,6 +533,8 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
   const int64_t stride = int64_t(gridDim.x) * GC;
   const bool read_res = P.a != real(0);
   bool bad = false;
+  bool oob = false;  // checked build only: an index out of range was met
+  (void)oob;
   // cursor into the source groups: the first one at or after this team's
   // first group (the team's groups only increase; group indices fit 32 bits)
   const int nsg = int(P.n_src_groups);
@@ -609,7 +621,19 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
         const int c = CS[f * V + v];
         if (c >= 0) {
           const int64_t nb = int64_t(c >> 5);
+          if constexpr (kChecked) {
+            if (nb >= G * V || (c & 7) >= 6) {
+              oob = true;
+              continue;
+            }
+          }
           const int ni = tab.nidx[(((c >> 3) & 3) * 6 + (c & 7)) * Nfp + a];
+          if constexpr (kChecked) {
+            if (ni >= Np) {
+              oob = true;
+              continue;
+            }
+          }
           const int64_t gq = nb / V;
           const real* src = P.qin + (size_t(gq) * QV + ni) * V + (nb - gq * V);
 #pragma unroll
@@ -652,7 +676,13 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
       for (int it = t; it < 4 * Nfp; it += T) {
         const int f = it / Nfp;
         const int a = it - f * Nfp;
-        const int io = tab.fidx[it];
+        int io = tab.fidx[it];
+        if constexpr (kChecked) {
+          if (io >= Np) {
+            oob = true;
+            io = 0;
+          }
+        }
         const vt pm = vld<real, V>(Q + io * V), um = vld<real, V>(Q + (Np + io) * V),
                  vm = vld<real, V>(Q + (2 * Np + io) * V), wm = vld<real, V>(Q + (3 * Np + io) * V);
         vt pp = vld<real, V>(trace(0, f, a)), up = vld<real, V>(trace(1, f, a)),
@@ -792,7 +822,13 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
           const uint32_t lg = tab.lgat[i];
 #pragma unroll
           for (int f = 0; f < 4; ++f) {
-            const int o = int((lg >> (8 * f)) & 255u);
+            int o = int((lg >> (8 * f)) & 255u);
+            if constexpr (kChecked) {
+              if (o >= Np) {
+                oob = true;
+                o = 0;
+              }
+            }
             const vt gu = vld<real, V>(pyr(1, f, o));
             ad = vaxpy(ad, real(1), vld<real, V>(pyr(0, f, o)));
 #pragma unroll
@@ -892,6 +928,9 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
     team_sync<T>();  // the next group reuses this team's shared region
   }
   if (bad) atomicOr(P.status, 1u);
+  if constexpr (kChecked) {
+    if (oob) atomicOr(P.status, 2u);
+  }
 }
 
 // The weight-adjusted update alone: out = P^{N+M}_N (c2 * rhs) per element,
