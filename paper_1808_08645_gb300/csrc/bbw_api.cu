@@ -524,36 +524,42 @@ namespace {
 // their centroids (10 bits per axis over the mesh's bounding box; ties keep
 // the caller's order), so that face neighbours are close in memory and their
 // traces are more often still in L2 when gathered.
-bbw_status renumber_elements(bbw_solver* s) {
+// With ranges, elements are reordered only within each [lo, hi) range (each
+// with its own bounding box) and elements outside every range keep their
+// place.
+bbw_status renumber_elements(bbw_solver* s, const std::vector<std::pair<int64_t, int64_t>>& ranges) {
   const int64_t K = s->K;
-  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   std::vector<double> cen(size_t(K) * 3, 0.0);
   for (int64_t e = 0; e < K; ++e)
     for (int v = 0; v < 4; ++v)
-      for (int d = 0; d < 3; ++d) {
-        const double x = s->vxyz[size_t(s->etov[size_t(e) * 4 + v]) * 3 + d];
-        cen[size_t(e) * 3 + d] += 0.25 * x;
-        lo[d] = std::min(lo[d], x);
-        hi[d] = std::max(hi[d], x);
-      }
+      for (int d = 0; d < 3; ++d) cen[size_t(e) * 3 + d] += 0.25 * s->vxyz[size_t(s->etov[size_t(e) * 4 + v]) * 3 + d];
   auto spread = [](uint64_t v) {
     uint64_t r = 0;
     for (int b = 0; b < 10; ++b) r |= ((v >> b) & 1u) << (3 * b);
     return r;
   };
-  std::vector<uint64_t> key(static_cast<size_t>(K), 0);
-  for (int64_t e = 0; e < K; ++e) {
-    uint64_t k = 0;
-    for (int d = 0; d < 3; ++d) {
-      const double w = hi[d] > lo[d] ? (cen[size_t(e) * 3 + d] - lo[d]) / (hi[d] - lo[d]) : 0.0;
-      const uint64_t q = uint64_t(std::min(1023.0, std::max(0.0, std::floor(w * 1024.0))));
-      k |= spread(q) << d;
-    }
-    key[size_t(e)] = k;
-  }
   s->perm.resize(size_t(K));
   for (int64_t e = 0; e < K; ++e) s->perm[size_t(e)] = int32_t(e);
-  std::stable_sort(s->perm.begin(), s->perm.end(), [&](int32_t a, int32_t b) { return key[size_t(a)] < key[size_t(b)]; });
+  std::vector<uint64_t> key(static_cast<size_t>(K), 0);
+  for (const auto& [r0, r1] : ranges) {
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t e = r0; e < r1; ++e)
+      for (int d = 0; d < 3; ++d) {
+        lo[d] = std::min(lo[d], cen[size_t(e) * 3 + d]);
+        hi[d] = std::max(hi[d], cen[size_t(e) * 3 + d]);
+      }
+    for (int64_t e = r0; e < r1; ++e) {
+      uint64_t k = 0;
+      for (int d = 0; d < 3; ++d) {
+        const double w = hi[d] > lo[d] ? (cen[size_t(e) * 3 + d] - lo[d]) / (hi[d] - lo[d]) : 0.0;
+        const uint64_t q = uint64_t(std::min(1023.0, std::max(0.0, std::floor(w * 1024.0))));
+        k |= spread(q) << d;
+      }
+      key[size_t(e)] = k;
+    }
+    std::stable_sort(s->perm.begin() + r0, s->perm.begin() + r1,
+                     [&](int32_t a, int32_t b) { return key[size_t(a)] < key[size_t(b)]; });
+  }
   s->inv.resize(size_t(K));
   for (int64_t e = 0; e < K; ++e) s->inv[size_t(s->perm[size_t(e)])] = int32_t(e);
   BBW_CUDA(cudaMalloc(reinterpret_cast<void**>(&s->d_perm), size_t(K) * sizeof(int32_t)));
@@ -641,13 +647,15 @@ const char* bbw_last_error(void) { return g_err.c_str(); }
 
 bbw_status bbw_create(int64_t nverts, const double* vxyz, int64_t K, const int64_t* etov, int N, int M,
                       int precision, void* cuda_stream, bbw_solver** out) {
-  return bbw::create_solver(nverts, vxyz, K, etov, N, M, precision, cuda_stream, true, out);
+  const std::vector<std::pair<int64_t, int64_t>> all = {{0, K}};
+  return bbw::create_solver(nverts, vxyz, K, etov, N, M, precision, cuda_stream, &all, out);
 }
 
 }  // extern "C"
 
 bbw_status bbw::create_solver(int64_t nverts, const double* vxyz, int64_t K, const int64_t* etov, int N, int M,
-                              int precision, void* cuda_stream, bool renumber, bbw_solver** out) {
+                              int precision, void* cuda_stream,
+                              const std::vector<std::pair<int64_t, int64_t>>* renumber, bbw_solver** out) {
   if (!out) return fail(BBW_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (!vxyz || !etov || nverts <= 0 || K <= 0) return fail(BBW_ERR_ARG, "empty mesh or NULL array");
@@ -665,8 +673,13 @@ bbw_status bbw::create_solver(int64_t nverts, const double* vxyz, int64_t K, con
     free_solver(s);
     return st;
   }
-  if (renumber) {
-    st = renumber_elements(s);
+  if (renumber && !renumber->empty()) {
+    for (const auto& [r0, r1] : *renumber)
+      if (r0 < 0 || r1 > K || r0 > r1) {
+        free_solver(s);
+        return fail(BBW_ERR_ARG, "renumbering range out of bounds");
+      }
+    st = renumber_elements(s, *renumber);
     if (st != BBW_OK) {
       free_solver(s);
       return st;

@@ -200,26 +200,30 @@ bbw_status build_graph(bbw_batch* b, int parity, double dt) {
   return BBW_OK;
 }
 
+// Member element e (the caller's order, 0 <= e < K) sits at internal slot
+// s->slot(e0 + e) - e0 of the member's groups (renumbered within the member).
 template <typename T>
-void fill_member_state(const bbw_solver* s, const double* src, int64_t K, T* p) {
+void fill_member_state(const bbw_solver* s, const double* src, int64_t e0, int64_t K, T* p) {
   // [G_i][4][Np][V] from [4][K][Np]; padding lanes zero
   const int Np = s->Np, V = s->V;
   const int64_t Gi = (K + V - 1) / V;
   std::memset(p, 0, size_t(Gi) * 4 * Np * V * sizeof(T));
   for (int f = 0; f < 4; ++f)
     for (int64_t e = 0; e < K; ++e) {
+      const int64_t ie = s->slot(e0 + e) - e0;
       const double* row = src + (size_t(f) * K + e) * Np;
-      for (int i = 0; i < Np; ++i) p[((size_t(e / V) * 4 + f) * Np + i) * V + size_t(e % V)] = T(row[i]);
+      for (int i = 0; i < Np; ++i) p[((size_t(ie / V) * 4 + f) * Np + i) * V + size_t(ie % V)] = T(row[i]);
     }
 }
 
 template <typename T>
-void take_member_state(const bbw_solver* s, const T* p, int64_t K, double* dst) {
+void take_member_state(const bbw_solver* s, const T* p, int64_t e0, int64_t K, double* dst) {
   const int Np = s->Np, V = s->V;
   for (int f = 0; f < 4; ++f)
     for (int64_t e = 0; e < K; ++e) {
+      const int64_t ie = s->slot(e0 + e) - e0;
       double* row = dst + (size_t(f) * K + e) * Np;
-      for (int i = 0; i < Np; ++i) row[i] = double(p[((size_t(e / V) * 4 + f) * Np + i) * V + size_t(e % V)]);
+      for (int i = 0; i < Np; ++i) row[i] = double(p[((size_t(ie / V) * 4 + f) * Np + i) * V + size_t(ie % V)]);
     }
 }
 
@@ -232,9 +236,9 @@ bbw_status upload_member_state(bbw_batch* b, int i, const double* src, void* bas
   bbw_status st = bbw::ensure_pinned(s, n * 8);
   if (st != BBW_OK) return st;
   if (s->prec == 64)
-    fill_member_state(s, src, m.K, static_cast<double*>(s->pinned));
+    fill_member_state(s, src, m.e0, m.K, static_cast<double*>(s->pinned));
   else
-    fill_member_state(s, src, m.K, static_cast<float*>(s->pinned));
+    fill_member_state(s, src, m.e0, m.K, static_cast<float*>(s->pinned));
   char* dst = static_cast<char*>(base) + size_t(m.e0) * 4 * s->Np * s->rsz();
   BBW_CUDA(cudaMemcpyAsync(dst, s->pinned, n * s->rsz(), cudaMemcpyHostToDevice, b->stream));
   BBW_CUDA(cudaStreamSynchronize(b->stream));
@@ -252,9 +256,9 @@ bbw_status download_member_state(bbw_batch* b, int i, const void* base, double* 
   BBW_CUDA(cudaMemcpyAsync(s->pinned, src, n * s->rsz(), cudaMemcpyDeviceToHost, b->stream));
   BBW_CUDA(cudaStreamSynchronize(b->stream));
   if (s->prec == 64)
-    take_member_state(s, static_cast<const double*>(s->pinned), m.K, dst);
+    take_member_state(s, static_cast<const double*>(s->pinned), m.e0, m.K, dst);
   else
-    take_member_state(s, static_cast<const float*>(s->pinned), m.K, dst);
+    take_member_state(s, static_cast<const float*>(s->pinned), m.e0, m.K, dst);
   return BBW_OK;
 }
 
@@ -264,8 +268,8 @@ bbw_status upload_sources(bbw_batch* b, bbw_batch::Bucket& k) {
   const int V = k.s->V;
   std::map<int64_t, std::vector<int32_t>> groups;
   for (size_t slot = 0; slot < k.src_elem.size(); ++slot) {
-    const int64_t e = k.src_elem[slot];
-    if (e < 0) continue;
+    if (k.src_elem[slot] < 0) continue;
+    const int64_t e = k.s->slot(k.src_elem[slot]);  // internal position of the source element
     auto& lanes = groups.try_emplace(e / V, std::vector<int32_t>(size_t(V), -1)).first->second;
     lanes[size_t(e % V)] = int32_t(slot);
   }
@@ -350,9 +354,12 @@ bbw_status bbw_batch_create(int n, const int64_t* nverts, const double* const* v
       }
     }
     if (e >= bbw::kMaxElements) return bail(fail(BBW_ERR_ARG, "too many elements of one degree (limit 2^26)"));
-    // the caller's element order is kept: each instance stays one contiguous range
+    // elements are renumbered for locality within each instance only, so that
+    // every instance stays one contiguous range of groups
+    std::vector<std::pair<int64_t, int64_t>> ranges;
+    for (int i : ids) ranges.emplace_back(b->members[size_t(i)].e0, b->members[size_t(i)].e0 + K[i]);
     bbw_status st = bbw::create_solver(int64_t(xyz.size() / 3), xyz.data(), e, tets.data(), deg, M, precision,
-                                       b->stream, false, &k.s);
+                                       b->stream, &ranges, &k.s);
     if (st != BBW_OK) return bail(st);
     k.src_elem.assign(ids.size(), -1);
     k.grid0 = k.s->grid_stage;
@@ -429,7 +436,8 @@ bbw_status bbw_batch_set_c2(bbw_batch* b, int i, const double* c2) {
     using T = std::remove_pointer_t<decltype(p)>;
     for (int64_t e = 0; e < Gi * V; ++e)
       for (int w = 0; w < Mp; ++w)
-        p[(size_t(e / V) * Mp + w) * V + size_t(e % V)] = T(e < m.K ? c2[size_t(e) * Mp + w] : 1.0);
+        p[(size_t(e / V) * Mp + w) * V + size_t(e % V)] =
+            T(e < m.K ? c2[size_t(s->user(m.e0 + e) - m.e0) * Mp + w] : 1.0);
   };
   if (s->prec == 64)
     fill(static_cast<double*>(s->pinned));

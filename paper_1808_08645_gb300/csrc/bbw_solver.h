@@ -8,6 +8,7 @@
 #include <array>
 #include <cstdint>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "bbw_common.h"
@@ -102,10 +103,13 @@ cudaError_t copy_to_internal(const void* src, int src_prec, void* dst, int dst_p
                              const int32_t* perm, cudaStream_t s);
 cudaError_t copy_to_user(const void* src, int src_prec, void* dst, int dst_prec, int64_t K, int Np, int V,
                          const int32_t* inv, cudaStream_t s);
-// Create a solver (as bbw_create); renumber: order the elements internally
-// by a Morton key of their centroids (false: keep the caller's order).
+// Create a solver (as bbw_create). renumber: element ranges [lo, hi) within
+// which the elements are ordered internally by the Morton key of their
+// centroids (each range over its own bounding box); NULL or empty: keep the
+// caller's order.
 bbw_status create_solver(int64_t nverts, const double* vxyz, int64_t K, const int64_t* etov, int N, int M,
-                         int precision, void* cuda_stream, bool renumber, bbw_solver** out);
+                         int precision, void* cuda_stream, const std::vector<std::pair<int64_t, int64_t>>* renumber,
+                         bbw_solver** out);
 // n!, the degree-n multi-indices (alpha_0..alpha_3) in the library order, and
 // a solve with the normalised degree-n Bernstein mass matrix (in place;
 // false if the factorisation fails).
