@@ -22,6 +22,13 @@ and Ricker source per instance) advanced together by graph-replayed batch
 steps, against the same instances stepped one after another by solo solvers
 ("plain"); the line reports the speedup, both throughputs and the largest
 relative L2 difference between the two final states.
+
+``--workload elastic`` measures the elastic stage kernel (the velocity-stress
+system of Sec. 2.2, nine fields, matrix-weighted update) on the same mesh:
+N = 1..9, M = 2 media (rho^{-1}, lambda, mu from seeded smooth random fields),
+a Gaussian compressional pulse, interleaved by stage as above; the metric is
+9 K N_p / t_stage. ``--impl reference --workload elastic`` times the FP64
+elastic oracle on a sub-cube.
 """
 from __future__ import annotations
 
@@ -57,6 +64,15 @@ def algorithmic_bytes_per_element(N: int, M: int, real: int = 4) -> float:
     and not counted.
     """
     vals = (12 + 4 * 4 / 5) * np3(N) + np3(M) + 9
+    return vals * real + 16
+
+
+def elastic_bytes_per_element(N: int, M: int, real: int = 4) -> float:
+    """Bytes one elastic stage must move per element, averaged over the five
+    stages: q_in read, q_out and res written (27 N_p values), res read
+    (9 N_p) on stages 1-4, the three media polynomials (3 M_p values),
+    geometry (9 values) and the packed connectivity (16 B)."""
+    vals = (27 + 9 * 4 / 5) * np3(N) + 3 * np3(M) + 9
     return vals * real + 16
 
 
@@ -313,24 +329,27 @@ def run_e2e(solvers, host_q0, Ns, dts, K, steps, stream):
 # the sources that decide the stage kernel's memory traffic: the kernel and
 # its tables, and the host code that lays out and orders the elements
 KERNEL_SOURCES = ("bbw_stage.cuh", "bbw_common.h", "bbw_stage_inst.cuh", "bbw_api.cu")
+# the same for the elastic stage kernel
+ELASTIC_SOURCES = ("bbw_elastic.cuh", "bbw_stage.cuh", "bbw_common.h", "bbw_elastic_inst.cuh",
+                   "bbw_elastic.cu", "bbw_api.cu")
 
 
-def kernel_sources_sha256() -> str:
+def sources_sha256(names) -> str:
     import hashlib
     h = hashlib.sha256()
-    for name in KERNEL_SOURCES:
+    for name in names:
         with open(os.path.join(ROOT, "paper_1808_08645_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
 
-def load_traffic(N: int):
-    """DRAM bytes per launch of the degree-N stage kernel from a committed ncu
-    summary (profiles/stage_kernel_n<N>_*dram_traffic.md, its
-    ``machine-readable:`` line). None when there is no capture for N or when
-    the kernel sources changed since the counters were taken."""
+def kernel_sources_sha256() -> str:
+    return sources_sha256(KERNEL_SOURCES)
+
+
+def _traffic_from_profiles(pattern: str, N: int, sha: str):
     import glob
-    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", f"stage_kernel_n{N}_*dram_traffic.md"))):
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", pattern))):
         with open(path) as fh:
             for line in fh:
                 if line.startswith("machine-readable:"):
@@ -338,9 +357,23 @@ def load_traffic(N: int):
                         data = json.loads(line.split(":", 1)[1])
                     except ValueError:
                         continue
-                    if data.get("N") == N and data.get("kernel_sources_sha256") == kernel_sources_sha256():
+                    if data.get("N") == N and data.get("kernel_sources_sha256") == sha:
                         return float(data["traffic_bytes_per_launch"])
     return None
+
+
+def load_traffic(N: int):
+    """DRAM bytes per launch of the degree-N stage kernel from a committed ncu
+    summary (profiles/stage_kernel_n<N>_*dram_traffic.md, its
+    ``machine-readable:`` line). None when there is no capture for N or when
+    the kernel sources changed since the counters were taken."""
+    return _traffic_from_profiles(f"stage_kernel_n{N}_*dram_traffic.md", N, kernel_sources_sha256())
+
+
+def load_elastic_traffic(N: int):
+    """As load_traffic, for the elastic stage kernel
+    (profiles/elastic_stage_kernel_n<N>_*dram_traffic.md)."""
+    return _traffic_from_profiles(f"elastic_stage_kernel_n{N}_*dram_traffic.md", N, sources_sha256(ELASTIC_SOURCES))
 
 
 # ---------------------------------------------------------------------------
@@ -594,6 +627,203 @@ def run_adjoint(args):
     }
 
 
+# ---------------------------------------------------------------------------
+# elastic workload
+
+def _elastic_setup(hexes: int, N: int, M: int):
+    vxyz, etov = inputs.cube_mesh(hexes)
+    media = inputs.elastic_media(vxyz, etov, M, seed=inputs.ELASTIC_CONFIG["seed"])
+    return vxyz, etov, media, inputs.elastic_pulse(vxyz, etov, N)
+
+
+def _elastic_oracle_sample(hexes: int, Ns, reps: int):
+    """Time `reps` FP64 elastic oracle stages per degree on a hexes^3 x 6
+    sub-cube; returns (DOF updates, seconds)."""
+    from oracle.elastic import ElasticOracle
+    M = inputs.ELASTIC_CONFIG["M"]
+    dofs, secs = 0, 0.0
+    for N in Ns:
+        vxyz, etov, media, q0 = _elastic_setup(hexes, N, M)
+        orc = ElasticOracle(vxyz, etov, N, M, *media)
+        res = np.zeros_like(q0)
+        orc.stage(q0, res, 0, 1e-4)  # warm caches
+        t = time.perf_counter()
+        q, r = q0, res
+        for i in range(reps):
+            q, r = orc.stage(q, r, i % 5, 1e-4)
+        secs += time.perf_counter() - t
+        dofs += reps * 9 * len(etov) * np3(N)
+    return dofs, secs
+
+
+def elastic_cpu_baseline(args):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    Ns = [int(x) for x in args.Ns.split(",")]
+    hexes, reps = 2, 3
+    code = (f"import sys, json; sys.path.insert(0, {ROOT!r}); import bench; "
+            f"d, s = bench._elastic_oracle_sample({hexes}, {Ns!r}, {reps}); print(json.dumps([d, s]))")
+    p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if p.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": "failed: " + p.stderr.strip().splitlines()[-1] if p.stderr else "failed"}
+    d, s = json.loads(p.stdout.strip().splitlines()[-1])
+    return {"value": d / s, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{reps} FP64 elastic oracle stages per degree N={Ns[0]}..{Ns[-1]} on the "
+                      f"{hexes}^3 x 6 = {6 * hexes ** 3}-tet sub-cube of the same workload (same media "
+                      f"recipe and pulse); {s:.1f} s of CPU work, 1 thread"}
+
+
+def run_elastic_reference(args):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return None
+    Ns = [int(x) for x in args.Ns.split(",")]
+    hexes = 2
+    for _ in range(args.warmup):
+        _elastic_oracle_sample(hexes, Ns, 1)
+    dofs_total, secs_total = 0, 0.0
+    for _ in range(args.steps):
+        d, s = _elastic_oracle_sample(hexes, Ns, 1)
+        dofs_total += d
+        secs_total += s
+    value = dofs_total / secs_total
+    K = 6 * hexes ** 3
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs_total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"FP64 elastic oracle: one stage per degree N={Ns[0]}..{Ns[-1]} on the "
+                               f"{hexes}^3 x 6 = {K}-tet sub-cube of the elastic workload",
+                   "Ns": Ns, "M": inputs.ELASTIC_CONFIG["M"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{K}-tet sub-cube, one stage per degree per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def run_elastic(args):
+    import torch
+
+    from paper_1808_08645_gb300 import binding as B
+    from paper_1808_08645_gb300 import build as libbuild
+
+    libbuild.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    cfg = inputs.ELASTIC_CONFIG
+    M = cfg["M"]
+    Ns = [int(x) for x in args.Ns.split(",")]
+    vxyz, etov = inputs.cube_mesh(args.hexes)
+    K = len(etov)
+    media = inputs.elastic_media(vxyz, etov, M, seed=cfg["seed"])
+    stream = torch.cuda.Stream()
+    solvers = {}
+    for N in Ns:
+        s = B.ElasticSolver(vxyz, etov, N, M, B.F32, stream=stream.cuda_stream)
+        s.set_media(*media)
+        s.set_state(inputs.elastic_pulse(vxyz, etov, N))
+        solvers[N] = s
+    dts = {N: solvers[N].cfl_dt(cfg["cfl"]) for N in Ns}
+
+    def sweep_step(events=None):
+        for st in range(5):
+            for N in Ns:
+                if events is not None:
+                    events[N][st][0].record(stream)
+                solvers[N].stage(st, dts[N])
+                if events is not None:
+                    events[N][st][1].record(stream)
+
+    for _ in range(args.warmup):
+        sweep_step()
+    torch.cuda.synchronize()
+    ev = [{N: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(5)] for N in Ns} for _ in range(args.steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.synchronize()
+    clocks.start()
+    t0.record(stream)
+    for k in range(args.steps):
+        sweep_step(ev[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    for s in solvers.values():
+        s.sync()
+    total_ms = t0.elapsed_time(t1)
+    kern_ms = {N: [sum(ev[k][N][st][0].elapsed_time(ev[k][N][st][1]) for st in range(5))
+                   for k in range(args.steps)] for N in Ns}
+    per_n = {}
+    for N in Ns:
+        t_stage = statistics.median(kern_ms[N]) / 5 / 1e3
+        per_n[str(N)] = {"dof_updates_per_s": 9 * K * np3(N) / t_stage, "us_per_stage": t_stage * 1e6,
+                         "achieved_gbs": elastic_bytes_per_element(N, M) * K / t_stage / 1e9}
+    value = sum(5 * 9 * K * np3(N) for N in Ns) * args.steps / (total_ms / 1e3)
+    top = max(Ns, key=lambda N: statistics.median(kern_ms[N]))
+    t_launch = statistics.mean([x / 5 for x in kern_ms[top]]) / 1e3
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = elastic_bytes_per_element(top, M) * K / t_launch / 1e9
+
+    # end to end, one degree at a time: pinned host FP64 in, steps, pinned host FP64 out
+    e2e_steps = max(1, args.e2e_steps // 4)
+    wall, h2d, d2h, dofs = 0.0, 0, 0, 0
+    for N in Ns:
+        q0 = inputs.elastic_pulse(vxyz, etov, N)
+        pin_in = torch.empty(q0.size, dtype=torch.float64, pin_memory=True).numpy()
+        pin_in[:] = q0.ravel()
+        pin_out = torch.empty(q0.size, dtype=torch.float64, pin_memory=True).numpy()
+        pin_out[:] = 0.0
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        solvers[N].set_state(pin_in)
+        solvers[N].step(dts[N], e2e_steps)
+        solvers[N].get_state(out=pin_out)
+        torch.cuda.synchronize()
+        wall += time.perf_counter() - t
+        h2d += pin_in.nbytes
+        d2h += pin_out.nbytes
+        dofs += 5 * e2e_steps * 9 * K * np3(N)
+        del pin_in, pin_out
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {
+            "workload": f"BBWADG elastic (velocity-stress, 9 fields) LSRK4 stage sweep, {args.hexes}^3 hexes "
+                        f"x 6 = {K} affine tets, N={Ns[0]}..{Ns[-1]}, M={M}, smooth random rho, lambda, mu "
+                        "with planar layer jump, Gaussian compressional pulse",
+            "mesh_elements": K, "Ns": Ns, "M": M,
+            "step": "one LSRK4 step (5 stages) per degree, interleaved by stage",
+            "l2": "inputs larger than L2: between two stages of one degree the other degrees stream "
+                  "several GB through the 129 MB L2",
+            "parallelism": "replicas x1"},
+        "sweep": per_n,
+        "roofline": {"bound": "hbm", "kernel": f"elastic_stage_kernel N={top} M={M} f32",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": load_elastic_traffic(top),
+                     "algorithmic_bytes_per_launch": elastic_bytes_per_element(top, M) * K,
+                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"},
+        "e2e": {"value": dofs / wall, "unit": UNIT, "h2d_bytes_per_step": h2d / e2e_steps,
+                "d2h_bytes_per_step": d2h / e2e_steps,
+                "note": f"per degree: bbw_elastic_set_state from pinned host FP64, {e2e_steps} RK steps, "
+                        "bbw_elastic_get_state into pinned host FP64"},
+        "gpu_launches": 5 * len(Ns) * args.steps,
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = elastic_cpu_baseline(args)
+    for s in solvers.values():
+        s.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -607,7 +837,7 @@ def main():
     ap.add_argument("--cpu-reps", type=int, default=15)
     ap.add_argument("--ref-hexes", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["sweep", "batched", "adjoint"], default="sweep")
+    ap.add_argument("--workload", choices=["sweep", "batched", "adjoint", "elastic"], default="sweep")
     ap.add_argument("--adjoint-steps", type=int, default=inputs.ADJOINT_CONFIG["steps"])
     ap.add_argument("--instances", type=int, default=inputs.BATCH_CONFIG["instances"])
     args = ap.parse_args()
@@ -622,6 +852,8 @@ def main():
             "impl": "reference", "workload": "batched",
             "unavailable": "the batched form has no oracle counterpart; its reference is plain one-by-one "
                            "solving, reported in the same line"}
+    elif args.workload == "elastic":
+        out = run_elastic_reference(args) if args.impl == "reference" else run_elastic(args)
     else:
         out = run_reference(args) if args.impl == "reference" else run_gpu(args)
     if out is not None:

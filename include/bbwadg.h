@@ -58,6 +58,7 @@ extern "C" {
 
 typedef struct bbw_solver bbw_solver; /* opaque, library-owned */
 typedef struct bbw_batch bbw_batch;   /* opaque, library-owned */
+typedef struct bbw_elastic bbw_elastic; /* opaque, library-owned */
 
 typedef enum bbw_status {
   BBW_OK = 0,
@@ -396,6 +397,61 @@ bbw_status bbw_batch_sync(bbw_batch* b);
 
 /* Time and number of steps since the last bbw_batch_set_time (or creation). */
 bbw_status bbw_batch_get_time(const bbw_batch* b, double* t, int64_t* steps);
+
+/* ---------------------------------------------------------------------------
+ * Elastic solver (Sec. 2.2): the velocity-stress system
+ *
+ *     rho dv/dt = sum_i A_i^T d sigma/dx_i,   C^{-1} dsigma/dt = sum_i A_i dv/dx_i
+ *
+ * with the isotropic constitutive matrix C(lambda, mu) and the matrix-weighted
+ * weight-adjusted update of Eq. (ewadg). One bbw_elastic_stage() is one LSRK
+ * stage over all elements in one fused GPU kernel: the Bernstein derivatives
+ * (Sec. 4), penalty fluxes
+ *     F_v = 1/2 A_n^T [[sigma]] + tau_v/2 A_n^T A_n [[v]],
+ *     F_s = 1/2 A_n [[v]] + tau_s/2 A_n A_n^T [[sigma]]    (A_n = sum_i n_i A_i),
+ * the factored lift, the products with the degree-M media polynomials and the
+ * telescoped projection of Eq. (20) (ten scalar projections per element:
+ * three with rho^{-1}, one with lambda, six with mu), and the LSRK update.
+ *
+ *  - State arrays are [9][K][N_p], fields (v_x, v_y, v_z, s_xx, s_yy, s_zz,
+ *    s_yz, s_xz, s_xy) in the multi-index order above.
+ *  - Media arrays (rho^{-1}, lambda, mu) are [K][M_p] Bernstein coefficients
+ *    of degree M; rho^{-1} coefficients must be > 0, lambda and mu >= 0.
+ *  - Walls are traction-free mirrors: sigma+ = -sigma, v+ = v.
+ *  - Ownership, streams and errors follow the acoustic solver; the mesh rules
+ *    and limits of bbw_create apply.
+ * ------------------------------------------------------------------------- */
+
+/* Create an elastic solver on the mesh (as bbw_create); media default to
+ * rho^{-1} = lambda = mu = 1, penalties tau_v = tau_s = 1, state 0. */
+bbw_status bbw_elastic_create(int64_t nverts, const double* vxyz, int64_t K, const int64_t* etov, int N, int M,
+                              int precision, void* cuda_stream, bbw_elastic** out);
+/* Wait for the solver's stream and free it (NULL: no-op). */
+void bbw_elastic_destroy(bbw_elastic* s);
+/* Sizes and precision (any pointer may be NULL). */
+bbw_status bbw_elastic_info(const bbw_elastic* s, int64_t* K, int* N, int* M, int* Np, int* Mp, int* precision);
+/* Media: rho_inv, lam, mu each [K][M_p]. BBW_ERR_NONPOS_C2 if a rho^{-1}
+ * coefficient is <= 0, a lambda or mu coefficient < 0, or any is not finite. */
+bbw_status bbw_elastic_set_media(bbw_elastic* s, const double* rho_inv, const double* lam, const double* mu);
+/* Penalty parameters (finite, >= 0); tau = 0 gives central fluxes. */
+bbw_status bbw_elastic_set_params(bbw_elastic* s, double tau_v, double tau_s);
+/* State q [9][K][N_p], RK residual res (NULL: zero) and time t. */
+bbw_status bbw_elastic_set_state(bbw_elastic* s, const double* q, const double* res, double t);
+/* Read back q and res ([9][K][N_p], either may be NULL) and t; waits and
+ * reports asynchronous failures as bbw_elastic_sync. */
+bbw_status bbw_elastic_get_state(bbw_elastic* s, double* q, double* res, double* t);
+/* One LSRK stage s in 0..4 with step dt (asynchronous). */
+bbw_status bbw_elastic_stage(bbw_elastic* s, int stage, double dt);
+/* nsteps full RK steps of size dt (asynchronous). */
+bbw_status bbw_elastic_step(bbw_elastic* s, double dt, int64_t nsteps);
+/* dt = cfl / (c_p,max (N+1)(N+3)/3 max_f |f|/|D|), c_p,max^2 bounded by the
+ * largest element value of max(lambda + 2 mu) max(rho^{-1}) (coefficients). */
+bbw_status bbw_elastic_cfl_dt(const bbw_elastic* s, double cfl, double* dt);
+/* Wait for the solver's stream; BBW_ERR_NONFINITE if a stage produced a NaN
+ * or Inf since the last check. */
+bbw_status bbw_elastic_sync(bbw_elastic* s);
+/* Time and number of stages since the last bbw_elastic_set_state. */
+bbw_status bbw_elastic_get_time(const bbw_elastic* s, double* t, int64_t* stages);
 
 #ifdef __cplusplus
 }

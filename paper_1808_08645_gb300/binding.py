@@ -14,7 +14,7 @@ import os
 
 import numpy as np
 
-__all__ = ["BBWError", "lib", "lib_path", "Solver", "Batch", "mesh_analyze", "projection_coeffs",
+__all__ = ["BBWError", "lib", "lib_path", "Solver", "Batch", "ElasticSolver", "mesh_analyze", "projection_coeffs",
            "lsrk_coeffs", "validate_tables", "wadg_update", "wadg_update_noalloc", "EXPORTS", "F32", "F64"]
 
 F32, F64 = 32, 64
@@ -85,6 +85,18 @@ EXPORTS = {
     "bbw_batch_autotune": (_int, [_p, _int, _ip, _dp]),
     "bbw_batch_sync": (_int, [_p]),
     "bbw_batch_get_time": (_int, [_p, _dp, _i64p]),
+    "bbw_elastic_create": (_int, [_i64, _dp, _i64, _i64p, _int, _int, _int, _p, C.POINTER(_p)]),
+    "bbw_elastic_destroy": (None, [_p]),
+    "bbw_elastic_info": (_int, [_p, _i64p, _ip, _ip, _ip, _ip, _ip]),
+    "bbw_elastic_set_media": (_int, [_p, _dp, _dp, _dp]),
+    "bbw_elastic_set_params": (_int, [_p, _d, _d]),
+    "bbw_elastic_set_state": (_int, [_p, _dp, _dp, _d]),
+    "bbw_elastic_get_state": (_int, [_p, _dp, _dp, _dp]),
+    "bbw_elastic_stage": (_int, [_p, _int, _d]),
+    "bbw_elastic_step": (_int, [_p, _d, _i64]),
+    "bbw_elastic_cfl_dt": (_int, [_p, _d, _dp]),
+    "bbw_elastic_sync": (_int, [_p]),
+    "bbw_elastic_get_time": (_int, [_p, _dp, _i64p]),
 }
 
 
@@ -467,3 +479,91 @@ class Batch:
         n = C.c_int64()
         _check(lib().bbw_batch_get_time(self._h, C.byref(t), C.byref(n)), "bbw_batch_get_time")
         return t.value, n.value
+
+
+class ElasticSolver:
+    """Owner of one ``bbw_elastic`` handle (the velocity-stress solver of
+    Sec. 2.2); methods map one-to-one to the ``bbw_elastic_*`` ABI. State
+    arrays are [9, K, Np]: (v_x, v_y, v_z, s_xx, s_yy, s_zz, s_yz, s_xz, s_xy)."""
+
+    NF = 9
+
+    def __init__(self, vxyz, etov, N: int, M: int, precision: int = F32, stream=None):
+        vxyz = _f64(vxyz)
+        etov = np.ascontiguousarray(etov, dtype=np.int64)
+        h = C.c_void_p()
+        _check(lib().bbw_elastic_create(len(vxyz), _ptr(vxyz, C.c_double), len(etov), _ptr(etov, C.c_int64),
+                                        N, M, precision, _dev(stream), C.byref(h)), "bbw_elastic_create")
+        self._h = h
+        self.K, self.N, self.M, self.precision = len(etov), N, M, precision
+        self.Np = (N + 1) * (N + 2) * (N + 3) // 6
+        self.Mp = (M + 1) * (M + 2) * (M + 3) // 6
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().bbw_elastic_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_media(self, rho_inv, lam, mu):
+        a, b, c = (_f64(x).reshape(self.K, self.Mp) for x in (rho_inv, lam, mu))
+        _check(lib().bbw_elastic_set_media(self._h, _ptr(a, C.c_double), _ptr(b, C.c_double),
+                                           _ptr(c, C.c_double)), "bbw_elastic_set_media")
+
+    def set_params(self, tau_v: float, tau_s: float):
+        _check(lib().bbw_elastic_set_params(self._h, tau_v, tau_s), "bbw_elastic_set_params")
+
+    def set_state(self, q, res=None, t: float = 0.0):
+        q = _f64(q).reshape(9, self.K, self.Np)
+        r = None if res is None else _f64(res).reshape(9, self.K, self.Np)
+        _check(lib().bbw_elastic_set_state(self._h, _ptr(q, C.c_double),
+                                           None if r is None else _ptr(r, C.c_double), t),
+               "bbw_elastic_set_state")
+
+    def get_state(self, with_res: bool = False, out=None):
+        """(q, t) or (q, res, t); ``out`` (C-contiguous float64, 9*K*Np values)
+        receives q if given."""
+        if out is not None:
+            if out.dtype != np.float64 or not out.flags.c_contiguous or out.size != 9 * self.K * self.Np:
+                raise ValueError("out must be a C-contiguous float64 array of 9*K*Np values")
+            q = out.reshape(9, self.K, self.Np)
+        else:
+            q = np.empty((9, self.K, self.Np))
+        r = np.empty((9, self.K, self.Np)) if with_res else None
+        t = C.c_double()
+        _check(lib().bbw_elastic_get_state(self._h, _ptr(q, C.c_double),
+                                           None if r is None else _ptr(r, C.c_double), C.byref(t)),
+               "bbw_elastic_get_state")
+        return (q, r, t.value) if with_res else (q, t.value)
+
+    def stage(self, s: int, dt: float):
+        _check(lib().bbw_elastic_stage(self._h, s, dt), "bbw_elastic_stage")
+
+    def step(self, dt: float, nsteps: int = 1):
+        _check(lib().bbw_elastic_step(self._h, dt, nsteps), "bbw_elastic_step")
+
+    def cfl_dt(self, cfl: float) -> float:
+        dt = C.c_double()
+        _check(lib().bbw_elastic_cfl_dt(self._h, cfl, C.byref(dt)), "bbw_elastic_cfl_dt")
+        return dt.value
+
+    def sync(self):
+        _check(lib().bbw_elastic_sync(self._h), "bbw_elastic_sync")
+
+    def time(self):
+        t = C.c_double()
+        n = C.c_int64()
+        _check(lib().bbw_elastic_get_time(self._h, C.byref(t), C.byref(n)), "bbw_elastic_get_time")
+        return t.value, n.value
+

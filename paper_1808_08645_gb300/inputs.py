@@ -25,7 +25,7 @@ __all__ = [
     "cube_mesh", "multi_index_points", "sample_at_domain_points",
     "c2_smooth_random", "c2_config_small", "gaussian_pulse", "random_state",
     "PARITY_CONFIG", "SWEEP_CONFIG", "BATCH_CONFIG", "batched_instances", "ADJOINT_CONFIG",
-    "top_face_receivers",
+    "top_face_receivers", "ELASTIC_CONFIG", "elastic_media", "elastic_pulse",
 ]
 
 #: the FP64 parity workload: 4^3 hexes x 6 = 384 tets, N=3, M=1, T=0.5
@@ -126,6 +126,46 @@ def multi_index_points(n: int) -> np.ndarray:
     if n == 0:
         return np.full((1, 4), 0.25)
     return a / n
+
+
+#: the elastic workload (the velocity-stress system of Sec. 2.2): the
+#: throughput mesh (32^3 hexes x 6 = 196,608 tets), N = 1..9, M = 2 media
+#: (rho^{-1}, lambda, mu from seeded smooth random fields with a layer jump),
+#: a Gaussian compressional pulse as initial state, FP32
+ELASTIC_CONFIG = dict(hexes=32, Ns=tuple(range(1, 10)), M=2, cfl=0.5, seed=0)
+
+
+def elastic_media(vxyz, etov, M: int, seed: int = 0):
+    """(rho_inv, lam, mu), each [K, M_p] Bernstein coefficients of degree M
+    (field values at the domain points, so every coefficient is positive).
+
+    c_p^2 = 2 f_0(x) in [1, 6] (f_0 the smooth random medium of seed ``seed``
+    with its layer jump), c_s^2 = c_p^2 / 3 (Poisson ratio 1/4, lambda = mu),
+    rho = f_1(x) in [0.5, 3] (seed + 1); lambda = rho (c_p^2 - 2 c_s^2),
+    mu = rho c_s^2."""
+    f0 = c2_smooth_random(seed)
+    rho = c2_smooth_random(seed + 1)
+
+    def rho_inv(x):
+        return 1.0 / rho(x)
+
+    def mu(x):  # rho c_s^2 = rho (2 f_0) / 3
+        return rho(x) * 2.0 * f0(x) / 3.0
+
+    def lam(x):  # rho (c_p^2 - 2 c_s^2) = rho (2 f_0) / 3
+        return rho(x) * 2.0 * f0(x) / 3.0
+
+    return tuple(sample_at_domain_points(vxyz, etov, M, f) for f in (rho_inv, lam, mu))
+
+
+def elastic_pulse(vxyz, etov, N: int, center=(0.5, 0.5, 0.5), width: float = 0.1) -> np.ndarray:
+    """Initial state [9, K, N_p]: v = 0, sigma = -g I with g the Gaussian
+    pulse (an isotropic pressure-like load that radiates a P wave); the
+    Bernstein coefficients are the pulse values at the domain points."""
+    g = sample_at_domain_points(vxyz, etov, N, gaussian_pulse(center, width))
+    q = np.zeros((9,) + g.shape)
+    q[3:6] = -g
+    return q
 
 
 def sample_at_domain_points(vxyz, etov, n: int, field) -> np.ndarray:

@@ -77,3 +77,30 @@ def test_top_face_receivers():
     assert np.all(r[:, 2] == 1.0)
     assert np.all((r[:, :2] > 0) & (r[:, :2] < 1))
     assert len({tuple(x) for x in r}) == 64
+
+
+def test_elastic_reference_line_and_bytes():
+    args = argparse.Namespace(Ns="1,2", steps=1, warmup=0, gpus=1)
+    out = bench.run_elastic_reference(args)
+    json.dumps(out)
+    for k in REQUIRED:
+        assert k in out, k
+    assert out["impl"] == "reference" and out["value"] > 0
+    N, M = 9, 2
+    np3 = lambda n: (n + 1) * (n + 2) * (n + 3) // 6
+    want = 4 * ((27 + 36 / 5) * np3(N) + 3 * np3(M) + 9) + 16
+    assert abs(bench.elastic_bytes_per_element(N, M) - want) < 1e-9
+    assert bench.load_elastic_traffic(9) is None or bench.load_elastic_traffic(9) > 0
+
+
+def test_elastic_inputs_recipe():
+    vxyz, etov = inputs.cube_mesh(2)
+    rho_inv, lam, mu = inputs.elastic_media(vxyz, etov, 2)
+    assert rho_inv.shape == lam.shape == mu.shape == (48, 10)
+    assert rho_inv.min() > 0 and lam.min() > 0 and mu.min() > 0
+    assert np.allclose(lam, mu)  # Poisson ratio 1/4
+    q = inputs.elastic_pulse(vxyz, etov, 3)
+    assert q.shape == (9, 48, 20)
+    assert np.all(q[:3] == 0) and np.all(q[6:] == 0)
+    assert np.array_equal(q[3], q[4]) and np.array_equal(q[4], q[5]) and q[3].min() < 0
+

@@ -1,5 +1,5 @@
 """The range-checked build (libbbwadg_checked.so, kernels compiled with
-BBW_CHECKED) runs the same cases clean -- no neighbour word or table index out
+BBW_CHECKED) runs the same acoustic and elastic cases clean -- no neighbour word or table index out
 of range -- and agrees with the normal build. It stands in for a device
 memory checker: the checks skip a bad access and report it through the
 device status word instead of faulting."""
@@ -52,6 +52,16 @@ CASES = textwrap.dedent("""
     for i in range(3):
         out["batch%d" % i] = b.get_state(i)
     b.close()
+    ve, ee = inputs.cube_mesh(2, jitter=0.15, shuffle=True, seed=4)
+    for N in (3, 9):
+        K, Np = len(ee), (N + 1) * (N + 2) * (N + 3) // 6
+        e = B.ElasticSolver(ve, ee, N, 2, 32)
+        e.set_media(*inputs.elastic_media(ve, ee, 2))
+        e.set_state(np.random.default_rng(N).standard_normal((9, K, Np)))
+        e.step(1e-3, 2)
+        e.sync()
+        out["elastic%d" % N] = e.get_state()[0]
+        e.close()
     np.savez({path!r}, **out)
 """)
 
