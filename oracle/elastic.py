@@ -151,9 +151,9 @@ class ElasticOracle:
         Mr = self.weighted_mass(self.rho_inv)
         Ml = self.weighted_mass(self.lam)
         Mm = self.weighted_mass(self.mu)
-        Minv = np.linalg.inv(self.Mhat)
+        # M^{-1} by an LU solve (backward stable), not an explicit inverse
         for c in range(3):
-            out[c] = np.einsum("ij,kjl,kl->ki", Minv, Mr, r[c])
+            out[c] = np.linalg.solve(self.Mhat, np.einsum("kjl,kl->jk", Mr, r[c])).T
         for a in range(6):
             acc = np.zeros_like(r[0])
             for b in range(6):
@@ -161,7 +161,7 @@ class ElasticOracle:
                     acc += LAMBDA_PATTERN[a, b] * np.einsum("kjl,kl->kj", Ml, r[3 + b])
                 if MU_PATTERN[a, b]:
                     acc += MU_PATTERN[a, b] * np.einsum("kjl,kl->kj", Mm, r[3 + b])
-            out[3 + a] = acc @ Minv.T
+            out[3 + a] = np.linalg.solve(self.Mhat, acc.T).T
         return out
 
     def rhs(self, q: np.ndarray) -> np.ndarray:
