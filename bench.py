@@ -659,7 +659,7 @@ def _elastic_oracle_sample(hexes: int, Ns, reps: int):
 def elastic_cpu_baseline(args):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     Ns = [int(x) for x in args.Ns.split(",")]
-    hexes, reps = 2, 3
+    hexes, reps = 3, 15  # about 10 s of FP64 work on the GPU machine's host cores
     code = (f"import sys, json; sys.path.insert(0, {ROOT!r}); import bench; "
             f"d, s = bench._elastic_oracle_sample({hexes}, {Ns!r}, {reps}); print(json.dumps([d, s]))")
     p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)

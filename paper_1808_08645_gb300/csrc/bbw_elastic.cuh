@@ -75,13 +75,16 @@ struct ElasticCfg {
   //   Q [9][Np] | PYR [6][4][Np] | V1B [9][Nm1p] | TR [9][4][Nfp] |
   //   normals [4][4] | media [3][Mp] | connectivity words [4][V] (int32)
   // TR holds the neighbour traces until F2 and the right-hand side R [9][Np]
-  // after it (36 Nfp >= 9 Np for N <= 9); the WADG ping-pong buffers (2 BUF)
-  // reuse PYR after V2.
-  static constexpr int S_PYR = 24 * Np;
+  // after it (36 Nfp >= 9 Np for N <= 9); the WADG ping-pong buffers reuse
+  // PYR after V2.
+  // FP32 projects the fields in pairs (vectors of 2V, 16-byte aligned
+  // ping-pong buffers in the pyramid region); FP64 one field at a time
+  static constexpr bool PAIR = sizeof(real) == 4;
+  static constexpr int S_W = PAIR ? 4 * BUF + 4 : 2 * BUF;
+  static constexpr int S_PYR = 24 * Np > S_W ? 24 * Np : S_W;
   static constexpr int S_V1 = 9 * Nm1p;
   static constexpr int S_TR = 36 * Nfp;
   static_assert(S_TR >= 9 * Np, "right-hand side in the trace region");
-  static_assert(S_PYR >= 2 * BUF, "projection buffers in the pyramid region");
   static constexpr int CONNV = (16 * V + int(sizeof(real)) * V - 1) / (int(sizeof(real)) * V);  // 4 V int32
   static constexpr int TEAMV = (9 * Np + S_PYR + S_V1 + S_TR + 16 + 3 * Mp + CONNV) | 1;
   static constexpr int TAB = table_bytes<N, M, real>();
@@ -92,13 +95,15 @@ struct ElasticCfg {
   static_assert(T <= 32 || GC <= 15, "one named barrier per multi-warp team");
 };
 
-// Teams per CTA: as many as fit the shared memory of one CTA per SM and 512
-// threads (128 threads below N = 4).
+// Teams per CTA: as many as fit the shared memory of one CTA per SM and 256
+// threads, so that every thread may hold 255 registers (the paired
+// projections keep 2V-wide telescoping levels in registers); 128 threads
+// below N = 4.
 template <int N, int M, typename real, int T, int V>
 constexpr int elastic_cta_groups() {
   constexpr int team_bytes = int(sizeof(real)) * V * ElasticCfg<N, M, real, T, V, 1>::TEAMV;
   constexpr int by_smem = (kSmemPerCta - table_bytes<N, M, real>()) / team_bytes;
-  constexpr int by_threads = (N <= 3 ? 128 : 512) / T;
+  constexpr int by_threads = (N <= 3 ? 128 : 256) / T;
   constexpr int g = by_smem < by_threads ? by_smem : by_threads;
   return T > 32 && g > 15 ? 15 : g;
 }
@@ -430,59 +435,130 @@ __global__ void __launch_bounds__(T* GC) elastic_stage_kernel(const ElasticParam
 
     // ---- W + RK: weight-adjusted update of every field, then its RK update ----
     {
-      real* A = PYR;
-      real* B = PYR + C::BUF * V;
       real* resg = P.res + size_t(g) * QV * V;
       real* qog = P.qout + size_t(g) * QV * V;
-      vt bh[3][Mp];
-#pragma unroll
-      for (int w = 0; w < 3; ++w)
-#pragma unroll
-        for (int b = 0; b < Mp; ++b) bh[w][b] = vmuls(tab.invfactM[b], vld<real, V>(MED + (w * Mp + b) * V));
-      vt lv[N + 1][C::RMAX];
       vt ptr[C::RMAX];  // P(lambda tr R_s)
-      // fill A with (sum of wt_k R[k]) / alpha!, A[Np] = 0
-      auto fill = [&](int k0, int nk, real wt) {
-        for (int i = t; i < Np; i += T) {
-          vt x = vld<real, V>(R + (k0 * Np + i) * V);
-          for (int k = 1; k < nk; ++k) x = vaxpy(x, real(1), vld<real, V>(R + ((k0 + k) * Np + i) * V));
-          vst(A + i * V, vmuls(wt * tab.invfactN[i], x));
-        }
-        if (t == 0) vst(A + Np * V, vzero<real, V>());
-        team_sync<T>();
+      // RK update of field fld from its weight-adjusted right-hand side
+      auto rk1 = [&](int fld, int r, vt rhs) {
+        const int i = t + r * T;
+        vt rn = vmuls(P.dt, rhs);
+        if (read_res) vfmas(rn, P.a, vld<real, V>(resg + size_t(fld * Np + i) * V));
+        vst(resg + size_t(fld * Np + i) * V, rn);
+        const vt qn = vaxpy(vld<real, V>(Q + (fld * Np + i) * V), P.b, rn);
+        vst(qog + size_t(fld * Np + i) * V, qn);
+#pragma unroll
+        for (int v = 0; v < V; ++v) bad |= !isfinite(qn.get(v));
       };
-      auto rk = [&](int fld, bool with_tr) {
-#pragma unroll
-        for (int r = 0; r < C::RMAX; ++r) {
-          const int i = t + r * T;
-          if (i < Np) {
-            vt rhs = lv[0][r];
-            if (with_tr) rhs = vaxpy(rhs, real(1), ptr[r]);
-            vt rn = vmuls(P.dt, rhs);
-            if (read_res) vfmas(rn, P.a, vld<real, V>(resg + size_t(fld * Np + i) * V));
-            vst(resg + size_t(fld * Np + i) * V, rn);
-            const vt qn = vaxpy(vld<real, V>(Q + (fld * Np + i) * V), P.b, rn);
-            vst(qog + size_t(fld * Np + i) * V, qn);
-#pragma unroll
-            for (int v = 0; v < V; ++v) bad |= !isfinite(qn.get(v));
+      // (sum of the fields R[k], k in [k0, k0 + nk)) * wt / alpha! at node i
+      auto rsum = [&](int k0, int nk, real wt, int i) {
+        vt x = vld<real, V>(R + (k0 * Np + i) * V);
+        for (int k = 1; k < nk; ++k) x = vaxpy(x, real(1), vld<real, V>(R + ((k0 + k) * Np + i) * V));
+        return vmuls(wt * tab.invfactN[i], x);
+      };
+      if constexpr (C::PAIR) {
+        // two fields per projection: vectors of 2V lanes (the first field's
+        // V element lanes, then the second's), each lane with its own weight
+        constexpr int W2 = 2 * V;
+        using wt2 = vec<real, W2>;
+        real* A2 = reinterpret_cast<real*>((reinterpret_cast<uintptr_t>(PYR) + 15) & ~uintptr_t(15));
+        real* B2 = A2 + C::BUF * W2;
+        wt2 lv[N + 1][C::RMAX];
+        // project (wt1 sum R[k1..k1+n1) ; wt2 sum R[k2..k2+n2)) with weights (w1 ; w2)
+        auto project = [&](int k1, int n1, real s1, int w1, int k2, int n2, real s2, int w2) {
+          for (int i = t; i < Np; i += T) {
+            vst<real, V>(A2 + i * W2, rsum(k1, n1, s1, i));
+            vst<real, V>(A2 + i * W2 + V, rsum(k2, n2, s2, i));
           }
-        }
-      };
-#pragma unroll 1
-      for (int c = 0; c < 3; ++c) {  // velocity: rho^{-1}
-        fill(c, 1, real(1));
-        wadg_group<N, M, real, T, V, C::RMAX>(tab, A, B, bh[0], true, t, lv);
-        rk(c, false);
-      }
-      fill(3, 3, real(1));  // lambda tr(R_s)
-      wadg_group<N, M, real, T, V, C::RMAX>(tab, A, B, bh[1], true, t, lv);
+          if (t == 0) vst<real, W2>(A2 + Np * W2, vzero<real, W2>());
+          wt2 bh2[Mp];  // weight coefficients / beta!, per lane
 #pragma unroll
-      for (int r = 0; r < C::RMAX; ++r) ptr[r] = lv[0][r];
+          for (int b = 0; b < Mp; ++b)
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+              bh2[b].set(v, tab.invfactM[b] * MED[(w1 * Mp + b) * V + v]);
+              bh2[b].set(V + v, tab.invfactM[b] * MED[(w2 * Mp + b) * V + v]);
+            }
+          team_sync<T>();
+          wadg_group<N, M, real, T, W2, C::RMAX>(tab, A2, B2, bh2, true, t, lv);
+        };
+        auto half = [&](const wt2& x, int h) {
+          vt y;
+#pragma unroll
+          for (int v = 0; v < V; ++v) y.set(v, x.get(h * V + v));
+          return y;
+        };
+        // (v_x, v_y) with rho^{-1}
+        project(0, 1, real(1), 0, 1, 1, real(1), 0);
+#pragma unroll
+        for (int r = 0; r < C::RMAX; ++r)
+          if (t + r * T < Np) {
+            rk1(0, r, half(lv[0][r], 0));
+            rk1(1, r, half(lv[0][r], 1));
+          }
+        // (v_z with rho^{-1}, tr R_s with lambda)
+        project(2, 1, real(1), 0, 3, 3, real(1), 1);
+#pragma unroll
+        for (int r = 0; r < C::RMAX; ++r)
+          if (t + r * T < Np) {
+            rk1(2, r, half(lv[0][r], 0));
+            ptr[r] = half(lv[0][r], 1);
+          }
+        // (s_xx, s_yy) with mu, times 2, plus P(lambda tr)
+        project(3, 1, real(2), 2, 4, 1, real(2), 2);
+#pragma unroll
+        for (int r = 0; r < C::RMAX; ++r)
+          if (t + r * T < Np) {
+            rk1(3, r, vaxpy(half(lv[0][r], 0), real(1), ptr[r]));
+            rk1(4, r, vaxpy(half(lv[0][r], 1), real(1), ptr[r]));
+          }
+        // (s_zz with 2 mu plus P(lambda tr), s_yz with mu)
+        project(5, 1, real(2), 2, 6, 1, real(1), 2);
+#pragma unroll
+        for (int r = 0; r < C::RMAX; ++r)
+          if (t + r * T < Np) {
+            rk1(5, r, vaxpy(half(lv[0][r], 0), real(1), ptr[r]));
+            rk1(6, r, half(lv[0][r], 1));
+          }
+        // (s_xz, s_xy) with mu
+        project(7, 1, real(1), 2, 8, 1, real(1), 2);
+#pragma unroll
+        for (int r = 0; r < C::RMAX; ++r)
+          if (t + r * T < Np) {
+            rk1(7, r, half(lv[0][r], 0));
+            rk1(8, r, half(lv[0][r], 1));
+          }
+      } else {
+        real* A = PYR;
+        real* B = PYR + C::BUF * V;
+        vt bh[3][Mp];  // weight coefficients / beta!
+#pragma unroll
+        for (int w = 0; w < 3; ++w)
+#pragma unroll
+          for (int b = 0; b < Mp; ++b) bh[w][b] = vmuls(tab.invfactM[b], vld<real, V>(MED + (w * Mp + b) * V));
+        vt lv[N + 1][C::RMAX];
+        auto project = [&](int k0, int nk, real wt, int w) {
+          for (int i = t; i < Np; i += T) vst(A + i * V, rsum(k0, nk, wt, i));
+          if (t == 0) vst(A + Np * V, vzero<real, V>());
+          team_sync<T>();
+          wadg_group<N, M, real, T, V, C::RMAX>(tab, A, B, bh[w], true, t, lv);
+        };
 #pragma unroll 1
-      for (int a = 0; a < 6; ++a) {  // mu: 2 R_s,a on the normal entries, R_s,a on the shear entries
-        fill(3 + a, 1, a < 3 ? real(2) : real(1));
-        wadg_group<N, M, real, T, V, C::RMAX>(tab, A, B, bh[2], true, t, lv);
-        rk(3 + a, a < 3);
+        for (int c = 0; c < 3; ++c) {  // velocity: rho^{-1}
+          project(c, 1, real(1), 0);
+#pragma unroll
+          for (int r = 0; r < C::RMAX; ++r)
+            if (t + r * T < Np) rk1(c, r, lv[0][r]);
+        }
+        project(3, 3, real(1), 1);  // lambda tr(R_s)
+#pragma unroll
+        for (int r = 0; r < C::RMAX; ++r) ptr[r] = lv[0][r];
+#pragma unroll 1
+        for (int a = 0; a < 6; ++a) {  // mu: 2 R_s,a on the normal entries, R_s,a on the shear entries
+          project(3 + a, 1, a < 3 ? real(2) : real(1), 2);
+#pragma unroll
+          for (int r = 0; r < C::RMAX; ++r)
+            if (t + r * T < Np) rk1(3 + a, r, a < 3 ? vaxpy(lv[0][r], real(1), ptr[r]) : lv[0][r]);
+        }
       }
     }
     team_sync<T>();
