@@ -95,15 +95,23 @@ struct ElasticCfg {
   static_assert(T <= 32 || GC <= 15, "one named barrier per multi-warp team");
 };
 
-// Teams per CTA: as many as fit the shared memory of one CTA per SM and 256
-// threads, so that every thread may hold 255 registers (the paired
-// projections keep 2V-wide telescoping levels in registers); 128 threads
-// below N = 4.
+// Thread budget of one CTA: 128 below N = 4 (several CTAs per SM), else one
+// CTA per SM with up to 512 threads. The paired projections with V = 2 keep
+// 4-wide telescoping levels in registers: at N = 4 they fit 384 threads, at
+// N = 5 256 (ptxas: no spills at M <= 2).
+template <int N, int V, typename real>
+constexpr int elastic_cta_threads() {
+  if (N <= 3) return 128;
+  if (V > 1 && sizeof(real) == 4) return N == 4 ? 384 : 256;
+  return 512;
+}
+
+// Teams per CTA: as many as fit the shared memory and the thread budget.
 template <int N, int M, typename real, int T, int V>
 constexpr int elastic_cta_groups() {
   constexpr int team_bytes = int(sizeof(real)) * V * ElasticCfg<N, M, real, T, V, 1>::TEAMV;
   constexpr int by_smem = (kSmemPerCta - table_bytes<N, M, real>()) / team_bytes;
-  constexpr int by_threads = (N <= 3 ? 128 : 256) / T;
+  constexpr int by_threads = elastic_cta_threads<N, V, real>() / T;
   constexpr int g = by_smem < by_threads ? by_smem : by_threads;
   return T > 32 && g > 15 ? 15 : g;
 }
