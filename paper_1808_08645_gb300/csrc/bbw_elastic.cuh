@@ -72,19 +72,21 @@ struct ElasticCfg {
   static constexpr int THREADS = T * GC;
   static constexpr int BUF = NMp > Np + 1 ? NMp : Np + 1;
   // per-team region, in vectors of V:
-  //   Q [9][Np] | PYR [6][4][Np] | V1B [9][Nm1p] | TR [9][4][Nfp] |
+  //   Q [9][Np] | PYR [6][4][Np] | V1B [9][Nm1p] | TR [9][4][Nfp] (N < 5) |
   //   normals [4][4] | media [3][Mp] | connectivity words [4][V] (int32)
-  // TR holds the neighbour traces until F2 and the right-hand side R [9][Np]
-  // after it (36 Nfp >= 9 Np for N <= 9); the WADG ping-pong buffers reuse
-  // PYR after V2.
+  // From N = 5 the neighbour traces fit the pyramid blocks above level 0
+  // (6 (Np - Nfp) >= 9 Nfp), which stay free until F2 has read them; below,
+  // they have a region of their own. The right-hand side R [9][Np] reuses Q
+  // once F2 has read the own traces (the RK update reads q_in from global
+  // memory, an L2 hit). The WADG ping-pong buffers reuse PYR after V2.
+  static constexpr bool TR_IN_P = 6 * (Np - Nfp) >= 9 * Nfp;
   // FP32 projects the fields in pairs (vectors of 2V, 16-byte aligned
   // ping-pong buffers in the pyramid region); FP64 one field at a time
   static constexpr bool PAIR = sizeof(real) == 4;
   static constexpr int S_W = PAIR ? 4 * BUF + 4 : 2 * BUF;
   static constexpr int S_PYR = 24 * Np > S_W ? 24 * Np : S_W;
   static constexpr int S_V1 = 9 * Nm1p;
-  static constexpr int S_TR = 36 * Nfp;
-  static_assert(S_TR >= 9 * Np, "right-hand side in the trace region");
+  static constexpr int S_TR = TR_IN_P ? 0 : 36 * Nfp;
   static constexpr int CONNV = (16 * V + int(sizeof(real)) * V - 1) / (int(sizeof(real)) * V);  // 4 V int32
   static constexpr int TEAMV = (9 * Np + S_PYR + S_V1 + S_TR + 16 + 3 * Mp + CONNV) | 1;
   static constexpr int TAB = table_bytes<N, M, real>();
@@ -163,13 +165,23 @@ __global__ void __launch_bounds__(T* GC) elastic_stage_kernel(const ElasticParam
   real* Q = reinterpret_cast<real*>(smem + C::TAB) + team * C::TEAMV * V;  // [9][Np]
   real* PYR = Q + QV * V;                 // [6][4][Np]
   real* V1B = PYR + C::S_PYR * V;         // [9][Nm1p]
-  real* TR = V1B + C::S_V1 * V;           // [9][4][Nfp], later R [9][Np]
+  real* TR = V1B + C::S_V1 * V;           // [9][4][Nfp] (N < 5)
   real* NRM = TR + C::S_TR * V;           // [4][nx, ny, nz, (1/2)|f|/|D|]
   real* MED = NRM + 16 * V;               // [3][Mp]
   int* CS = reinterpret_cast<int*>(MED + 3 * Mp * V);  // [4][V]
   auto pyr = [&](int k, int f, int slot) { return PYR + ((k * 4 + f) * Np + slot) * V; };
-  auto trace = [&](int fld, int f, int a) { return TR + ((fld * 4 + f) * Nfp + a) * V; };
-  real* R = TR;
+  // neighbour trace of field fld at face node a of face f
+  auto trace = [&](int fld, int f, int a) -> real* {
+    if constexpr (C::TR_IN_P) {
+      constexpr int FREE = Np - Nfp;  // slots above level 0 in one pyramid block
+      const int j = fld * Nfp + a;
+      const int k = j / FREE;
+      return pyr(k, f, Nfp + (j - k * FREE));
+    } else {
+      return TR + ((fld * 4 + f) * Nfp + a) * V;
+    }
+  };
+  real* R = Q;  // [9][Np] right-hand side, written in V2 (Q is not read after F2)
 
   const int64_t G = P.G;
   const int64_t stride = int64_t(gridDim.x) * GC;
@@ -446,13 +458,26 @@ __global__ void __launch_bounds__(T* GC) elastic_stage_kernel(const ElasticParam
       real* resg = P.res + size_t(g) * QV * V;
       real* qog = P.qout + size_t(g) * QV * V;
       vt ptr[C::RMAX];  // P(lambda tr R_s)
+      const real* qig = P.qin + size_t(g) * QV * V;
+      // res and q_in of field fld at this lane's nodes, loaded before the
+      // field's projection so that the loads are in flight during it
+      vt pres[2][C::RMAX], pq[2][C::RMAX];
+      auto prefetch = [&](int slot, int fld) {
+#pragma unroll
+        for (int r = 0; r < C::RMAX; ++r) {
+          const int i = t + r * T;
+          const bool ok = i < Np;
+          pres[slot][r] = ok && read_res ? vld<real, V>(resg + size_t(fld * Np + i) * V) : vzero<real, V>();
+          pq[slot][r] = ok ? vld<real, V>(qig + size_t(fld * Np + i) * V) : vzero<real, V>();
+        }
+      };
       // RK update of field fld from its weight-adjusted right-hand side
-      auto rk1 = [&](int fld, int r, vt rhs) {
+      auto rk1 = [&](int fld, int slot, int r, vt rhs) {
         const int i = t + r * T;
         vt rn = vmuls(P.dt, rhs);
-        if (read_res) vfmas(rn, P.a, vld<real, V>(resg + size_t(fld * Np + i) * V));
+        vfmas(rn, P.a, pres[slot][r]);
         vst(resg + size_t(fld * Np + i) * V, rn);
-        const vt qn = vaxpy(vld<real, V>(Q + (fld * Np + i) * V), P.b, rn);
+        const vt qn = vaxpy(pq[slot][r], P.b, rn);
         vst(qog + size_t(fld * Np + i) * V, qn);
 #pragma unroll
         for (int v = 0; v < V; ++v) bad |= !isfinite(qn.get(v));
@@ -496,44 +521,53 @@ __global__ void __launch_bounds__(T* GC) elastic_stage_kernel(const ElasticParam
           return y;
         };
         // (v_x, v_y) with rho^{-1}
+        prefetch(0, 0);
+        prefetch(1, 1);
         project(0, 1, real(1), 0, 1, 1, real(1), 0);
 #pragma unroll
         for (int r = 0; r < C::RMAX; ++r)
           if (t + r * T < Np) {
-            rk1(0, r, half(lv[0][r], 0));
-            rk1(1, r, half(lv[0][r], 1));
+            rk1(0, 0, r, half(lv[0][r], 0));
+            rk1(1, 1, r, half(lv[0][r], 1));
           }
         // (v_z with rho^{-1}, tr R_s with lambda)
+        prefetch(0, 2);
         project(2, 1, real(1), 0, 3, 3, real(1), 1);
 #pragma unroll
         for (int r = 0; r < C::RMAX; ++r)
           if (t + r * T < Np) {
-            rk1(2, r, half(lv[0][r], 0));
+            rk1(2, 0, r, half(lv[0][r], 0));
             ptr[r] = half(lv[0][r], 1);
           }
         // (s_xx, s_yy) with mu, times 2, plus P(lambda tr)
+        prefetch(0, 3);
+        prefetch(1, 4);
         project(3, 1, real(2), 2, 4, 1, real(2), 2);
 #pragma unroll
         for (int r = 0; r < C::RMAX; ++r)
           if (t + r * T < Np) {
-            rk1(3, r, vaxpy(half(lv[0][r], 0), real(1), ptr[r]));
-            rk1(4, r, vaxpy(half(lv[0][r], 1), real(1), ptr[r]));
+            rk1(3, 0, r, vaxpy(half(lv[0][r], 0), real(1), ptr[r]));
+            rk1(4, 1, r, vaxpy(half(lv[0][r], 1), real(1), ptr[r]));
           }
         // (s_zz with 2 mu plus P(lambda tr), s_yz with mu)
+        prefetch(0, 5);
+        prefetch(1, 6);
         project(5, 1, real(2), 2, 6, 1, real(1), 2);
 #pragma unroll
         for (int r = 0; r < C::RMAX; ++r)
           if (t + r * T < Np) {
-            rk1(5, r, vaxpy(half(lv[0][r], 0), real(1), ptr[r]));
-            rk1(6, r, half(lv[0][r], 1));
+            rk1(5, 0, r, vaxpy(half(lv[0][r], 0), real(1), ptr[r]));
+            rk1(6, 1, r, half(lv[0][r], 1));
           }
         // (s_xz, s_xy) with mu
+        prefetch(0, 7);
+        prefetch(1, 8);
         project(7, 1, real(1), 2, 8, 1, real(1), 2);
 #pragma unroll
         for (int r = 0; r < C::RMAX; ++r)
           if (t + r * T < Np) {
-            rk1(7, r, half(lv[0][r], 0));
-            rk1(8, r, half(lv[0][r], 1));
+            rk1(7, 0, r, half(lv[0][r], 0));
+            rk1(8, 1, r, half(lv[0][r], 1));
           }
       } else {
         real* A = PYR;
@@ -552,20 +586,22 @@ __global__ void __launch_bounds__(T* GC) elastic_stage_kernel(const ElasticParam
         };
 #pragma unroll 1
         for (int c = 0; c < 3; ++c) {  // velocity: rho^{-1}
+          prefetch(0, c);
           project(c, 1, real(1), 0);
 #pragma unroll
           for (int r = 0; r < C::RMAX; ++r)
-            if (t + r * T < Np) rk1(c, r, lv[0][r]);
+            if (t + r * T < Np) rk1(c, 0, r, lv[0][r]);
         }
         project(3, 3, real(1), 1);  // lambda tr(R_s)
 #pragma unroll
         for (int r = 0; r < C::RMAX; ++r) ptr[r] = lv[0][r];
 #pragma unroll 1
         for (int a = 0; a < 6; ++a) {  // mu: 2 R_s,a on the normal entries, R_s,a on the shear entries
+          prefetch(0, 3 + a);
           project(3 + a, 1, a < 3 ? real(2) : real(1), 2);
 #pragma unroll
           for (int r = 0; r < C::RMAX; ++r)
-            if (t + r * T < Np) rk1(3 + a, r, a < 3 ? vaxpy(lv[0][r], real(1), ptr[r]) : lv[0][r]);
+            if (t + r * T < Np) rk1(3 + a, 0, r, a < 3 ? vaxpy(lv[0][r], real(1), ptr[r]) : lv[0][r]);
         }
       }
     }
