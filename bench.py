@@ -233,7 +233,7 @@ def run_gpu(args):
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = algorithmic_bytes_per_element(top, M) * K / t_launch / 1e9
-    traffic = load_traffic(top)
+    traffic = load_traffic(top, K)
 
     # end to end through the public API with host buffers
     e2e = run_e2e(solvers, host_q0, Ns, dts, K, args.e2e_steps, stream)
@@ -347,7 +347,7 @@ def kernel_sources_sha256() -> str:
     return sources_sha256(KERNEL_SOURCES)
 
 
-def _traffic_from_profiles(pattern: str, N: int, sha: str):
+def _traffic_from_profiles(pattern: str, N: int, sha: str, K=None):
     import glob
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", pattern))):
         with open(path) as fh:
@@ -357,23 +357,27 @@ def _traffic_from_profiles(pattern: str, N: int, sha: str):
                         data = json.loads(line.split(":", 1)[1])
                     except ValueError:
                         continue
+                    if K is not None and data.get("K", K) != K:
+                        continue  # captured on another mesh
                     if data.get("N") == N and data.get("kernel_sources_sha256") == sha:
                         return float(data["traffic_bytes_per_launch"])
     return None
 
 
-def load_traffic(N: int):
+def load_traffic(N: int, K=None):
     """DRAM bytes per launch of the degree-N stage kernel from a committed ncu
     summary (profiles/stage_kernel_n<N>_*dram_traffic.md, its
-    ``machine-readable:`` line). None when there is no capture for N or when
-    the kernel sources changed since the counters were taken."""
-    return _traffic_from_profiles(f"stage_kernel_n{N}_*dram_traffic.md", N, kernel_sources_sha256())
+    ``machine-readable:`` line). None when there is no capture for N (on a
+    mesh of K elements, if K is given) or when the kernel sources changed
+    since the counters were taken."""
+    return _traffic_from_profiles(f"stage_kernel_n{N}_*dram_traffic.md", N, kernel_sources_sha256(), K)
 
 
-def load_elastic_traffic(N: int):
+def load_elastic_traffic(N: int, K=None):
     """As load_traffic, for the elastic stage kernel
     (profiles/elastic_stage_kernel_n<N>_*dram_traffic.md)."""
-    return _traffic_from_profiles(f"elastic_stage_kernel_n{N}_*dram_traffic.md", N, sources_sha256(ELASTIC_SOURCES))
+    return _traffic_from_profiles(f"elastic_stage_kernel_n{N}_*dram_traffic.md", N,
+                                  sources_sha256(ELASTIC_SOURCES), K)
 
 
 # ---------------------------------------------------------------------------
@@ -807,7 +811,7 @@ def run_elastic(args):
         "sweep": per_n,
         "roofline": {"bound": "hbm", "kernel": f"elastic_stage_kernel N={top} M={M} f32",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": load_elastic_traffic(top),
+                     "traffic": load_elastic_traffic(top, K),
                      "algorithmic_bytes_per_launch": elastic_bytes_per_element(top, M) * K,
                      "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"},
         "e2e": {"value": dofs / wall, "unit": UNIT, "h2d_bytes_per_step": h2d / e2e_steps,

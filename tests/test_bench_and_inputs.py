@@ -43,6 +43,10 @@ def test_traffic_lookup_tracks_the_kernel_sources(tmp_path, monkeypatch):
     # the sources are read from the real tree
     monkeypatch.setattr(bench, "kernel_sources_sha256", lambda: line["kernel_sources_sha256"])
     assert bench.load_traffic(4) == 123.0
+    line["K"] = 196608
+    (prof / "stage_kernel_n4_test_dram_traffic.md").write_text("x\nmachine-readable: " + json.dumps(line) + "\n")
+    assert bench.load_traffic(4, 196608) == 123.0
+    assert bench.load_traffic(4, 10368) is None  # captured on another mesh
     monkeypatch.setattr(bench, "kernel_sources_sha256", lambda: "0" * 64)
     assert bench.load_traffic(4) is None
     assert bench.load_traffic(5) is None
