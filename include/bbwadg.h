@@ -440,6 +440,12 @@ bbw_status bbw_elastic_set_state(bbw_elastic* s, const double* q, const double* 
 /* Read back q and res ([9][K][N_p], either may be NULL) and t; waits and
  * reports asynchronous failures as bbw_elastic_sync. */
 bbw_status bbw_elastic_get_state(bbw_elastic* s, double* q, double* res, double* t);
+/* State from caller-owned device memory [9][K][N_p] of type dtype (32 | 64),
+ * res may be NULL (zero); ordered on the solver's stream. */
+bbw_status bbw_elastic_set_state_device(bbw_elastic* s, const void* q, const void* res, int dtype, double t);
+/* Copy q (and res if non-NULL) to caller-owned device memory [9][K][N_p] of
+ * type dtype, ordered on the solver's stream. */
+bbw_status bbw_elastic_get_state_device(bbw_elastic* s, void* q, void* res, int dtype);
 /* One LSRK stage s in 0..4 with step dt (asynchronous). */
 bbw_status bbw_elastic_stage(bbw_elastic* s, int stage, double dt);
 /* nsteps full RK steps of size dt (asynchronous). */
@@ -447,6 +453,9 @@ bbw_status bbw_elastic_step(bbw_elastic* s, double dt, int64_t nsteps);
 /* dt = cfl / (c_p,max (N+1)(N+3)/3 max_f |f|/|D|), c_p,max^2 bounded by the
  * largest element value of max(lambda + 2 mu) max(rho^{-1}) (coefficients). */
 bbw_status bbw_elastic_cfl_dt(const bbw_elastic* s, double cfl, double* dt);
+/* Advance by T with nsteps = ceil(T / dt_cfl) steps of dt = T / nsteps
+ * (dt_used, nsteps may be NULL). */
+bbw_status bbw_elastic_advance(bbw_elastic* s, double T, double cfl, double* dt_used, int64_t* nsteps);
 /* Wait for the solver's stream; BBW_ERR_NONFINITE if a stage produced a NaN
  * or Inf since the last check. */
 bbw_status bbw_elastic_sync(bbw_elastic* s);

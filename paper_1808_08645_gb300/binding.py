@@ -92,9 +92,12 @@ EXPORTS = {
     "bbw_elastic_set_params": (_int, [_p, _d, _d]),
     "bbw_elastic_set_state": (_int, [_p, _dp, _dp, _d]),
     "bbw_elastic_get_state": (_int, [_p, _dp, _dp, _dp]),
+    "bbw_elastic_set_state_device": (_int, [_p, _p, _p, _int, _d]),
+    "bbw_elastic_get_state_device": (_int, [_p, _p, _p, _int]),
     "bbw_elastic_stage": (_int, [_p, _int, _d]),
     "bbw_elastic_step": (_int, [_p, _d, _i64]),
     "bbw_elastic_cfl_dt": (_int, [_p, _d, _dp]),
+    "bbw_elastic_advance": (_int, [_p, _d, _d, _dp, _i64p]),
     "bbw_elastic_sync": (_int, [_p]),
     "bbw_elastic_get_time": (_int, [_p, _dp, _i64p]),
 }
@@ -547,6 +550,14 @@ class ElasticSolver:
                "bbw_elastic_get_state")
         return (q, r, t.value) if with_res else (q, t.value)
 
+    def set_state_device(self, q, res=None, dtype: int = F32, t: float = 0.0):
+        _check(lib().bbw_elastic_set_state_device(self._h, _dev(q), _dev(res), dtype, t),
+               "bbw_elastic_set_state_device")
+
+    def get_state_device(self, q, res=None, dtype: int = F32):
+        _check(lib().bbw_elastic_get_state_device(self._h, _dev(q), _dev(res), dtype),
+               "bbw_elastic_get_state_device")
+
     def stage(self, s: int, dt: float):
         _check(lib().bbw_elastic_stage(self._h, s, dt), "bbw_elastic_stage")
 
@@ -557,6 +568,12 @@ class ElasticSolver:
         dt = C.c_double()
         _check(lib().bbw_elastic_cfl_dt(self._h, cfl, C.byref(dt)), "bbw_elastic_cfl_dt")
         return dt.value
+
+    def advance(self, T: float, cfl: float):
+        dt = C.c_double()
+        n = C.c_int64()
+        _check(lib().bbw_elastic_advance(self._h, T, cfl, C.byref(dt), C.byref(n)), "bbw_elastic_advance")
+        return dt.value, n.value
 
     def sync(self):
         _check(lib().bbw_elastic_sync(self._h), "bbw_elastic_sync")

@@ -47,8 +47,8 @@ namespace {
 // [F][K][Np] FP64 (caller's element order) <-> [G][F][Np][V] of the solver
 // precision; internal slot e holds the caller's element perm[e]. Padding
 // entries of the internal layout are set to zero.
-template <typename real>
-__global__ void elastic_to_internal(const double* __restrict__ src, real* __restrict__ dst, int64_t K, int Np, int V,
+template <typename From, typename real>
+__global__ void elastic_to_internal(const From* __restrict__ src, real* __restrict__ dst, int64_t K, int Np, int V,
                                     int F, const int32_t* __restrict__ perm, size_t n) {
   for (size_t x = blockIdx.x * size_t(blockDim.x) + threadIdx.x; x < n; x += size_t(gridDim.x) * blockDim.x) {
     const int v = int(x % V);
@@ -61,8 +61,8 @@ __global__ void elastic_to_internal(const double* __restrict__ src, real* __rest
   }
 }
 
-template <typename real>
-__global__ void elastic_to_user(const real* __restrict__ src, double* __restrict__ dst, int64_t K, int Np, int V,
+template <typename real, typename To>
+__global__ void elastic_to_user(const real* __restrict__ src, To* __restrict__ dst, int64_t K, int Np, int V,
                                 int F, const int32_t* __restrict__ inv) {
   const size_t n = size_t(F) * K * Np;
   for (size_t x = blockIdx.x * size_t(blockDim.x) + threadIdx.x; x < n; x += size_t(gridDim.x) * blockDim.x) {
@@ -71,7 +71,7 @@ __global__ void elastic_to_user(const real* __restrict__ src, double* __restrict
     const int64_t eu = int64_t(r % K);
     const int f = int(r / K);
     const int64_t e = inv ? inv[eu] : eu;
-    dst[x] = double(src[((size_t(e / V) * F + f) * Np + i) * V + size_t(e % V)]);
+    dst[x] = To(src[((size_t(e / V) * F + f) * Np + i) * V + size_t(e % V)]);
   }
 }
 
@@ -161,28 +161,46 @@ bbw_status launch(bbw_elastic* s, int stage, double dt) {
   return BBW_OK;
 }
 
-bbw_status to_internal(bbw_elastic* s, const double* d_src, void* dst) {
+// user layout [9][K][Np] of precision src_prec (device) -> internal layout
+template <typename From>
+void to_internal_t(bbw_elastic* s, const From* src, void* dst) {
   bbw_solver* m = s->m;
   const size_t n = s->ninternal();
   if (m->prec == 64)
-    elastic_to_internal<double><<<conv_blocks(n), 256, 0, m->stream>>>(d_src, static_cast<double*>(dst), m->K, m->Np,
-                                                                        s->V, 9, m->d_perm, n);
+    elastic_to_internal<From, double><<<conv_blocks(n), 256, 0, m->stream>>>(src, static_cast<double*>(dst), m->K,
+                                                                              m->Np, s->V, 9, m->d_perm, n);
   else
-    elastic_to_internal<float><<<conv_blocks(n), 256, 0, m->stream>>>(d_src, static_cast<float*>(dst), m->K, m->Np,
-                                                                       s->V, 9, m->d_perm, n);
+    elastic_to_internal<From, float><<<conv_blocks(n), 256, 0, m->stream>>>(src, static_cast<float*>(dst), m->K,
+                                                                             m->Np, s->V, 9, m->d_perm, n);
+}
+
+bbw_status to_internal(bbw_elastic* s, const void* src, int src_prec, void* dst) {
+  if (src_prec == 64)
+    to_internal_t(s, static_cast<const double*>(src), dst);
+  else
+    to_internal_t(s, static_cast<const float*>(src), dst);
   BBW_CUDA(cudaGetLastError());
   return BBW_OK;
 }
 
-bbw_status to_user(bbw_elastic* s, const void* src, double* d_dst) {
+// internal layout -> user layout [9][K][Np] of precision dst_prec (device)
+template <typename To>
+void to_user_t(bbw_elastic* s, const void* src, To* dst) {
   bbw_solver* m = s->m;
   const size_t n = s->nuser();
   if (m->prec == 64)
-    elastic_to_user<double><<<conv_blocks(n), 256, 0, m->stream>>>(static_cast<const double*>(src), d_dst, m->K,
-                                                                    m->Np, s->V, 9, m->d_inv);
+    elastic_to_user<double, To><<<conv_blocks(n), 256, 0, m->stream>>>(static_cast<const double*>(src), dst, m->K,
+                                                                        m->Np, s->V, 9, m->d_inv);
   else
-    elastic_to_user<float><<<conv_blocks(n), 256, 0, m->stream>>>(static_cast<const float*>(src), d_dst, m->K, m->Np,
-                                                                   s->V, 9, m->d_inv);
+    elastic_to_user<float, To><<<conv_blocks(n), 256, 0, m->stream>>>(static_cast<const float*>(src), dst, m->K,
+                                                                       m->Np, s->V, 9, m->d_inv);
+}
+
+bbw_status to_user(bbw_elastic* s, const void* src, void* dst, int dst_prec) {
+  if (dst_prec == 64)
+    to_user_t(s, src, static_cast<double*>(dst));
+  else
+    to_user_t(s, src, static_cast<float*>(dst));
   BBW_CUDA(cudaGetLastError());
   return BBW_OK;
 }
@@ -293,11 +311,11 @@ bbw_status bbw_elastic_set_state(bbw_elastic* s, const double* q, const double* 
   const size_t bytes = s->nuser() * 8;
   double* d = static_cast<double*>(s->d_stage);
   BBW_CUDA(cudaMemcpyAsync(d, q, bytes, cudaMemcpyHostToDevice, m->stream));
-  bbw_status st = to_internal(s, d, s->q[s->cur]);
+  bbw_status st = to_internal(s, d, 64, s->q[s->cur]);
   if (st != BBW_OK) return st;
   if (res) {
     BBW_CUDA(cudaMemcpyAsync(d, res, bytes, cudaMemcpyHostToDevice, m->stream));
-    st = to_internal(s, d, s->res);
+    st = to_internal(s, d, 64, s->res);
     if (st != BBW_OK) return st;
   } else {
     BBW_CUDA(cudaMemsetAsync(s->res, 0, s->ninternal() * s->rsz(), m->stream));
@@ -316,18 +334,49 @@ bbw_status bbw_elastic_get_state(bbw_elastic* s, double* q, double* res, double*
   const size_t bytes = s->nuser() * 8;
   double* d = static_cast<double*>(s->d_stage);
   if (q) {
-    st = to_user(s, s->q[s->cur], d);
+    st = to_user(s, s->q[s->cur], d, 64);
     if (st != BBW_OK) return st;
     BBW_CUDA(cudaMemcpyAsync(q, d, bytes, cudaMemcpyDeviceToHost, m->stream));
     BBW_CUDA(cudaStreamSynchronize(m->stream));
   }
   if (res) {
-    st = to_user(s, s->res, d);
+    st = to_user(s, s->res, d, 64);
     if (st != BBW_OK) return st;
     BBW_CUDA(cudaMemcpyAsync(res, d, bytes, cudaMemcpyDeviceToHost, m->stream));
     BBW_CUDA(cudaStreamSynchronize(m->stream));
   }
   if (t) *t = s->t;
+  return BBW_OK;
+}
+
+bbw_status bbw_elastic_set_state_device(bbw_elastic* s, const void* q, const void* res, int dtype, double t) {
+  if (!s || !q) return fail(BBW_ERR_ARG, "NULL argument");
+  if (dtype != 32 && dtype != 64) return fail(BBW_ERR_ARG, "dtype must be 32 or 64");
+  if (!std::isfinite(t)) return fail(BBW_ERR_ARG, "t is not finite");
+  bbw_status st = to_internal(s, q, dtype, s->q[s->cur]);
+  if (st != BBW_OK) return st;
+  if (res) {
+    st = to_internal(s, res, dtype, s->res);
+    if (st != BBW_OK) return st;
+  } else {
+    BBW_CUDA(cudaMemsetAsync(s->res, 0, s->ninternal() * s->rsz(), s->m->stream));
+  }
+  s->t = t;
+  s->stages = 0;
+  return BBW_OK;
+}
+
+bbw_status bbw_elastic_get_state_device(bbw_elastic* s, void* q, void* res, int dtype) {
+  if (!s) return fail(BBW_ERR_ARG, "solver is NULL");
+  if (dtype != 32 && dtype != 64) return fail(BBW_ERR_ARG, "dtype must be 32 or 64");
+  if (q) {
+    bbw_status st = to_user(s, s->q[s->cur], q, dtype);
+    if (st != BBW_OK) return st;
+  }
+  if (res) {
+    bbw_status st = to_user(s, s->res, res, dtype);
+    if (st != BBW_OK) return st;
+  }
   return BBW_OK;
 }
 
@@ -373,6 +422,19 @@ bbw_status bbw_elastic_cfl_dt(const bbw_elastic* s, double cfl, double* dt) {
   const double cn = (m->N + 1) * (m->N + 3) / 3.0;
   *dt = cfl / (std::sqrt(cp2) * cn * ratio);
   return BBW_OK;
+}
+
+bbw_status bbw_elastic_advance(bbw_elastic* s, double T, double cfl, double* dt_used, int64_t* nsteps) {
+  if (!s) return fail(BBW_ERR_ARG, "solver is NULL");
+  if (!(T >= 0.0) || !std::isfinite(T)) return fail(BBW_ERR_ARG, "T must be finite and >= 0");
+  double dt = 0.0;
+  bbw_status st = bbw_elastic_cfl_dt(s, cfl, &dt);
+  if (st != BBW_OK) return st;
+  const int64_t n = int64_t(std::ceil(T / dt));
+  const double h = n > 0 ? T / double(n) : 0.0;
+  if (dt_used) *dt_used = h;
+  if (nsteps) *nsteps = n;
+  return bbw_elastic_step(s, h, n);
 }
 
 bbw_status bbw_elastic_sync(bbw_elastic* s) {

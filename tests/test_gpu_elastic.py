@@ -2,7 +2,8 @@
 against the FP64 elastic oracle: every degree in both precisions, media of
 every degree, penalties, padded groups, the final time of a short run, the
 full-size throughput mesh (sampled), the acoustic limit (mu = 0) against the
-acoustic kernel, energy decay, and the error paths."""
+acoustic kernel, energy decay, device-resident state transfers, advance(),
+and the error paths."""
 from __future__ import annotations
 
 import numpy as np
@@ -240,3 +241,34 @@ def test_elastic_rejects_bad_media_and_reports_nonfinite():
     with pytest.raises(B.BBWError, match="BBW_ERR_NONFINITE"):
         g.sync()
     g.close()
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_elastic_device_state_roundtrip_and_advance(prec):
+    """set_state_device / get_state_device with torch tensors of either
+    dtype, then advance(): same result as the host path."""
+    N, M = 4, 2
+    vxyz, etov, media, q, res = _case(1, N, M, prec, seed=15)
+    K, Np = len(etov), bb.np_count(N)
+    g = _solver(vxyz, etov, N, M, prec, media, q, res)
+    dev = torch.device("cuda")
+    for dt_ in (B.F32, B.F64):
+        tq = torch.tensor(q, dtype=torch.float32 if dt_ == B.F32 else torch.float64, device=dev)
+        tr = torch.tensor(res, dtype=tq.dtype, device=dev)
+        g.set_state_device(tq, tr, dtype=dt_, t=0.25)
+        oq, orr = torch.empty_like(tq), torch.empty_like(tr)
+        g.get_state_device(oq, orr, dtype=dt_)
+        g.sync()
+        want_q = q.astype(np.float32) if dt_ == B.F32 else q
+        assert np.array_equal(oq.cpu().numpy(), want_q)
+        assert g.time()[0] == 0.25
+    g.set_state(q)
+    dt, n = g.advance(0.01, 0.5)
+    assert n >= 1 and abs(dt * n - 0.01) < 1e-15
+    qa, t = g.get_state()
+    g.set_state(q)
+    g.step(dt, n)
+    qb, _ = g.get_state()
+    assert np.array_equal(qa, qb) and abs(t - 0.01) < 1e-12
+    g.close()
+
