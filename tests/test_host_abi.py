@@ -152,3 +152,28 @@ def test_table_validation_rejects_bad_arguments():
         B.validate_tables(10, 2, 32)
     with pytest.raises(B.BBWError, match="BBW_ERR_ARG"):
         B.validate_tables(3, 2, 16)
+
+
+def test_elastic_argument_and_mesh_errors_need_no_device():
+    """bbw_elastic_create validates sizes, precision and the mesh on the host
+    before any device work; every call rejects a NULL handle."""
+    vxyz = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1.0]])
+    with pytest.raises(B.BBWError, match="BBW_ERR_UNSUPPORTED"):
+        B.ElasticSolver(vxyz, np.array([[0, 1, 2, 3]]), 10, 2)
+    with pytest.raises(B.BBWError, match="BBW_ERR_UNSUPPORTED"):
+        B.ElasticSolver(vxyz, np.array([[0, 1, 2, 3]]), 3, 4)
+    with pytest.raises(B.BBWError, match="BBW_ERR_ARG"):
+        B.ElasticSolver(vxyz, np.array([[0, 1, 2, 3]]), 3, 2, precision=16)
+    with pytest.raises(B.BBWError, match="BBW_ERR_MESH"):        # inverted element
+        B.ElasticSolver(vxyz, np.array([[0, 2, 1, 3]]), 3, 2)
+    L = B.lib()
+    assert L.bbw_elastic_stage(None, 0, 1e-3) == -1
+    assert L.bbw_elastic_step(None, 1e-3, 1) == -1
+    assert L.bbw_elastic_set_params(None, 1.0, 1.0) == -1
+    assert L.bbw_elastic_set_media(None, None, None, None) == -1
+    assert L.bbw_elastic_set_state(None, None, None, 0.0) == -1
+    assert L.bbw_elastic_get_state(None, None, None, None) == -1
+    assert L.bbw_elastic_sync(None) == -1
+    assert L.bbw_elastic_get_time(None, None, None) == -1
+    assert L.bbw_elastic_info(None, None, None, None, None, None, None) == -1
+    L.bbw_elastic_destroy(None)  # no-op
