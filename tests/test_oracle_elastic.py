@@ -11,7 +11,9 @@ the mathematics fix, each independent of the oracle's own formulas:
 * the assembled operator is skew in the weight-adjusted energy inner product
   for tau = 0 and dissipative for tau > 0 (energy stability, Sec. 2.2);
 * the matrix-weighted update equals a quadrature L2 projection of C(x) r(x)
-  with C(x) assembled pointwise from Hooke's law (Eq. 7 with a matrix weight).
+  with C(x) assembled pointwise from Hooke's law (Eq. 7 with a matrix weight);
+* with central fluxes the operator is rotation covariant (v -> R v,
+  sigma -> R sigma R^T, the stress rotated as a tensor, not through A_i).
 """
 from __future__ import annotations
 
@@ -203,3 +205,46 @@ def test_energy_decays_over_steps_with_penalty():
         q, res = orc.step(q, res, 2e-3)
         e.append(orc.energy(q))
     assert all(b < a for a, b in zip(e, e[1:]))
+
+
+def _voigt_to_tensor(s):
+    """(xx, yy, zz, yz, xz, xy) -> symmetric 3x3 tensor, leading axes kept."""
+    T = np.empty(s.shape[1:] + (3, 3))
+    T[..., 0, 0], T[..., 1, 1], T[..., 2, 2] = s[0], s[1], s[2]
+    T[..., 1, 2] = T[..., 2, 1] = s[3]
+    T[..., 0, 2] = T[..., 2, 0] = s[4]
+    T[..., 0, 1] = T[..., 1, 0] = s[5]
+    return T
+
+
+def _tensor_to_voigt(T):
+    return np.stack([T[..., 0, 0], T[..., 1, 1], T[..., 2, 2], T[..., 1, 2], T[..., 0, 2], T[..., 0, 1]])
+
+
+def test_central_flux_operator_is_rotation_covariant():
+    """Isotropic media, tau = 0: rotating the mesh by R and the fields by
+    v -> R v, sigma -> R sigma R^T rotates the right-hand side the same way
+    (the velocity-stress system is frame-indifferent; the rotation acts on
+    the stress tensor, written here without the A_i matrices). Bernstein
+    coefficients rotate like values because the rotation is linear and the
+    elements keep their vertex order."""
+    vxyz, etov = inputs.cube_mesh(1, jitter=0.1, shuffle=True, seed=12)
+    K = len(etov)
+    N, M = 3, 1
+    Mp = bb.np_count(M)
+    rng = np.random.default_rng(21)
+    media = (rng.uniform(0.5, 1.5, (K, Mp)), rng.uniform(0.5, 2.0, (K, Mp)), rng.uniform(0.3, 1.0, (K, Mp)))
+    A = rng.standard_normal((3, 3))
+    R, _ = np.linalg.qr(A)
+    if np.linalg.det(R) < 0:
+        R[:, 0] = -R[:, 0]
+    q = rng.standard_normal((9, K, bb.np_count(N)))
+    r = ElasticOracle(vxyz, etov, N, M, *media, tau_v=0.0, tau_s=0.0).rhs(q)
+    qr = np.empty_like(q)
+    qr[:3] = np.einsum("ij,jkn->ikn", R, q[:3])
+    qr[3:] = _tensor_to_voigt(R @ _voigt_to_tensor(q[3:]) @ R.T)
+    rr = ElasticOracle(np.asarray(vxyz) @ R.T, etov, N, M, *media, tau_v=0.0, tau_s=0.0).rhs(qr)
+    want = np.empty_like(r)
+    want[:3] = np.einsum("ij,jkn->ikn", R, r[:3])
+    want[3:] = _tensor_to_voigt(R @ _voigt_to_tensor(r[3:]) @ R.T)
+    assert np.abs(rr - want).max() <= 1e-11 * np.abs(r).max()
