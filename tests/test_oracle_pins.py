@@ -405,7 +405,9 @@ def test_ricker_closed_form():
     assert ricker(t0, f0, t0) == 1.0
     tz = t0 + 1.0 / (np.pi * f0 * np.sqrt(2.0))   # zero crossing of (1 - 2a)
     assert abs(ricker(tz, f0, t0)) < 1e-15
-    assert ricker(t0 + 0.3, f0, t0) < 1e-30 + abs(ricker(t0 + 0.3, f0, t0))
+    # one period of pi f0 away from the peak: a = 1, so r = (1 - 2) e^{-1}
+    for tm in (t0 - 1.0 / (np.pi * f0), t0 + 1.0 / (np.pi * f0)):
+        assert abs(ricker(tm, f0, t0) + np.exp(-1.0)) < 1e-15
 
 
 def test_energy_conserved_without_penalty():
