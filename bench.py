@@ -170,10 +170,14 @@ def run_gpu(args):
         s = B.Solver(vxyz, etov, N, M, B.F32, stream=stream.cuda_stream)
         s.set_c2(c2)
         s.set_state(q0)
-        s.set_point_source(np.array(cfg["source"]), f0=cfg["f0"])
         solvers[N] = s
         host_q0[N] = q0
     dts = {N: solvers[N].cfl_dt(0.5) for N in Ns}
+    # the Ricker source's amplitude samples, one per stage, for every step the
+    # bench runs (warm-up, timed, end to end)
+    horizon = args.warmup + args.steps + args.e2e_steps + 1
+    for N in Ns:
+        solvers[N].set_point_source(np.array(cfg["source"]), B.ricker_samples(dts[N], horizon, f0=cfg["f0"]))
 
     def sweep_step(events=None):
         for st in range(5):
@@ -383,6 +387,11 @@ def load_elastic_traffic(N: int, K=None):
 # ---------------------------------------------------------------------------
 # CPU oracle arms
 
+def _oracle_stage_times():
+    from oracle.acoustic import lsrk_stage_times
+    return [float(c) for c in lsrk_stage_times()]
+
+
 def _oracle_sample(hexes: int, Ns, reps: int):
     """Time one oracle stage per degree on a hexes^3 x 6 sub-mesh; returns
     (DOF updates, seconds)."""
@@ -396,13 +405,14 @@ def _oracle_sample(hexes: int, Ns, reps: int):
     for N in Ns:
         c2, q0 = make_workload(N, cfg["M"], vxyz, etov, field, pulse)
         orc = AcousticOracle(vxyz, etov, N, cfg["M"], c2)
-        orc.set_point_source(np.array(cfg["source"]), f0=cfg["f0"])
+        orc.set_point_source(np.array(cfg["source"]),
+                             inputs.ricker_samples(cfg["f0"], 1.0 / cfg["f0"], 1e-4, reps, _oracle_stage_times()))
         res = np.zeros_like(q0)
-        orc.stage(q0, res, 0, 1e-4, 0.0)  # warm caches
+        orc.stage(q0, res, 0, 1e-4)  # warm caches
         t = time.perf_counter()
         q, r = q0, res
         for i in range(reps):
-            q, r = orc.stage(q, r, i % 5, 1e-4, 0.0)
+            q, r = orc.stage(q, r, i % 5, 1e-4, i // 5)
         secs += time.perf_counter() - t
         dofs += reps * 4 * K * np3(N)
     return dofs, secs
@@ -483,13 +493,15 @@ def run_batched(args):
     solos = []
     for i, d in enumerate(specs):
         batch.set_c2(i, c2s[i])
-        batch.set_point_source(i, d["source"], f0=cfg["f0"])
         s = B.Solver(meshes[i][0], meshes[i][1], d["N"], M, B.F32, stream=stream.cuda_stream)
         s.set_c2(c2s[i])
-        s.set_point_source(d["source"], f0=cfg["f0"])
         solos.append(s)
-    t_setup = time.perf_counter() - t_setup
     dt = batch.cfl_dt(cfg["cfl"])
+    amp = B.ricker_samples(dt, 4 * (args.warmup + args.steps) + 16, f0=cfg["f0"])
+    for i, d in enumerate(specs):
+        batch.set_point_source(i, d["source"], amp)
+        solos[i].set_point_source(d["source"], amp)
+    t_setup = time.perf_counter() - t_setup
     schedule, tuned_ms = batch.autotune(3)
     dofs_step = sum(5 * 4 * len(m[1]) * np3(N) for m, N in zip(meshes, Ns))
 
@@ -574,7 +586,6 @@ def run_adjoint(args):
     rec = inputs.top_face_receivers()
     stream = torch.cuda.Stream()
     s = B.Solver(vxyz, etov, N, M, B.F32, stream=stream.cuda_stream)
-    s.set_point_source(np.array(cfg["source"]), f0=cfg["f0"])
     s.set_receivers(rec)
     q0 = np.zeros((4, K, np3(N)))
     s.set_c2(c2_true)
@@ -582,6 +593,7 @@ def run_adjoint(args):
     dt = s.cfl_dt(cfg["cfl"])
     s.set_c2(c2)
     dt = min(dt, s.cfl_dt(cfg["cfl"]))
+    s.set_point_source(np.array(cfg["source"]), B.ricker_samples(dt, nsteps, f0=cfg["f0"]))
     every = max(1, int(round(np.sqrt(nsteps))))
 
     def timed(fn):

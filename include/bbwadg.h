@@ -167,19 +167,40 @@ bbw_status bbw_get_state(bbw_solver* s, double* q, double* res, double* t);
 bbw_status bbw_get_state_device(bbw_solver* s, void* q, void* res, int dtype);
 
 /*
- * Point source delta(x - xs) r(t) in the pressure equation, with the Ricker
- * wavelet r(t) = (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2).
- * It is placed in the lowest-numbered element whose closure contains xs,
- * with coefficients M^{-1} B(xs) / |D^k| and enters inside the
- * weight-adjusted bracket of the p equation. *elem receives that element
- * (may be NULL). Errors: BBW_ERR_ARG if xs lies outside the mesh.
+ * Sources. A source adds a(t) f(x) to the right-hand side of the pressure
+ * equation (Eq. 1), inside the weight-adjusted bracket of Eq. (4), where the
+ * spatial part f is given by degree-N Bernstein coefficients on some elements
+ * and the time signature a(t) by host-given samples, one per RK stage:
+ * sample 5 n + s is used at stage s of the n-th RK step counted from the last
+ * bbw_set_state (its stage time is t + c_s dt, c_s from bbw_lsrk_coeffs);
+ * samples past the end of amp are 0. The samples are copied; the kernels
+ * read them from device memory, so any time function (a wavelet, a
+ * manufactured forcing) can be driven. Setting a source replaces the
+ * previous sources; nsamples = 0 removes them. Waits for the solver's stream.
+ * Errors: BBW_ERR_ARG (element out of range, an element listed twice,
+ * non-finite coefficients or samples, NULL with a positive count).
  */
-bbw_status bbw_set_point_source(bbw_solver* s, const double* xs, double f0, double t0,
-                                int64_t* elem);
 
-/* A source with caller-given coefficients [N_p] on element elem, same wavelet. */
-bbw_status bbw_set_source(bbw_solver* s, int64_t elem, const double* coeffs, double f0,
-                          double t0);
+/* One element: coeffs [N_p] on element elem, amplitude samples amp [nsamples]. */
+bbw_status bbw_set_source(bbw_solver* s, int64_t elem, const double* coeffs, const double* amp,
+                          int64_t nsamples);
+
+/*
+ * A forcing spread over nelem distinct elems [nelem] (caller's numbering) with
+ * coefficients coeffs [nelem][N_p] and one common amplitude series
+ * amp [nsamples]: f(x, t) = a(t) g(x) with g given per element.
+ */
+bbw_status bbw_set_forcing(bbw_solver* s, int64_t nelem, const int64_t* elems, const double* coeffs,
+                           const double* amp, int64_t nsamples);
+
+/*
+ * Point source delta(x - xs) a(t) in the pressure equation: placed in the
+ * lowest-numbered element whose closure contains xs, with coefficients
+ * M^{-1} B(xs) / |D^k|. *elem receives that element (may be NULL).
+ * Errors: BBW_ERR_ARG if xs lies outside the mesh.
+ */
+bbw_status bbw_set_point_source(bbw_solver* s, const double* xs, const double* amp, int64_t nsamples,
+                                int64_t* elem);
 
 /* Remove the source. */
 bbw_status bbw_clear_source(bbw_solver* s);
@@ -357,11 +378,12 @@ bbw_status bbw_batch_get_state(bbw_batch* b, int i, double* q, double* res);
 /* Penalty parameters of every instance (as bbw_set_params). */
 bbw_status bbw_batch_set_params(bbw_batch* b, double tau_p, double tau_u);
 
-/* Ricker point source of instance i at xs (as bbw_set_point_source, searched
- * within instance i); elem (may be NULL) receives its element in instance i.
- * Setting it again moves the source. */
-bbw_status bbw_batch_set_point_source(bbw_batch* b, int i, const double* xs, double f0,
-                                      double t0, int64_t* elem);
+/* Point source of instance i at xs with amplitude samples amp [nsamples]
+ * (as bbw_set_point_source, searched within instance i; sample 5 n + s at
+ * stage s of the n-th step since the last bbw_batch_set_time); elem (may be
+ * NULL) receives its element in instance i. Setting it again replaces it. */
+bbw_status bbw_batch_set_point_source(bbw_batch* b, int i, const double* xs, const double* amp,
+                                      int64_t nsamples, int64_t* elem);
 
 /* Remove every source of the batch. */
 bbw_status bbw_batch_clear_sources(bbw_batch* b);
@@ -369,7 +391,7 @@ bbw_status bbw_batch_clear_sources(bbw_batch* b);
 /* The smallest CFL time step over the instances (rule of bbw_cfl_dt). */
 bbw_status bbw_batch_cfl_dt(const bbw_batch* b, double cfl, double* dt);
 
-/* Set the common time (and reset the step counter). */
+/* Set the common time and reset the step counter (amplitude sample 0 comes next). */
 bbw_status bbw_batch_set_time(bbw_batch* b, double t);
 
 /*

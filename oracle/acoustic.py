@@ -134,11 +134,14 @@ class AcousticOracle:
         self.T = bb.weighted_mass_terms(n, m)
         A = bb.multi_indices(n)
         self.face_nodes = [np.array([i for i, a in enumerate(A) if a[f] == 0]) for f in range(4)]
-        self.source = None  # (element, vector, f0, t0)
+        # sources: (elements, coefficient vectors [n, Np], amplitude samples);
+        # sample 5 n + s drives stage s of step n, zero past the end
+        self.source = None
 
     # -- sources -------------------------------------------------------------
-    def set_point_source(self, x, f0: float = 10.0, t0: float | None = None):
-        """Point source delta(x - x_s) r(t) added to the pressure equation.
+    def set_point_source(self, x, amp):
+        """Point source delta(x - x_s) a(t) added to the pressure equation,
+        a(t) given by one sample per RK stage.
 
         Its degree-N coefficients on the containing element are
         M^{-1} B(x_s) / |T| (test against every basis function, strong form).
@@ -146,13 +149,22 @@ class AcousticOracle:
         e, lam = locate_point(self.vxyz, self.etov, x)
         B = bb.evaluate(np.eye(self.Np), self.N, lam[None, :])[:, 0]
         vec = np.linalg.solve(self.Mhat, B) / self.geo["vol"][e]
-        self.source = (e, vec, float(f0), 1.0 / f0 if t0 is None else float(t0))
+        self.set_forcing([e], vec[None, :], amp)
         return e, vec
 
-    def source_amplitude(self, t: float) -> float:
-        if self.source is None:
+    def set_forcing(self, elems, coeffs, amp):
+        """Forcing a(t) g(x) in the pressure equation: g given by degree-N
+        Bernstein coefficients coeffs [n, Np] on elements elems, a(t) by one
+        sample per RK stage."""
+        elems = np.asarray(elems, dtype=np.int64).ravel()
+        coeffs = np.asarray(coeffs, dtype=np.float64).reshape(len(elems), self.Np)
+        self.source = (elems, coeffs, np.asarray(amp, dtype=np.float64).ravel())
+
+    def source_amplitude(self, k) -> float:
+        """Amplitude sample k (None or past the end of the series: 0)."""
+        if self.source is None or k is None or not 0 <= k < len(self.source[2]):
             return 0.0
-        return ricker(t, self.source[2], self.source[3])
+        return float(self.source[2][k])
 
     # -- operator ------------------------------------------------------------
     def traces(self, q: np.ndarray, f: int):
@@ -168,17 +180,19 @@ class AcousticOracle:
         nbr = np.where(wall[None], mirror, nbr)
         return own, nbr
 
-    def rhs(self, q: np.ndarray, t: float = 0.0) -> np.ndarray:
-        """Semi-discrete right-hand side: velocity rows as they are, the
-        pressure bracket through the weight-adjusted update (Eq. 4)."""
-        out, bracket = self.spatial(q, t)
+    def rhs(self, q: np.ndarray, k=None) -> np.ndarray:
+        """Semi-discrete right-hand side with the sources at amplitude sample k:
+        velocity rows as they are, the pressure bracket through the
+        weight-adjusted update (Eq. 4)."""
+        out, bracket = self.spatial(q, k)
         out[0] = self.wadg(bracket)
         return out
 
-    def spatial(self, q: np.ndarray, t: float = 0.0):
+    def spatial(self, q: np.ndarray, k=None):
         """(out, bracket): out[1:4] the velocity right-hand sides, bracket the
         pressure right-hand side before the weight-adjusted update (volume
-        term, lifted penalty fluxes of Eq. (2) and the point source)."""
+        term, lifted penalty fluxes of Eq. (2) and the sources at amplitude
+        sample k)."""
         q = np.asarray(q, dtype=np.float64)
         p, u = q[0], q[1:4]
         g = self.geo["grad"]                                 # (K, 4, 3)
@@ -206,9 +220,9 @@ class AcousticOracle:
         out = np.empty_like(q)
         out[1:4] = -gradp + lift_u
         bracket = -divu + lift_p
-        if self.source is not None:
-            e, vec = self.source[0], self.source[1]
-            bracket[e] += self.source_amplitude(t) * vec
+        a = self.source_amplitude(k)
+        if a != 0.0:
+            bracket[self.source[0]] += a * self.source[1]
         out[0] = 0.0
         return out, bracket
 
@@ -219,23 +233,24 @@ class AcousticOracle:
         return np.linalg.solve(self.Mhat, Mr.T).T
 
     # -- time stepping -------------------------------------------------------
-    def stage(self, q, res, s: int, dt: float, t: float):
-        """One LSRK stage: res = a_s res + dt rhs(q, t + c_s dt); q += b_s res."""
-        c = lsrk_stage_times()
-        r = self.rhs(q, t + float(c[s]) * dt)
+    def stage(self, q, res, s: int, dt: float, step: int = 0):
+        """Stage s of RK step `step`: res = a_s res + dt rhs(q), q += b_s res,
+        with the sources at amplitude sample 5 step + s (the stage time is
+        t + c_s dt)."""
+        r = self.rhs(q, 5 * int(step) + s)
         res = float(LSRK_A[s]) * res + dt * r
         q = q + float(LSRK_B[s]) * res
         return q, res
 
-    def step(self, q, res, dt: float, t: float):
+    def step(self, q, res, dt: float, step: int = 0):
         for s in range(5):
-            q, res = self.stage(q, res, s, dt, t)
+            q, res = self.stage(q, res, s, dt, step)
         return q, res
 
-    def run(self, q, dt: float, nsteps: int, t: float = 0.0):
+    def run(self, q, dt: float, nsteps: int, step0: int = 0):
         res = np.zeros_like(q)
         for i in range(nsteps):
-            q, res = self.step(q, res, dt, t + i * dt)
+            q, res = self.step(q, res, dt, step0 + i)
         return q, res
 
     def dt_for(self, T: float, cfl: float):

@@ -20,7 +20,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import bernstein as bb
-from .acoustic import LSRK_A, LSRK_B, AcousticOracle, lsrk_stage_times
+from .acoustic import LSRK_A, LSRK_B, AcousticOracle
 from .mesh import locate_point
 
 __all__ = ["receiver_matrix", "record", "misfit_gradient"]
@@ -38,25 +38,24 @@ def receiver_matrix(orc: AcousticOracle, xyz) -> np.ndarray:
     return R
 
 
-def record(orc: AcousticOracle, q0, dt: float, nsteps: int, R: np.ndarray, t0: float = 0.0):
+def record(orc: AcousticOracle, q0, dt: float, nsteps: int, R: np.ndarray, step0: int = 0):
     """Traces [nsteps, nrec] after every step, and the stage inputs of every
     step (list of 5 arrays per step) for the reverse sweep."""
     q = np.asarray(q0, dtype=np.float64).copy()
     res = np.zeros_like(q)
     traces, stages = [], []
     for n in range(nsteps):
-        t = t0 + n * dt
         ins = []
         for s in range(5):
             ins.append(q.copy())
-            q, res = orc.stage(q, res, s, dt, t)
+            q, res = orc.stage(q, res, s, dt, step0 + n)
         stages.append(ins)
         traces.append(R @ q.ravel())
     return np.array(traces), stages
 
 
 def _stage_matrix(orc: AcousticOracle) -> np.ndarray:
-    """L with rhs(q, t) = L q + rhs(0, t): the linear part, column by column."""
+    """L with rhs(q, k) = L q + rhs(0, k): the linear part, column by column."""
     n = 4 * orc.K * orc.Np
     src = orc.source
     orc.source = None
@@ -70,12 +69,11 @@ def _stage_matrix(orc: AcousticOracle) -> np.ndarray:
 
 
 def misfit_gradient(orc: AcousticOracle, q0, dt: float, nsteps: int, R: np.ndarray, trace_grad,
-                    t0: float = 0.0):
+                    step0: int = 0):
     """(grad_c2 [K, Mp], grad_q0 [4, K, Np]) of J = sum(trace_grad * traces)."""
     g = np.asarray(trace_grad, dtype=np.float64).reshape(nsteps, -1)
-    _, stages = record(orc, q0, dt, nsteps, R, t0)
+    _, stages = record(orc, q0, dt, nsteps, R, step0)
     L = _stage_matrix(orc)
-    c = lsrk_stage_times()
     K, Np, Mp = orc.K, orc.Np, bb.np_count(orc.M)
     Minv = np.linalg.inv(orc.Mhat)
     qb = np.zeros(4 * K * Np)
@@ -83,11 +81,10 @@ def misfit_gradient(orc: AcousticOracle, q0, dt: float, nsteps: int, R: np.ndarr
     gc = np.zeros((K, Mp))
     for n in range(nsteps - 1, -1, -1):
         qb += R.T @ g[n]
-        t = t0 + n * dt
         for s in range(4, -1, -1):
             rt = rb + float(LSRK_B[s]) * qb
             qb = qb + dt * (L.T @ rt)
-            _, v = orc.spatial(stages[n][s], t + float(c[s]) * dt)
+            _, v = orc.spatial(stages[n][s], 5 * (step0 + n) + s)
             rp = rt.reshape(4, K, Np)[0]
             for k in range(K):
                 for b in range(Mp):

@@ -51,8 +51,9 @@ EXPORTS = {
     "bbw_set_state_device": (_int, [_p, _p, _p, _int, _d]),
     "bbw_get_state": (_int, [_p, _dp, _dp, _dp]),
     "bbw_get_state_device": (_int, [_p, _p, _p, _int]),
-    "bbw_set_point_source": (_int, [_p, _dp, _d, _d, _i64p]),
-    "bbw_set_source": (_int, [_p, _i64, _dp, _d, _d]),
+    "bbw_set_point_source": (_int, [_p, _dp, _dp, _i64, _i64p]),
+    "bbw_set_source": (_int, [_p, _i64, _dp, _dp, _i64]),
+    "bbw_set_forcing": (_int, [_p, _i64, _i64p, _dp, _dp, _i64]),
     "bbw_clear_source": (_int, [_p]),
     "bbw_stage": (_int, [_p, _int, _d]),
     "bbw_step": (_int, [_p, _d, _i64]),
@@ -77,7 +78,7 @@ EXPORTS = {
     "bbw_batch_set_state": (_int, [_p, _int, _dp, _dp]),
     "bbw_batch_get_state": (_int, [_p, _int, _dp, _dp]),
     "bbw_batch_set_params": (_int, [_p, _d, _d]),
-    "bbw_batch_set_point_source": (_int, [_p, _int, _dp, _d, _d, _i64p]),
+    "bbw_batch_set_point_source": (_int, [_p, _int, _dp, _dp, _i64, _i64p]),
     "bbw_batch_clear_sources": (_int, [_p]),
     "bbw_batch_cfl_dt": (_int, [_p, _d, _dp]),
     "bbw_batch_set_time": (_int, [_p, _d]),
@@ -168,6 +169,16 @@ def lsrk_coeffs():
     _check(lib().bbw_lsrk_coeffs(_ptr(a, C.c_double), _ptr(b, C.c_double), _ptr(c, C.c_double)),
            "bbw_lsrk_coeffs")
     return a, b, c
+
+
+def ricker_samples(dt: float, nsteps: int, f0: float = 10.0, t0: float | None = None,
+                   t_start: float = 0.0) -> np.ndarray:
+    """Amplitude samples of a Ricker wavelet of peak frequency f0 and delay t0
+    (default 1/f0) for nsteps RK steps of size dt starting at t_start, one per
+    stage at the library's stage times (bbw_lsrk_coeffs): the ``amp`` argument
+    of the source calls."""
+    from . import inputs
+    return inputs.ricker_samples(f0, 1.0 / f0 if t0 is None else t0, dt, nsteps, lsrk_coeffs()[2], t_start)
 
 
 def mesh_analyze(vxyz, etov, N: int):
@@ -294,17 +305,30 @@ class Solver:
     def get_state_device(self, q, res=None, dtype: int = F32):
         _check(lib().bbw_get_state_device(self._h, _dev(q), _dev(res), dtype), "bbw_get_state_device")
 
-    def set_point_source(self, xs, f0: float = 10.0, t0: float | None = None) -> int:
+    def set_point_source(self, xs, amp) -> int:
+        """Point source at xs with amplitude samples amp (one per RK stage,
+        sample 5 n + s at stage s of step n since set_state); its element."""
         xs = _f64(xs)
+        a = _f64(amp).ravel()
         e = C.c_int64()
-        _check(lib().bbw_set_point_source(self._h, _ptr(xs, C.c_double), f0,
-                                          1.0 / f0 if t0 is None else t0, C.byref(e)),
-               "bbw_set_point_source")
+        _check(lib().bbw_set_point_source(self._h, _ptr(xs, C.c_double), _ptr(a, C.c_double), a.size,
+                                          C.byref(e)), "bbw_set_point_source")
         return e.value
 
-    def set_source(self, elem: int, coeffs, f0: float, t0: float):
+    def set_source(self, elem: int, coeffs, amp):
         c = _f64(coeffs)
-        _check(lib().bbw_set_source(self._h, elem, _ptr(c, C.c_double), f0, t0), "bbw_set_source")
+        a = _f64(amp).ravel()
+        _check(lib().bbw_set_source(self._h, elem, _ptr(c, C.c_double), _ptr(a, C.c_double), a.size),
+               "bbw_set_source")
+
+    def set_forcing(self, elems, coeffs, amp):
+        """Forcing a(t) g(x): g by coefficients coeffs [n, Np] on elements
+        elems [n], a(t) by the samples amp."""
+        el = np.ascontiguousarray(elems, dtype=np.int64).ravel()
+        c = _f64(coeffs).reshape(el.size, self.Np)
+        a = _f64(amp).ravel()
+        _check(lib().bbw_set_forcing(self._h, el.size, _ptr(el, C.c_int64), _ptr(c, C.c_double),
+                                     _ptr(a, C.c_double), a.size), "bbw_set_forcing")
 
     def clear_source(self):
         _check(lib().bbw_clear_source(self._h), "bbw_clear_source")
@@ -444,12 +468,14 @@ class Batch:
     def set_params(self, tau_p: float, tau_u: float):
         _check(lib().bbw_batch_set_params(self._h, tau_p, tau_u), "bbw_batch_set_params")
 
-    def set_point_source(self, i: int, xs, f0: float = 10.0, t0: float | None = None) -> int:
+    def set_point_source(self, i: int, xs, amp) -> int:
+        """Point source of instance i at xs with amplitude samples amp (one per
+        RK stage, sample 5 n + s at stage s of step n since set_time)."""
         xs = _f64(xs)
+        a = _f64(amp).ravel()
         e = C.c_int64()
-        _check(lib().bbw_batch_set_point_source(self._h, i, _ptr(xs, C.c_double), f0,
-                                                1.0 / f0 if t0 is None else t0, C.byref(e)),
-               "bbw_batch_set_point_source")
+        _check(lib().bbw_batch_set_point_source(self._h, i, _ptr(xs, C.c_double), _ptr(a, C.c_double),
+                                                a.size, C.byref(e)), "bbw_batch_set_point_source")
         return e.value
 
     def clear_sources(self):

@@ -62,7 +62,7 @@ struct AdjointData {
   bool recorded = false;
   double dt = 0.0;
   int64_t nsteps = 0, every = 1;
-  std::vector<double> t_step;   // start time of each step
+  std::vector<int64_t> k_step;  // the solver's step counter at the start of each step (amplitude samples)
   std::vector<void*> ckpt;      // internal-layout states at steps 0, C, 2C, ...
   double* d_traces = nullptr;   // [nsteps][nrec]
   // operator tables (real): M^{-1}, M [Np][Np]; T [Mp][Np][Np]
@@ -286,9 +286,10 @@ void free_run(AdjointData* a, bool release = false) {
 
 // One forward stage on explicit buffers: qin -> qout, res updated, time t.
 template <typename real>
-bbw_status forward_stage(bbw_solver* s, const void* qin, void* qout, void* res, int stage, double dt, double t) {
-  double ca[5], cb[5], cc[5];
-  bbw_lsrk_coeffs(ca, cb, cc);
+bbw_status forward_stage(bbw_solver* s, const void* qin, void* qout, void* res, int stage, double dt,
+                         int64_t step) {
+  double ca[5], cb[5];
+  bbw_lsrk_coeffs(ca, cb, nullptr);
   bbw::StageParams<real> P;
   P.qin = static_cast<const real*>(qin);
   P.qout = static_cast<real*>(qout);
@@ -303,14 +304,7 @@ bbw_status forward_stage(bbw_solver* s, const void* qin, void* qout, void* res, 
   P.dt = real(dt);
   P.tau_p = real(s->tau_p);
   P.tau_u = real(s->tau_u);
-  P.n_src_groups = s->src_elem >= 0 ? 1 : 0;
-  P.src_groups = s->d_src_group;
-  P.src_slots = s->d_src_slots;
-  P.src_vec = static_cast<const real*>(s->d_src);
-  P.src_wav = s->d_src_wav;
-  P.t_dev = nullptr;
-  P.t_step = t;
-  P.c_dt = cc[stage] * dt;
+  bbw::set_stage_sources<bbw::StageParams<real>, real>(s, P, step, stage, true);
   P.status = s->d_status;
   BBW_CUDA(s->ops->launch_stage(s->M, s->prec == 64, &P, s->grid_stage, s->stream));
   return BBW_OK;
@@ -319,10 +313,7 @@ bbw_status forward_stage(bbw_solver* s, const void* qin, void* qout, void* res, 
 // Spatial operator alone: out = [bracket_p (+ sources at t + c_s dt), rhs_u]
 // of qin (internal layout), penalties sgn * tau.
 template <typename real>
-bbw_status spatial(bbw_solver* s, const void* qin, void* out, double sgn, bool sources, int stage, double dt,
-                   double t) {
-  double ca[5], cb[5], cc[5];
-  bbw_lsrk_coeffs(ca, cb, cc);
+bbw_status spatial(bbw_solver* s, const void* qin, void* out, double sgn, bool sources, int stage, int64_t step) {
   bbw::StageParams<real> P;
   P.qin = static_cast<const real*>(qin);
   P.qout = static_cast<real*>(out);
@@ -337,14 +328,7 @@ bbw_status spatial(bbw_solver* s, const void* qin, void* out, double sgn, bool s
   P.dt = real(0);
   P.tau_p = real(sgn * s->tau_p);
   P.tau_u = real(sgn * s->tau_u);
-  P.n_src_groups = (sources && s->src_elem >= 0) ? 1 : 0;
-  P.src_groups = s->d_src_group;
-  P.src_slots = s->d_src_slots;
-  P.src_vec = static_cast<const real*>(s->d_src);
-  P.src_wav = s->d_src_wav;
-  P.t_dev = nullptr;
-  P.t_step = t;
-  P.c_dt = cc[stage] * dt;
+  bbw::set_stage_sources<bbw::StageParams<real>, real>(s, P, step, stage, sources);
   P.status = s->d_status;
   BBW_CUDA(s->ops->launch_spatial(s->M, s->prec == 64, &P, s->grid_stage, s->stream));
   return BBW_OK;
@@ -372,7 +356,7 @@ bbw_status wadg_user(bbw_solver* s, const void* in, const void* c2u, void* out) 
 // Adjoint of stage `stage` of the step starting at time t, whose stage input
 // (internal layout) is qin; updates qb, rb (user layout) and gc.
 template <typename real>
-bbw_status adjoint_stage(bbw_solver* s, AdjointData* a, const void* qin, int stage, double dt, double t) {
+bbw_status adjoint_stage(bbw_solver* s, AdjointData* a, const void* qin, int stage, double dt, int64_t step) {
   double ca[5], cb[5], cc[5];
   bbw_lsrk_coeffs(ca, cb, cc);
   const int64_t K = s->K;
@@ -403,10 +387,10 @@ bbw_status adjoint_stage(bbw_solver* s, AdjointData* a, const void* qin, int sta
   to_internal_scaled<real><<<blocks_for(ni), 256, 0, st>>>(y, static_cast<real*>(a->yi), K, Np, V, ivol, ni);
   BBW_CUDA(cudaGetLastError());
   // z = |D| A_{-tau}(y); v_p = (A_tau(q_s) + sources)_p
-  r = spatial<real>(s, a->yi, a->zi, -1.0, false, stage, dt, t);
+  r = spatial<real>(s, a->yi, a->zi, -1.0, false, stage, step);
   if (r != BBW_OK) return r;
   to_user_scaled<real><<<blocks_for(4 * nf), 256, 0, st>>>(static_cast<const real*>(a->zi), z, K, Np, V, 4, vol);
-  r = spatial<real>(s, qin, a->zi, 1.0, true, stage, dt, t);
+  r = spatial<real>(s, qin, a->zi, 1.0, true, stage, step);
   if (r != BBW_OK) return r;
   to_user_scaled<real><<<blocks_for(nf), 256, 0, st>>>(static_cast<const real*>(a->zi), v, K, Np, V, 1, nullptr);
   BBW_CUDA(cudaGetLastError());
@@ -427,7 +411,7 @@ bbw_status record(bbw_solver* s, double dt, int64_t nsteps, int64_t every, doubl
   a->dt = dt;
   a->nsteps = nsteps;
   a->every = every;
-  a->t_step.assign(size_t(nsteps), 0.0);
+  a->k_step.assign(size_t(nsteps), 0);
   const int64_t nck = std::max<int64_t>((nsteps + every - 1) / every, 1);
   while (int64_t(a->ckpt.size()) > nck) {  // keep the buffers of earlier runs, drop extras
     if (a->ckpt.back()) cudaFree(a->ckpt.back());
@@ -443,7 +427,7 @@ bbw_status record(bbw_solver* s, double dt, int64_t nsteps, int64_t every, doubl
   for (int64_t n = 0; n < nsteps; ++n) {
     if (n % every == 0)
       BBW_CUDA(cudaMemcpyAsync(a->ckpt[size_t(n / every)], s->q[s->cur], bytes, cudaMemcpyDeviceToDevice, s->stream));
-    a->t_step[size_t(n)] = s->t;
+    a->k_step[size_t(n)] = s->steps;
     bbw_status st = bbw_step(s, dt, 1);
     if (st != BBW_OK) return st;
     if (a->nrec > 0)
@@ -525,7 +509,7 @@ bbw_status adjoint(bbw_solver* s, const double* g, double* grad_c2, double* grad
       for (int sg = 0; sg < 5; ++sg) {
         if (sg == 4 && n + 1 == n1) break;  // the segment's final state is not needed
         void* out = sg < 4 ? a->seg[b5 + sg + 1] : a->seg[b5 + 5];
-        st = forward_stage<real>(s, a->seg[b5 + sg], out, a->rs, sg, dt, a->t_step[size_t(n)]);
+        st = forward_stage<real>(s, a->seg[b5 + sg], out, a->rs, sg, dt, a->k_step[size_t(n)]);
         if (st != BBW_OK) return st;
       }
     }
@@ -539,7 +523,7 @@ bbw_status adjoint(bbw_solver* s, const double* g, double* grad_c2, double* grad
       }
       const size_t b5 = size_t(n - n0) * 5;
       for (int sg = 4; sg >= 0; --sg) {
-        st = adjoint_stage<real>(s, a, a->seg[b5 + sg], sg, dt, a->t_step[size_t(n)]);
+        st = adjoint_stage<real>(s, a, a->seg[b5 + sg], sg, dt, a->k_step[size_t(n)]);
         if (st != BBW_OK) return st;
       }
       // the step's res enters only through stage 0 (a_0 = 0): the res

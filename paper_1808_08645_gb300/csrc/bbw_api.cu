@@ -273,8 +273,9 @@ void free_solver(bbw_solver* s) {
   if (!s) return;
   bbw::free_adjoint(s);
   for (void* p : {s->q[0], s->q[1], s->res, s->d_c2, s->d_geom, static_cast<void*>(s->d_conn), s->d_src,
-                  static_cast<void*>(s->d_src_group), static_cast<void*>(s->d_src_slots),
-                  static_cast<void*>(s->d_src_wav), s->d_stage, static_cast<void*>(s->d_perm),
+                  static_cast<void*>(s->d_src_groups), static_cast<void*>(s->d_src_slots),
+                  static_cast<void*>(s->d_src_ser), static_cast<void*>(s->d_src_amp), s->d_stage,
+                  static_cast<void*>(s->d_perm),
                   static_cast<void*>(s->d_inv),
                   static_cast<void*>(s->d_status)})
     if (p) cudaFree(p);
@@ -485,7 +486,6 @@ bbw_status upload_geometry(bbw_solver* s) {
 
 template <typename real>
 bbw_status launch_stage(bbw_solver* s, int stage, double dt) {
-  static const std::array<double, 5> c = rk_stage_times();
   bbw::StageParams<real> P;
   P.qin = static_cast<const real*>(s->q[s->cur]);
   P.qout = static_cast<real*>(s->q[1 - s->cur]);
@@ -500,19 +500,15 @@ bbw_status launch_stage(bbw_solver* s, int stage, double dt) {
   P.dt = real(dt);
   P.tau_p = real(s->tau_p);
   P.tau_u = real(s->tau_u);
-  P.n_src_groups = s->src_elem >= 0 ? 1 : 0;
-  P.src_groups = s->d_src_group;
-  P.src_slots = s->d_src_slots;
-  P.src_vec = static_cast<const real*>(s->d_src);
-  P.src_wav = s->d_src_wav;
-  P.t_dev = nullptr;
-  P.t_step = s->t;
-  P.c_dt = c[stage] * dt;
+  bbw::set_stage_sources<bbw::StageParams<real>, real>(s, P, s->steps, stage, true);
   P.status = s->d_status;
   BBW_CUDA(s->ops->launch_stage(s->M, s->prec == 64, &P, s->grid_stage, s->stream));
   s->cur = 1 - s->cur;
   s->stages += 1;
-  if (stage == 4) s->t += dt;
+  if (stage == 4) {
+    s->t += dt;
+    s->steps += 1;
+  }
   return BBW_OK;
 }
 
@@ -639,6 +635,85 @@ bbw_status bbw::point_source_vector(const bbw_solver* s, const double* xs, int64
 // ---------------------------------------------------------------------------
 // C ABI
 
+namespace {
+
+// Replace the solver's sources: nelem distinct elements (caller's numbering)
+// with coefficient vectors coeffs [nelem][Np] sharing the amplitude series
+// amp [nsamples]. Waits for the solver's stream before freeing old buffers.
+bbw_status install_sources(bbw_solver* s, int64_t nelem, const int64_t* elems, const double* coeffs,
+                           const double* amp, int64_t nsamples) {
+  if (nelem < 0 || nsamples < 0) return fail(BBW_ERR_ARG, "negative source count or sample count");
+  if ((nelem > 0 && (!elems || !coeffs)) || (nsamples > 0 && !amp)) return fail(BBW_ERR_ARG, "NULL argument");
+  if (nelem > s->K) return fail(BBW_ERR_ARG, "more source elements than elements");
+  std::vector<char> seen(size_t(s->K), 0);
+  std::vector<int64_t> ie(static_cast<size_t>(nelem));
+  for (int64_t k = 0; k < nelem; ++k) {
+    const int64_t e = elems[k];
+    if (e < 0 || e >= s->K) return fail(BBW_ERR_ARG, "source element out of range");
+    if (seen[size_t(e)]) return fail(BBW_ERR_ARG, "a source element is listed twice");
+    seen[size_t(e)] = 1;
+    ie[size_t(k)] = s->slot(e);
+  }
+  for (int64_t i = 0; i < nelem * s->Np; ++i)
+    if (!std::isfinite(coeffs[i])) return fail(BBW_ERR_ARG, "non-finite source coefficient");
+  for (int64_t i = 0; i < nsamples; ++i)
+    if (!std::isfinite(amp[i])) return fail(BBW_ERR_ARG, "non-finite amplitude sample");
+  BBW_CUDA(cudaStreamSynchronize(s->stream));
+  for (void** p : {&s->d_src, reinterpret_cast<void**>(&s->d_src_groups), reinterpret_cast<void**>(&s->d_src_slots),
+                   reinterpret_cast<void**>(&s->d_src_ser), reinterpret_cast<void**>(&s->d_src_amp)}) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+  }
+  s->nsrc = s->n_src_groups = s->n_amp = 0;
+  s->src_elems.clear();
+  if (nelem == 0 || nsamples == 0) return BBW_OK;
+  std::vector<int64_t> groups;
+  std::vector<int32_t> slots;
+  bbw::source_groups(ie, s->V, &groups, &slots);
+  const size_t nvec = size_t(nelem) * s->Np;
+  BBW_CUDA(cudaMalloc(&s->d_src, nvec * s->rsz()));
+  BBW_CUDA(cudaMalloc(reinterpret_cast<void**>(&s->d_src_groups), groups.size() * sizeof(int64_t)));
+  BBW_CUDA(cudaMalloc(reinterpret_cast<void**>(&s->d_src_slots), slots.size() * sizeof(int32_t)));
+  BBW_CUDA(cudaMalloc(reinterpret_cast<void**>(&s->d_src_ser), size_t(nelem) * sizeof(int32_t)));
+  BBW_CUDA(cudaMalloc(reinterpret_cast<void**>(&s->d_src_amp), size_t(nsamples) * sizeof(double)));
+  bbw_status st = upload(s, coeffs, s->d_src, nvec);
+  if (st != BBW_OK) return st;
+  const std::vector<int32_t> ser(static_cast<size_t>(nelem), 0);
+  BBW_CUDA(cudaMemcpy(s->d_src_groups, groups.data(), groups.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+  BBW_CUDA(cudaMemcpy(s->d_src_slots, slots.data(), slots.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  BBW_CUDA(cudaMemcpy(s->d_src_ser, ser.data(), ser.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  BBW_CUDA(cudaMemcpy(s->d_src_amp, amp, size_t(nsamples) * sizeof(double), cudaMemcpyHostToDevice));
+  BBW_CUDA(cudaStreamSynchronize(s->stream));
+  s->nsrc = nelem;
+  s->n_src_groups = int64_t(groups.size());
+  s->n_amp = nsamples;
+  s->src_elems.assign(elems, elems + nelem);
+  return BBW_OK;
+}
+
+}  // namespace
+
+namespace bbw {
+
+void source_groups(const std::vector<int64_t>& ie, int V, std::vector<int64_t>* groups,
+                   std::vector<int32_t>* slots) {
+  std::vector<std::pair<int64_t, int32_t>> by(ie.size());
+  for (size_t k = 0; k < ie.size(); ++k) by[k] = {ie[k], int32_t(k)};
+  std::sort(by.begin(), by.end());
+  groups->clear();
+  slots->clear();
+  for (const auto& [e, k] : by) {
+    const int64_t g = e / V;
+    if (groups->empty() || groups->back() != g) {
+      groups->push_back(g);
+      slots->insert(slots->end(), size_t(V), -1);
+    }
+    (*slots)[(groups->size() - 1) * size_t(V) + size_t(e % V)] = k;
+  }
+}
+
+}  // namespace bbw
+
 extern "C" {
 
 int bbw_version(void) { return 100; }
@@ -706,7 +781,7 @@ bbw_status bbw::create_solver(int64_t nverts, const double* vxyz, int64_t K, con
   bool ok = alloc(&s->q[0], s->nstate_internal() * rs) && alloc(&s->q[1], s->nstate_internal() * rs) &&
             alloc(&s->res, s->nstate_internal() * rs) && alloc(&s->d_c2, ng * s->Mp * rs) &&
             alloc(&s->d_geom, ng * 9 * rs) && alloc(reinterpret_cast<void**>(&s->d_conn), ng * 16) &&
-            alloc(&s->d_src, size_t(s->Np) * rs) && alloc(reinterpret_cast<void**>(&s->d_status), 16);
+            alloc(reinterpret_cast<void**>(&s->d_status), 16);
   if (!ok) {
     std::string msg = std::string("device allocation failed: ") + cudaGetErrorString(cudaGetLastError());
     free_solver(s);
@@ -840,6 +915,7 @@ bbw_status bbw_set_state(bbw_solver* s, const double* q, const double* res, doub
   }
   s->t = t;
   s->stages = 0;
+  s->steps = 0;
   return BBW_OK;
 }
 
@@ -853,6 +929,7 @@ bbw_status bbw_set_state_device(bbw_solver* s, const void* q, const void* res, i
     BBW_CUDA(cudaMemsetAsync(s->res, 0, s->nstate_internal() * s->rsz(), s->stream));
   s->t = t;
   s->stages = 0;
+  s->steps = 0;
   return BBW_OK;
 }
 
@@ -880,46 +957,32 @@ bbw_status bbw_get_state_device(bbw_solver* s, void* q, void* res, int dtype) {
   return BBW_OK;
 }
 
-bbw_status bbw_set_source(bbw_solver* s, int64_t elem, const double* coeffs, double f0, double t0) {
-  if (!s || !coeffs) return fail(BBW_ERR_ARG, "NULL argument");
-  if (elem < 0 || elem >= s->K) return fail(BBW_ERR_ARG, "source element out of range");
-  if (!std::isfinite(f0) || !std::isfinite(t0)) return fail(BBW_ERR_ARG, "non-finite wavelet parameter");
-  bbw_status st = upload(s, coeffs, s->d_src, size_t(s->Np));
-  if (st != BBW_OK) return st;
-  if (!s->d_src_group) BBW_CUDA(cudaMalloc(reinterpret_cast<void**>(&s->d_src_group), sizeof(int64_t)));
-  if (!s->d_src_slots) BBW_CUDA(cudaMalloc(reinterpret_cast<void**>(&s->d_src_slots), s->V * sizeof(int32_t)));
-  if (!s->d_src_wav) BBW_CUDA(cudaMalloc(reinterpret_cast<void**>(&s->d_src_wav), 2 * sizeof(double)));
-  // one source group: internal slot e of elem is lane e % V of group e / V
-  const int64_t ie = s->slot(elem);
-  const int64_t grp = ie / s->V;
-  std::vector<int32_t> slots(size_t(s->V), -1);
-  slots[size_t(ie % s->V)] = 0;
-  const double wav[2] = {f0, t0};
-  BBW_CUDA(cudaMemcpyAsync(s->d_src_group, &grp, sizeof(grp), cudaMemcpyHostToDevice, s->stream));
-  BBW_CUDA(cudaMemcpyAsync(s->d_src_slots, slots.data(), slots.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
-                           s->stream));
-  BBW_CUDA(cudaMemcpyAsync(s->d_src_wav, wav, sizeof(wav), cudaMemcpyHostToDevice, s->stream));
-  BBW_CUDA(cudaStreamSynchronize(s->stream));
-  s->src_elem = elem;
-  s->f0 = f0;
-  s->t0 = t0;
-  return BBW_OK;
+bbw_status bbw_set_source(bbw_solver* s, int64_t elem, const double* coeffs, const double* amp, int64_t nsamples) {
+  if (!s) return fail(BBW_ERR_ARG, "solver is NULL");
+  if (!coeffs) return fail(BBW_ERR_ARG, "NULL argument");
+  return install_sources(s, 1, &elem, coeffs, amp, nsamples);
 }
 
-bbw_status bbw_set_point_source(bbw_solver* s, const double* xs, double f0, double t0, int64_t* elem) {
+bbw_status bbw_set_forcing(bbw_solver* s, int64_t nelem, const int64_t* elems, const double* coeffs,
+                           const double* amp, int64_t nsamples) {
+  if (!s) return fail(BBW_ERR_ARG, "solver is NULL");
+  return install_sources(s, nelem, elems, coeffs, amp, nsamples);
+}
+
+bbw_status bbw_set_point_source(bbw_solver* s, const double* xs, const double* amp, int64_t nsamples,
+                                int64_t* elem) {
   if (!s || !xs) return fail(BBW_ERR_ARG, "NULL argument");
   int64_t found = -1;
   std::vector<double> b;
   bbw_status st = bbw::point_source_vector(s, xs, 0, s->K, &found, &b);
   if (st != BBW_OK) return st;
   if (elem) *elem = found;
-  return bbw_set_source(s, found, b.data(), f0, t0);
+  return install_sources(s, 1, &found, b.data(), amp, nsamples);
 }
 
 bbw_status bbw_clear_source(bbw_solver* s) {
   if (!s) return fail(BBW_ERR_ARG, "solver is NULL");
-  s->src_elem = -1;
-  return BBW_OK;
+  return install_sources(s, 0, nullptr, nullptr, nullptr, 0);
 }
 
 bbw_status bbw_stage(bbw_solver* s, int stage, double dt) {

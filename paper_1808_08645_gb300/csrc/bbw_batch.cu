@@ -13,8 +13,8 @@
 // One RK step over all buckets is captured into a CUDA graph (one fork/join
 // branch per bucket, so buckets that do not fill the GPU run side by side)
 // and replayed per step. Everything a replay needs lives on the device: the
-// step time (advanced by a one-thread kernel at the end of the step) from
-// which the stage kernel evaluates the point-source wavelets, and the source
+// step counter (advanced by a one-thread kernel at the end of the step) from
+// which the stage kernel picks the sources' amplitude samples, and the source
 // tables. Two graphs are kept, one per parity of the ping-pong state buffers
 // (a step has five stages, so the parity flips every step); they are
 // rebuilt when dt or the penalty parameters change.
@@ -38,7 +38,7 @@ using bbw::fail;
 
 namespace {
 
-__global__ void advance_time_kernel(double* t, double dt) { t[0] += dt; }
+__global__ void advance_step_kernel(int64_t* step) { step[0] += 1; }
 
 }  // namespace
 
@@ -58,8 +58,11 @@ struct bbw_batch {
     int32_t* d_slots = nullptr;          // [members][V] source slot per lane of those groups
     int64_t n_groups = 0;
     void* d_vec = nullptr;               // [members][Np] source vectors
-    double* d_wav = nullptr;             // [members][2] Ricker f0, t0
+    int32_t* d_ser = nullptr;            // [members] amplitude series of member slot x: x
+    double* d_amp = nullptr;             // [members][n_amp] amplitude samples, zero padded
+    int64_t n_amp = 0;
     std::vector<int64_t> src_elem;       // per member slot: element of its source or -1
+    std::vector<std::vector<double>> amp;  // per member slot: its amplitude samples
     int grid0 = 1;                       // persistent grid of the solo solver (CTAs)
   };
   int n = 0, M = 0, prec = 32;
@@ -67,7 +70,7 @@ struct bbw_batch {
   bool own_stream = false;  // created here when the caller passed the legacy default stream
   std::vector<Member> members;
   std::vector<Bucket> buckets;
-  double* d_t = nullptr;  // device time at the start of the step
+  int64_t* d_step = nullptr;  // device step counter (amplitude sample 5 step + stage)
   double t = 0.0;
   int64_t steps = 0;
   int cur = 0;  // parity of the ping-pong state buffers (equal in all buckets)
@@ -93,11 +96,11 @@ void free_batch(bbw_batch* b) {
     if (k.side) cudaStreamDestroy(k.side);
     if (k.done) cudaEventDestroy(k.done);
     for (void* p : {static_cast<void*>(k.d_groups), static_cast<void*>(k.d_slots), k.d_vec,
-                    static_cast<void*>(k.d_wav)})
+                    static_cast<void*>(k.d_ser), static_cast<void*>(k.d_amp)})
       if (p) cudaFree(p);
   }
   if (b->fork) cudaEventDestroy(b->fork);
-  if (b->d_t) cudaFree(b->d_t);
+  if (b->d_step) cudaFree(b->d_step);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }
@@ -119,8 +122,8 @@ bbw_status check_member(const bbw_batch* b, int i) {
 // The five stage launches of one bucket on stream st (state parity b->cur).
 template <typename real>
 bbw_status launch_bucket_step(bbw_batch* b, bbw_batch::Bucket& k, double dt, cudaStream_t st) {
-  double a[5], bb[5], c[5];
-  bbw_lsrk_coeffs(a, bb, c);
+  double a[5], bb[5];
+  bbw_lsrk_coeffs(a, bb, nullptr);
   bbw_solver* s = k.s;
   int cur = b->cur;
   for (int stage = 0; stage < 5; ++stage) {
@@ -142,10 +145,12 @@ bbw_status launch_bucket_step(bbw_batch* b, bbw_batch::Bucket& k, double dt, cud
     P.src_groups = k.d_groups;
     P.src_slots = k.d_slots;
     P.src_vec = static_cast<const real*>(k.d_vec);
-    P.src_wav = k.d_wav;
-    P.t_dev = b->d_t;
-    P.t_step = 0.0;
-    P.c_dt = c[stage] * dt;
+    P.src_ser = k.d_ser;
+    P.src_amp = k.d_amp;
+    P.n_amp = k.n_amp;
+    P.step_dev = b->d_step;
+    P.step_host = 0;
+    P.stage = stage;
     P.status = s->d_status;
     BBW_CUDA(s->ops->launch_stage(s->M, s->prec == 64, &P, s->grid_stage, st));
     cur = 1 - cur;
@@ -154,7 +159,7 @@ bbw_status launch_bucket_step(bbw_batch* b, bbw_batch::Bucket& k, double dt, cud
 }
 
 // One RK step of every bucket, forked onto the bucket streams and joined back
-// onto the batch stream, then the device time advanced by dt.
+// onto the batch stream, then the device step counter advanced.
 bbw_status enqueue_step(bbw_batch* b, double dt) {
   if (b->serial) {
     for (auto& k : b->buckets) {
@@ -173,7 +178,7 @@ bbw_status enqueue_step(bbw_batch* b, double dt) {
       BBW_CUDA(cudaStreamWaitEvent(b->stream, k.done, 0));
     }
   }
-  advance_time_kernel<<<1, 1, 0, b->stream>>>(b->d_t, dt);
+  advance_step_kernel<<<1, 1, 0, b->stream>>>(b->d_step);
   BBW_CUDA(cudaGetLastError());
   return BBW_OK;
 }
@@ -262,29 +267,44 @@ bbw_status download_member_state(bbw_batch* b, int i, const void* base, double* 
   return BBW_OK;
 }
 
-// The bucket's source-group list from the members' source elements. The
-// number of groups is a kernel parameter, so the step graphs are rebuilt.
+// The bucket's source-group list from the members' source elements, and the
+// amplitude series of every member slot, zero padded to the longest. The
+// number of groups and the series length are kernel parameters, so the step
+// graphs are rebuilt.
 bbw_status upload_sources(bbw_batch* b, bbw_batch::Bucket& k) {
-  const int V = k.s->V;
-  std::map<int64_t, std::vector<int32_t>> groups;
+  std::vector<int64_t> ie;
+  std::vector<int32_t> slot_of;  // source index -> member slot
+  int64_t namp = 0;
   for (size_t slot = 0; slot < k.src_elem.size(); ++slot) {
     if (k.src_elem[slot] < 0) continue;
-    const int64_t e = k.s->slot(k.src_elem[slot]);  // internal position of the source element
-    auto& lanes = groups.try_emplace(e / V, std::vector<int32_t>(size_t(V), -1)).first->second;
-    lanes[size_t(e % V)] = int32_t(slot);
+    ie.push_back(k.s->slot(k.src_elem[slot]));  // internal position of the source element
+    slot_of.push_back(int32_t(slot));
+    namp = std::max<int64_t>(namp, int64_t(k.amp[slot].size()));
   }
   std::vector<int64_t> g;
   std::vector<int32_t> sl;
-  for (const auto& [grp, lanes] : groups) {
-    g.push_back(grp);
-    sl.insert(sl.end(), lanes.begin(), lanes.end());
-  }
-  k.n_groups = int64_t(g.size());
-  if (!g.empty()) {
-    BBW_CUDA(cudaMemcpyAsync(k.d_groups, g.data(), g.size() * sizeof(int64_t), cudaMemcpyHostToDevice, b->stream));
-    BBW_CUDA(cudaMemcpyAsync(k.d_slots, sl.data(), sl.size() * sizeof(int32_t), cudaMemcpyHostToDevice, b->stream));
-  }
+  bbw::source_groups(ie, k.s->V, &g, &sl);
+  for (auto& x : sl)
+    if (x >= 0) x = slot_of[size_t(x)];  // the kernel indexes vectors and series by member slot
   BBW_CUDA(cudaStreamSynchronize(b->stream));
+  if (namp != k.n_amp) {
+    if (k.d_amp) cudaFree(k.d_amp);
+    k.d_amp = nullptr;
+    k.n_amp = 0;
+    if (namp > 0) BBW_CUDA(cudaMalloc(reinterpret_cast<void**>(&k.d_amp), size_t(namp) * k.amp.size() * sizeof(double)));
+    k.n_amp = namp;
+  }
+  if (namp > 0) {
+    std::vector<double> flat(size_t(namp) * k.amp.size(), 0.0);
+    for (size_t slot = 0; slot < k.amp.size(); ++slot)
+      std::copy(k.amp[slot].begin(), k.amp[slot].end(), flat.begin() + ptrdiff_t(slot * size_t(namp)));
+    BBW_CUDA(cudaMemcpy(k.d_amp, flat.data(), flat.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  k.n_groups = namp > 0 ? int64_t(g.size()) : 0;
+  if (!g.empty()) {
+    BBW_CUDA(cudaMemcpy(k.d_groups, g.data(), g.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+    BBW_CUDA(cudaMemcpy(k.d_slots, sl.data(), sl.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  }
   invalidate_graphs(b);
   return BBW_OK;
 }
@@ -362,21 +382,27 @@ bbw_status bbw_batch_create(int n, const int64_t* nverts, const double* const* v
                                        b->stream, &ranges, &k.s);
     if (st != BBW_OK) return bail(st);
     k.src_elem.assign(ids.size(), -1);
+    k.amp.assign(ids.size(), std::vector<double>());
     k.grid0 = k.s->grid_stage;
-    const bool ok = cudaStreamCreateWithFlags(&k.side, cudaStreamNonBlocking) == cudaSuccess &&
+    bool ok = cudaStreamCreateWithFlags(&k.side, cudaStreamNonBlocking) == cudaSuccess &&
                     cudaEventCreateWithFlags(&k.done, cudaEventDisableTiming) == cudaSuccess &&
                     cudaMalloc(reinterpret_cast<void**>(&k.d_groups), ids.size() * sizeof(int64_t)) == cudaSuccess &&
                     cudaMalloc(reinterpret_cast<void**>(&k.d_slots), ids.size() * V * sizeof(int32_t)) == cudaSuccess &&
                     cudaMalloc(&k.d_vec, ids.size() * k.s->Np * k.s->rsz()) == cudaSuccess &&
-                    cudaMalloc(reinterpret_cast<void**>(&k.d_wav), ids.size() * 2 * sizeof(double)) == cudaSuccess;
+                    cudaMalloc(reinterpret_cast<void**>(&k.d_ser), ids.size() * sizeof(int32_t)) == cudaSuccess;
+    if (ok) {
+      std::vector<int32_t> ser(ids.size());
+      for (size_t x = 0; x < ser.size(); ++x) ser[x] = int32_t(x);
+      ok = cudaMemcpy(k.d_ser, ser.data(), ser.size() * sizeof(int32_t), cudaMemcpyHostToDevice) == cudaSuccess;
+    }
     b->buckets.push_back(k);
     if (!ok) return bail(fail(BBW_ERR_CUDA, "batch allocation failed"));
     st = upload_sources(b, b->buckets.back());
     if (st != BBW_OK) return bail(st);
   }
   if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaMalloc(reinterpret_cast<void**>(&b->d_t), sizeof(double)) != cudaSuccess ||
-      cudaMemset(b->d_t, 0, sizeof(double)) != cudaSuccess)
+      cudaMalloc(reinterpret_cast<void**>(&b->d_step), sizeof(int64_t)) != cudaSuccess ||
+      cudaMemset(b->d_step, 0, sizeof(int64_t)) != cudaSuccess)
     return bail(fail(BBW_ERR_CUDA, "batch allocation failed"));
   *out = b;
   return BBW_OK;
@@ -487,11 +513,14 @@ bbw_status bbw_batch_get_state(bbw_batch* b, int i, double* q, double* res) {
   return BBW_OK;
 }
 
-bbw_status bbw_batch_set_point_source(bbw_batch* b, int i, const double* xs, double f0, double t0, int64_t* elem) {
+bbw_status bbw_batch_set_point_source(bbw_batch* b, int i, const double* xs, const double* amp, int64_t nsamples,
+                                      int64_t* elem) {
   bbw_status st = check_member(b, i);
   if (st != BBW_OK) return st;
-  if (!xs) return fail(BBW_ERR_ARG, "NULL argument");
-  if (!std::isfinite(f0) || !std::isfinite(t0)) return fail(BBW_ERR_ARG, "non-finite wavelet parameter");
+  if (!xs || (nsamples > 0 && !amp)) return fail(BBW_ERR_ARG, "NULL argument");
+  if (nsamples < 0) return fail(BBW_ERR_ARG, "nsamples < 0");
+  for (int64_t x = 0; x < nsamples; ++x)
+    if (!std::isfinite(amp[x])) return fail(BBW_ERR_ARG, "non-finite amplitude sample");
   const auto& m = b->members[size_t(i)];
   auto& k = b->buckets[size_t(m.bucket)];
   bbw_solver* s = k.s;
@@ -501,12 +530,11 @@ bbw_status bbw_batch_set_point_source(bbw_batch* b, int i, const double* xs, dou
   if (st != BBW_OK) return st;
   const int slot = int(std::find(k.members.begin(), k.members.end(), i) - k.members.begin());
   k.src_elem[size_t(slot)] = found;
-  const double wav[2] = {f0, t0};
+  k.amp[size_t(slot)].assign(amp, amp + nsamples);
   std::vector<float> vf(vec.begin(), vec.end());
   const void* vsrc = s->prec == 64 ? static_cast<const void*>(vec.data()) : static_cast<const void*>(vf.data());
   BBW_CUDA(cudaMemcpyAsync(static_cast<char*>(k.d_vec) + size_t(slot) * s->Np * s->rsz(), vsrc, s->Np * s->rsz(),
                            cudaMemcpyHostToDevice, b->stream));
-  BBW_CUDA(cudaMemcpyAsync(k.d_wav + 2 * slot, wav, sizeof(wav), cudaMemcpyHostToDevice, b->stream));
   st = upload_sources(b, k);
   if (st != BBW_OK) return st;
   if (elem) *elem = found - m.e0;
@@ -517,6 +545,7 @@ bbw_status bbw_batch_clear_sources(bbw_batch* b) {
   if (!b) return fail(BBW_ERR_ARG, "batch is NULL");
   for (auto& k : b->buckets) {
     std::fill(k.src_elem.begin(), k.src_elem.end(), -1);
+    for (auto& a : k.amp) a.clear();
     bbw_status st = upload_sources(b, k);
     if (st != BBW_OK) return st;
   }
@@ -620,6 +649,9 @@ bbw_status bbw_batch_autotune(bbw_batch* b, int steps, int* schedule, double* ms
   b->t = saved_t;
   b->steps = saved_steps;
   for (auto& k : b->buckets) k.s->t = saved_t;
+  cudaError_t ec = cudaStreamSynchronize(b->stream);
+  if (ec == cudaSuccess) ec = cudaMemcpy(b->d_step, &saved_steps, sizeof(int64_t), cudaMemcpyHostToDevice);
+  if (st == BBW_OK && ec != cudaSuccess) st = fail(BBW_ERR_CUDA, "step counter restore failed");
   if (st != BBW_OK) return st;
   if (schedule) *schedule = best_c;
   if (ms_per_step) *ms_per_step = double(best) / steps;
@@ -638,8 +670,9 @@ bbw_status bbw_batch_sync(bbw_batch* b) {
 bbw_status bbw_batch_set_time(bbw_batch* b, double t) {
   if (!b) return fail(BBW_ERR_ARG, "batch is NULL");
   if (!std::isfinite(t)) return fail(BBW_ERR_ARG, "t is not finite");
-  BBW_CUDA(cudaMemcpyAsync(b->d_t, &t, sizeof(double), cudaMemcpyHostToDevice, b->stream));
+  const int64_t zero = 0;
   BBW_CUDA(cudaStreamSynchronize(b->stream));
+  BBW_CUDA(cudaMemcpy(b->d_step, &zero, sizeof(int64_t), cudaMemcpyHostToDevice));
   b->t = t;
   b->steps = 0;
   for (auto& k : b->buckets) {

@@ -35,14 +35,6 @@ BBW_HD constexpr int idx3(int n, int j, int k, int l) {
 }
 BBW_HD constexpr int idx2(int n, int b1, int b2) { return b2 * (n + 1) - b2 * (b2 - 1) / 2 + b1; }
 
-// Ricker wavelet r(t) = (1 - 2 a) exp(-a), a = (pi f0 (t - t0))^2: the time
-// signature of the point sources (evaluated in double on host and device)
-BBW_HD double ricker_wavelet(double t, double f0, double t0) {
-  const double x = 3.14159265358979323846 * f0 * (t - t0);
-  const double a = x * x;
-  return (1.0 - 2.0 * a) * exp(-a);
-}
-
 // local vertices of face f (the three vertices other than f, increasing)
 constexpr int kFaceVerts[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
 // face orientation codes: own face vertex x <-> neighbour face vertex kPerm[c][x]

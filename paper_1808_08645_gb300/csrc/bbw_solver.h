@@ -62,10 +62,16 @@ struct bbw_solver {
   void* d_c2 = nullptr;
   void* d_geom = nullptr;
   int32_t* d_conn = nullptr;
-  void* d_src = nullptr;          // [Np] source vector
-  int64_t* d_src_group = nullptr;  // [1] group of src_elem
-  int32_t* d_src_slots = nullptr;  // [V] source slot per lane of that group (0 at src_elem, else -1)
-  double* d_src_wav = nullptr;    // [2] Ricker f0, t0
+  // sources (bbw_set_source / bbw_set_forcing): the source elements' groups
+  // in ascending order, the source index of each element lane of a listed
+  // group (-1: none), the source vectors and their one amplitude series
+  void* d_src = nullptr;            // [nsrc][Np] source vectors
+  int64_t* d_src_groups = nullptr;  // [n_src_groups]
+  int32_t* d_src_slots = nullptr;   // [n_src_groups][V]
+  int32_t* d_src_ser = nullptr;     // [nsrc] amplitude series of each source (all 0)
+  double* d_src_amp = nullptr;      // [n_amp] amplitude samples
+  int64_t nsrc = 0, n_src_groups = 0, n_amp = 0;
+  std::vector<int64_t> src_elems;   // the caller's element of each source
   unsigned int* d_status = nullptr;
   void* pinned = nullptr;
   size_t pinned_bytes = 0;
@@ -74,9 +80,8 @@ struct bbw_solver {
   int cur = 0;
   double t = 0.0;
   int64_t stages = 0;
+  int64_t steps = 0;  // completed RK steps since the last set_state: amplitude sample 5 steps + stage
   double tau_p = 1.0, tau_u = 1.0;
-  int64_t src_elem = -1;
-  double f0 = 0.0, t0 = 0.0;
   AdjointData* adj = nullptr;  // receivers, recorded run, adjoint buffers (bbw_adjoint.cu)
   // element renumbering for locality: internal slot e holds the caller's
   // element perm[e], inv[perm[e]] = e (empty / NULL: the identity)
@@ -122,10 +127,31 @@ void free_adjoint(bbw_solver* s);
 bbw_status ensure_pinned(bbw_solver* s, size_t bytes);
 // Wait for the solver's stream and surface the device status word.
 bbw_status check_status(bbw_solver* s);
+// Source tables of the stage kernel for a list of source elements (internal
+// slots ie[k], k = source index): the ascending list of their groups and, per
+// listed group, the source index of each of its V element lanes (-1: none).
+void source_groups(const std::vector<int64_t>& ie, int V, std::vector<int64_t>* groups,
+                   std::vector<int32_t>* slots);
 // Point source at xs searched among elements [e_begin, e_end) (lowest index
 // wins on shared faces): its element and the vector M^{-1} B(x_s) / |D| of
 // N_p Bernstein coefficients.
 bbw_status point_source_vector(const bbw_solver* s, const double* xs, int64_t e_begin, int64_t e_end,
                                int64_t* elem, std::vector<double>* vec);
+
+// Source fields of a stage launch of solver s at stage `stage` of step `step`
+// (sources off when on == false).
+template <typename P_t, typename real>
+void set_stage_sources(const bbw_solver* s, P_t& P, int64_t step, int stage, bool on) {
+  P.n_src_groups = on ? s->n_src_groups : 0;
+  P.src_groups = s->d_src_groups;
+  P.src_slots = s->d_src_slots;
+  P.src_vec = static_cast<const real*>(s->d_src);
+  P.src_ser = s->d_src_ser;
+  P.src_amp = s->d_src_amp;
+  P.n_amp = s->n_amp;
+  P.step_dev = nullptr;
+  P.step_host = step;
+  P.stage = stage;
+}
 
 }  // namespace bbw

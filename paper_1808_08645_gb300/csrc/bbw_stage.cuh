@@ -59,21 +59,23 @@ struct StageParams {
   int64_t G;                      // number of element groups
   real a, b, dt;
   real tau_p, tau_u;
-  // point sources, listed by group: src_groups[j] (ascending) holds at least
-  // one source and src_slots[j][v] is the source of its element lane v (-1:
-  // none); n_src_groups == 0: no sources. Source k adds r_k(t_s) src_vec[k][.]
-  // to the p right-hand side, r_k the Ricker wavelet of (f0, t0) =
-  // src_wav[k][0..1] at the stage time t_s = t + c_dt, where t, the time at
-  // the start of the step, is *t_dev (device-resident, for replayed graphs)
-  // or t_step.
+  // sources, listed by group: src_groups[j] (ascending) holds at least one
+  // source element and src_slots[j][v] is the source of its element lane v
+  // (-1: none); n_src_groups == 0: no sources. Source k adds
+  // a_k src_vec[k][.] to the p right-hand side, with the host-given amplitude
+  // sample a_k = src_amp[src_ser[k]][i] of sample i = 5 * step + stage
+  // (0 for i >= n_amp), where step, the number of completed RK steps, is
+  // *step_dev (device-resident, for replayed graphs) or step_host.
   int64_t n_src_groups;
   const int64_t* __restrict__ src_groups;  // [n_src_groups]
   const int32_t* __restrict__ src_slots;   // [n_src_groups][V]
   const real* __restrict__ src_vec;        // [nsrc][Np]
-  const double* __restrict__ src_wav;      // [nsrc][2]
-  const double* t_dev;
-  double t_step;
-  double c_dt;
+  const int32_t* __restrict__ src_ser;     // [nsrc] amplitude series of each source
+  const double* __restrict__ src_amp;      // [nseries][n_amp]
+  int64_t n_amp;
+  const int64_t* step_dev;
+  int64_t step_host;
+  int stage;
   unsigned int* status;           // bit 0: non-finite output
 };
 
@@ -484,12 +486,11 @@ __device__ __forceinline__ void wadg_group(const Tables<N, M, real>& tab, real* 
   }
 }
 
-// Ricker amplitude of source sd at the stage time; out of line, since only
-// the groups that hold a source call it.
+// Amplitude sample of source sd at this stage (0 past the end of its series).
 template <typename real>
-__device__ __noinline__ double stage_wavelet(const StageParams<real>& P, int sd) {
-  const double t = (P.t_dev ? *P.t_dev : P.t_step) + P.c_dt;
-  return ricker_wavelet(t, P.src_wav[2 * sd], P.src_wav[2 * sd + 1]);
+__device__ __forceinline__ double stage_amplitude(const StageParams<real>& P, int sd) {
+  const int64_t i = 5 * (P.step_dev ? *P.step_dev : P.step_host) + P.stage;
+  return i < P.n_amp ? P.src_amp[size_t(P.src_ser[sd]) * size_t(P.n_amp) + size_t(i)] : 0.0;
 }
 
 // SP = false: one LSRK stage (above). SP = true: the spatial operator alone,
@@ -573,7 +574,7 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
     if (t < V) {
       const int sd = next_src == g ? P.src_slots[size_t(js) * V + t] : -1;
       CS[4 * V + t] = sd;
-      if (sd >= 0) AMP[t] = real(stage_wavelet(P, sd));
+      if (sd >= 0) AMP[t] = real(stage_amplitude(P, sd));
     }
     vt gm[4][3];
 #pragma unroll

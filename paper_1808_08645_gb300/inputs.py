@@ -26,6 +26,7 @@ __all__ = [
     "c2_smooth_random", "c2_config_small", "gaussian_pulse", "random_state",
     "PARITY_CONFIG", "SWEEP_CONFIG", "BATCH_CONFIG", "batched_instances", "ADJOINT_CONFIG",
     "top_face_receivers", "ELASTIC_CONFIG", "elastic_media", "elastic_pulse",
+    "ricker", "ricker_samples", "manufactured_forcing",
 ]
 
 #: the FP64 parity workload: 4^3 hexes x 6 = 384 tets, N=3, M=1, T=0.5
@@ -226,3 +227,35 @@ def random_state(K: int, Np: int, seed: int = 0, dtype=np.float64) -> np.ndarray
     """Standard-normal state of shape (4, K, Np), rounded to ``dtype``."""
     rng = np.random.default_rng(seed)
     return rng.standard_normal((4, K, Np)).astype(dtype)
+
+
+def ricker(t, f0: float, t0: float):
+    """Ricker wavelet (1 - 2 a) exp(-a), a = (pi f0 (t - t0))^2 (a source time
+    signature; not part of the method)."""
+    a = (np.pi * f0 * (np.asarray(t, dtype=np.float64) - t0)) ** 2
+    return (1.0 - 2.0 * a) * np.exp(-a)
+
+
+def ricker_samples(f0: float, t0: float, dt: float, nsteps: int, stage_times, t_start: float = 0.0,
+                   signal=None) -> np.ndarray:
+    """Amplitude samples of a source time function, one per RK stage:
+    sample 5 n + s = signal(t_start + (n + c_s) dt) for n < nsteps, with
+    c_s = stage_times[s] (the RK scheme's stage times, passed in) and
+    signal the Ricker wavelet of (f0, t0) unless given."""
+    c = np.asarray(stage_times, dtype=np.float64).reshape(1, 5)
+    t = t_start + (np.arange(nsteps, dtype=np.float64)[:, None] + c) * dt
+    sig = signal if signal is not None else (lambda x: ricker(x, f0, t0))
+    return np.asarray(sig(t), dtype=np.float64).reshape(-1)
+
+
+def manufactured_forcing(c2):
+    """The spatial part g(x) of a separable forcing f(x, t) = g(x) sin(pi t):
+    g = (3 - 1/c^2(x)) pi sin(pi x) sin(pi y) sin(pi z), the forcing for which
+    p = sin(pi x) sin(pi y) sin(pi z) cos(pi t) solves the 3D acoustic system
+    with wave speed c^2 (the manufactured solution of the convergence study,
+    Sec. 6.1). Returns g as a field of points (P, 3)."""
+    def field(x):
+        s = np.sin(np.pi * x)
+        return (3.0 - 1.0 / c2(x)) * np.pi * s[:, 0] * s[:, 1] * s[:, 2]
+    return field
+

@@ -23,6 +23,12 @@ def rel_l2(a, b) -> float:
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+def stage_times():
+    """The RK stage times c_s as floats (the oracle's exact rationals)."""
+    from oracle.acoustic import lsrk_stage_times
+    return [float(c) for c in lsrk_stage_times()]
+
+
 def rounded(x, precision: int):
     return np.asarray(x, dtype=np.float32 if precision == 32 else np.float64).astype(np.float64)
 
@@ -49,13 +55,14 @@ def patch(etoe: np.ndarray, e: int):
     return out
 
 
-def oracle_stage_on_patch(vxyz, etov, etoe, e, N, M, c2, q, res, s, dt, t,
+def oracle_stage_on_patch(vxyz, etov, etoe, e, N, M, c2, q, res, s, dt, step=0,
                           tau=(1.0, 1.0), source=None):
     """Oracle stage for element e alone, on the sub-mesh of e and its neighbours.
 
     The right-hand side of e depends only on e and its face neighbours, and
     e's walls are walls of the sub-mesh too, so e's result equals its result
-    on the full mesh. ``source`` = (x, f0, t0) is applied only if e holds it.
+    on the full mesh. ``source`` = (x, amplitude samples) is applied only if
+    e holds it; ``step`` is the RK step the stage belongs to.
     Returns (q_out[:, e], res_out[:, e]).
     """
     els = patch(etoe, e)
@@ -65,6 +72,6 @@ def oracle_stage_on_patch(vxyz, etov, etoe, e, N, M, c2, q, res, s, dt, t,
     sub_vxyz = np.asarray(vxyz)[verts]
     orc = AcousticOracle(sub_vxyz, sub_etov, N, M, c2[els], tau_p=tau[0], tau_u=tau[1])
     if source is not None:
-        orc.set_point_source(source[0], f0=source[1], t0=source[2])
-    qo, ro = orc.stage(q[:, els], res[:, els], s, dt, t)
+        orc.set_point_source(source[0], source[1])
+    qo, ro = orc.stage(q[:, els], res[:, els], s, dt, step)
     return qo[:, 0], ro[:, 0]

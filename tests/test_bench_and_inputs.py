@@ -108,3 +108,45 @@ def test_elastic_inputs_recipe():
     assert np.all(q[:3] == 0) and np.all(q[6:] == 0)
     assert np.array_equal(q[3], q[4]) and np.array_equal(q[4], q[5]) and q[3].min() < 0
 
+
+
+def test_ricker_samples_are_the_wavelet_at_the_stage_times():
+    """Sample 5 n + s is the (separately pinned) oracle wavelet at
+    t_start + (n + c_s) dt, for the test helper and the library's helper."""
+    from oracle.acoustic import lsrk_stage_times, ricker
+    from paper_1808_08645_gb300 import binding as B
+    c = [float(x) for x in lsrk_stage_times()]
+    f0, t0, dt, n, ts = 10.0, 0.07, 3e-3, 9, 0.011
+    want = [ricker(ts + (k // 5 + c[k % 5]) * dt, f0, t0) for k in range(5 * n)]
+    got = inputs.ricker_samples(f0, t0, dt, n, c, t_start=ts)
+    assert np.allclose(got, want, rtol=0, atol=1e-15)
+    lib_got = B.ricker_samples(dt, n, f0=f0, t0=t0, t_start=ts)
+    assert np.allclose(lib_got, want, rtol=0, atol=1e-14)
+
+
+def test_manufactured_forcing_makes_the_manufactured_solution_exact():
+    """(1/c^2) dp/dt + div u = f and du/dt + grad p = 0 for
+    p = sin sin sin cos(pi t), u = -(cos sin sin, sin cos sin, sin sin cos) sin(pi t),
+    checked by central differences at random points and times."""
+    rng = np.random.default_rng(0)
+    x = rng.uniform(0.05, 0.95, (40, 3))
+    t = rng.uniform(0.0, 2.0, 40)
+    c2 = inputs.c2_config_small
+    g = inputs.manufactured_forcing(c2)(x)
+
+    def p(x, t):
+        s = np.sin(np.pi * x)
+        return s[:, 0] * s[:, 1] * s[:, 2] * np.cos(np.pi * t)
+
+    def u(x, t):
+        s, c = np.sin(np.pi * x), np.cos(np.pi * x)
+        return -np.stack([c[:, 0] * s[:, 1] * s[:, 2], s[:, 0] * c[:, 1] * s[:, 2],
+                          s[:, 0] * s[:, 1] * c[:, 2]], 1) * np.sin(np.pi * t)[:, None]
+
+    h = 1e-5
+    pt = (p(x, t + h) - p(x, t - h)) / (2 * h)
+    div = sum((u(x + h * np.eye(3)[i], t)[:, i] - u(x - h * np.eye(3)[i], t)[:, i]) / (2 * h) for i in range(3))
+    assert np.allclose(pt / c2(x) + div, g * np.sin(np.pi * t), atol=1e-8)
+    ut = (u(x, t + h) - u(x, t - h)) / (2 * h)
+    gp = np.stack([(p(x + h * np.eye(3)[i], t) - p(x - h * np.eye(3)[i], t)) / (2 * h) for i in range(3)], 1)
+    assert np.allclose(ut + gp, 0.0, atol=1e-8)

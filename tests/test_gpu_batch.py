@@ -35,7 +35,9 @@ def _instances(prec, seed=0):
         K, Np, Mp = len(etov), bb.np_count(N), bb.np_count(M)
         c2 = rounded(rng.uniform(0.5, 2.0, (K, Mp)), prec)
         q = rounded(rng.standard_normal((4, K, Np)) * 1e-2, prec)
-        out.append(dict(vxyz=vxyz, etov=etov, N=N, c2=c2, q=q, xs=xs))
+        # amplitude samples of uneven lengths (the batch pads them with zeros)
+        amp = rng.uniform(-1.0, 1.0, 11 + 3 * j)
+        out.append(dict(vxyz=vxyz, etov=etov, N=N, c2=c2, q=q, xs=xs, amp=amp))
     return out
 
 
@@ -45,7 +47,7 @@ def _batch(insts, prec):
         b.set_c2(i, d["c2"])
         b.set_state(i, d["q"])
         if d["xs"] is not None:
-            b.set_point_source(i, np.array(d["xs"]), f0=10.0, t0=0.1)
+            b.set_point_source(i, np.array(d["xs"]), d["amp"])
     return b
 
 
@@ -54,7 +56,7 @@ def _solo(d, prec):
     s.set_c2(d["c2"])
     s.set_state(d["q"])
     if d["xs"] is not None:
-        s.set_point_source(np.array(d["xs"]), f0=10.0, t0=0.1)
+        s.set_point_source(np.array(d["xs"]), d["amp"])
     return s
 
 
@@ -108,7 +110,7 @@ def test_batch_instance_matches_oracle():
     b.step(dt, nsteps)
     d = insts[2]
     orc = AcousticOracle(d["vxyz"], d["etov"], d["N"], M, d["c2"])
-    orc.set_point_source(np.array(d["xs"]), f0=10.0, t0=0.1)
+    orc.set_point_source(np.array(d["xs"]), d["amp"])
     qo, _ = orc.run(d["q"], dt, nsteps)
     assert rel_l2(b.get_state(2), qo) <= TOL_FINAL[prec]
     b.close()
@@ -128,9 +130,9 @@ def test_member_layout_and_moving_a_source():
             assert f1 >= f0 + k0
     # moving instance 0's source equals a solo solver with the moved source
     d = dict(insts[0], xs=(0.2, 0.3, 0.7))
-    e = b.set_point_source(0, np.array(d["xs"]), f0=10.0, t0=0.1)
+    e = b.set_point_source(0, np.array(d["xs"]), d["amp"])
     s = _solo(d, 32)
-    assert e == s.set_point_source(np.array(d["xs"]), f0=10.0, t0=0.1)
+    assert e == s.set_point_source(np.array(d["xs"]), d["amp"])
     b.step(2e-3, 2)
     s.step(2e-3, 2)
     assert np.array_equal(b.get_state(0), s.get_state()[0])
@@ -154,7 +156,7 @@ def test_batch_argument_errors():
     with pytest.raises(B.BBWError, match="BBW_ERR_NONPOS_C2"):
         b.set_c2(0, -np.ones((len(insts[0]["etov"]), bb.np_count(M))))
     with pytest.raises(B.BBWError, match="BBW_ERR_ARG"):
-        b.set_point_source(1, np.array([5.0, 5.0, 5.0]))
+        b.set_point_source(1, np.array([5.0, 5.0, 5.0]), np.ones(3))
     b.close()
 
 

@@ -35,7 +35,7 @@ CASES = textwrap.dedent("""
         s = B.Solver(vxyz, etov, N, 2, 32)
         s.set_c2(rng.uniform(0.5, 2.0, (K, 10)))
         s.set_state(rng.standard_normal((4, K, Np)))
-        s.set_point_source([0.5, 0.5, 0.5], f0=10.0, t0=0.05)
+        s.set_point_source([0.5, 0.5, 0.5], B.ricker_samples(1e-3, 2, f0=10.0, t0=0.05))
         s.step(1e-3, 2)
         s.sync()
         out["solo%d" % N] = s.get_state()[0]
@@ -46,7 +46,7 @@ CASES = textwrap.dedent("""
         Np = b.np_(i)
         b.set_c2(i, np.full((len(e), 10), 1.5))
         b.set_state(i, np.random.default_rng(i).standard_normal((4, len(e), Np)))
-    b.set_point_source(1, [0.4, 0.6, 0.5], f0=10.0, t0=0.05)
+    b.set_point_source(1, [0.4, 0.6, 0.5], B.ricker_samples(1e-3, 2, f0=10.0, t0=0.05))
     b.step(1e-3, 3)
     b.sync()
     for i in range(3):

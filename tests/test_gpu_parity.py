@@ -14,7 +14,7 @@ from paper_1808_08645_gb300 import binding as B
 from paper_1808_08645_gb300 import inputs
 
 from parity_util import (TOL_FINAL, TOL_STAGE, oracle_stage_on_patch, random_case,
-                         rel_l2, rounded)
+                         rel_l2, rounded, stage_times)
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -77,7 +77,7 @@ def test_stage_parity_all_degrees(N, prec):
         solver = _solver(vxyz, etov, N, M, prec, c2, q, res, t)
         solver.stage(s, dt)
         qg, rg, _ = solver.get_state(with_res=True)
-        qo, ro = orc.stage(q, res, s, dt, t)
+        qo, ro = orc.stage(q, res, s, dt)
         assert rel_l2(rg, ro) <= TOL_STAGE[prec], (s, rel_l2(rg, ro))
         assert rel_l2(qg, qo) <= TOL_STAGE[prec]
         solver.close()
@@ -91,7 +91,7 @@ def test_stage_parity_other_weight_degrees(M):
     solver = _solver(vxyz, etov, N, M, prec, c2, q, res)
     solver.stage(2, 2e-3)
     qg, rg, _ = solver.get_state(with_res=True)
-    qo, ro = orc.stage(q, res, 2, 2e-3, 0.0)
+    qo, ro = orc.stage(q, res, 2, 2e-3)
     assert rel_l2(rg, ro) <= TOL_STAGE[prec]
 
 
@@ -104,7 +104,7 @@ def test_stage_parity_penalties(tau):
     solver.set_params(*tau)
     solver.stage(1, 1e-3)
     _, rg, _ = solver.get_state(with_res=True)
-    _, ro = orc.stage(q, res, 1, 1e-3, 0.0)
+    _, ro = orc.stage(q, res, 1, 1e-3)
     assert rel_l2(rg, ro) <= TOL_STAGE[prec]
 
 
@@ -123,29 +123,65 @@ def test_stage_parity_single_element_and_unjittered_mesh():
         solver = _solver(vxyz, etov, 3, 2, 32, c2, q, res)
         solver.stage(4, 1e-3)
         _, rg, _ = solver.get_state(with_res=True)
-        _, ro = orc.stage(q, res, 4, 1e-3, 0.0)
+        _, ro = orc.stage(q, res, 4, 1e-3)
         assert rel_l2(rg, ro) <= TOL_STAGE[32]
 
 
 def test_stage_parity_point_source():
+    """A point source driven by arbitrary (random) amplitude samples, one per
+    stage, over two steps; samples past the end of the series are zero."""
     N, M, prec = 4, 2, 32
     vxyz, etov, c2, q, res = random_case(2, N, M, prec, seed=8)
     q *= 1e-3  # make the source dominate its element
     xs = np.array([0.41, 0.52, 0.37])
+    amp = np.random.default_rng(3).uniform(-2.0, 2.0, 7)  # ends inside the second step
     orc = AcousticOracle(vxyz, etov, N, M, c2)
-    e_or, _ = orc.set_point_source(xs, f0=10.0, t0=0.1)
+    e_or, _ = orc.set_point_source(xs, amp)
     solver = _solver(vxyz, etov, N, M, prec, c2, q, res, t=0.08)
-    e_gpu = solver.set_point_source(xs, f0=10.0, t0=0.1)
+    e_gpu = solver.set_point_source(xs, amp)
     assert e_gpu == e_or
-    for s in range(5):
-        solver.stage(s, 2e-3)
+    solver.step(2e-3, 3)
     qg, rg, tg = solver.get_state(with_res=True)
     qo, ro = q, res
-    for s in range(5):
-        qo, ro = orc.stage(qo, ro, s, 2e-3, 0.08)
-    assert abs(tg - 0.082) < 1e-15
+    for n in range(3):
+        qo, ro = orc.step(qo, ro, 2e-3, n)
+    assert abs(tg - 0.086) < 1e-15
     assert rel_l2(rg[:, e_or], ro[:, e_or]) <= 1e-5
-    assert rel_l2(rg, ro) <= 1e-5
+    assert rel_l2(qg, qo) <= 1e-5
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_manufactured_forcing_parity(prec):
+    """The separable forcing of the convergence study (Sec. 6.1),
+    f = (3 - 1/c^2) pi sin sin sin(x) sin(pi t), on every element through
+    bbw_set_forcing with sin(pi t) sampled at the stage times; the run
+    starting from the manufactured solution at t = 0 (p = sin sin sin,
+    u = 0) matches the oracle driven by the same samples."""
+    N, M, hexes = 3, 1, 2
+    vxyz, etov = inputs.cube_mesh(hexes, jitter=0.1, shuffle=True, seed=6)
+    K, Np = len(etov), bb.np_count(N)
+    c2 = rounded(inputs.sample_at_domain_points(vxyz, etov, M, inputs.c2_config_small), prec)
+    g = rounded(inputs.sample_at_domain_points(vxyz, etov, N,
+                                               inputs.manufactured_forcing(inputs.c2_config_small)), prec)
+    q0 = np.zeros((4, K, Np))
+    q0[0] = inputs.sample_at_domain_points(
+        vxyz, etov, N, lambda x: np.sin(np.pi * x[:, 0]) * np.sin(np.pi * x[:, 1]) * np.sin(np.pi * x[:, 2]))
+    q0 = rounded(q0, prec)
+    orc = AcousticOracle(vxyz, etov, N, M, c2)
+    dt, nsteps = orc.dt_for(0.1, 0.5)
+    amp = inputs.ricker_samples(0.0, 0.0, dt, nsteps, stage_times(), signal=lambda t: np.sin(np.pi * t))
+    elems = np.arange(K)
+    orc.set_forcing(elems, g, amp)
+    solver = _solver(vxyz, etov, N, M, prec, c2, q0, None)
+    solver.set_forcing(elems, g, amp)
+    solver.step(dt, nsteps)
+    qg, _ = solver.get_state()
+    qo, _ = orc.run(q0, dt, nsteps)
+    assert rel_l2(qg, qo) <= TOL_FINAL[prec]
+    # the forcing changes the result (the test is not vacuous)
+    orc.source = None
+    qn, _ = orc.run(q0, dt, nsteps)
+    assert rel_l2(qn, qo) > 1e-3
 
 
 # -- whole runs -------------------------------------------------------------------
@@ -177,16 +213,17 @@ def test_checkpoint_resume_is_bit_identical():
     N, M = 5, 2
     vxyz, etov, c2, q, _ = random_case(2, N, M, 32, seed=21)
     xs = np.array([0.5, 0.5, 0.5])
+    amp = B.ricker_samples(1e-3, 5, f0=10.0, t0=0.002)
     a = _solver(vxyz, etov, N, M, 32, c2, q, None)
-    a.set_point_source(xs)
+    a.set_point_source(xs, amp)
     a.step(1e-3, 5)
     qa, ra, ta = a.get_state(with_res=True)
     b = _solver(vxyz, etov, N, M, 32, c2, q, None)
-    b.set_point_source(xs)
+    b.set_point_source(xs, amp)
     b.step(1e-3, 2)
     qb, rb, tb = b.get_state(with_res=True)
     c = _solver(vxyz, etov, N, M, 32, c2, qb, rb, tb)
-    c.set_point_source(xs)
+    c.set_point_source(xs, amp[10:])  # samples count from the last set_state
     c.step(1e-3, 3)
     qc, rc, tc = c.get_state(with_res=True)
     assert np.array_equal(qa, qc) and np.array_equal(ra, rc) and ta == tc
@@ -205,7 +242,7 @@ def test_device_state_roundtrip_and_dtype_conversion():
     s.stage(0, 1e-3)
     qg, rg, _ = s.get_state(with_res=True)
     orc = AcousticOracle(vxyz, etov, N, M, c2)
-    _, ro = orc.stage(q, np.zeros_like(q), 0, 1e-3, 0.0)
+    _, ro = orc.stage(q, np.zeros_like(q), 0, 1e-3)
     assert rel_l2(rg, ro) <= TOL_STAGE[32]
 
 
@@ -246,16 +283,16 @@ def test_full_size_sweep_mesh_sampled(N):
     q = rounded(rng.standard_normal((4, K, Np)), prec)
     res = rounded(rng.standard_normal((4, K, Np)), prec)
     s = _solver(vxyz, etov, N, M, prec, c2, q, res, t=0.05)
-    src = s.set_point_source(np.array(cfg["source"]), f0=cfg["f0"])
+    amp = inputs.ricker_samples(cfg["f0"], 1.0 / cfg["f0"], 1e-4, 1, stage_times(), t_start=0.05)
+    src = s.set_point_source(np.array(cfg["source"]), amp)
     s.stage(2, 1e-4)
     qg, rg, _ = s.get_state(with_res=True)
     etoe = B.mesh_analyze(vxyz, etov, N)["etoe"]
     sample = sorted(set([0, K - 1, src] + list(rng.choice(K, 24, replace=False))))
     got, want = [], []
     for e in sample:
-        qo, ro = oracle_stage_on_patch(vxyz, etov, etoe, e, N, M, c2, q, res, 2, 1e-4, 0.05,
-                                       source=(np.array(cfg["source"]), cfg["f0"], 1.0 / cfg["f0"])
-                                       if e == src else None)
+        qo, ro = oracle_stage_on_patch(vxyz, etov, etoe, e, N, M, c2, q, res, 2, 1e-4, 0,
+                                       source=(np.array(cfg["source"]), amp) if e == src else None)
         got.append(rg[:, e])
         want.append(ro)
     assert rel_l2(np.array(got), np.array(want)) <= TOL_STAGE[prec]
@@ -278,7 +315,7 @@ def test_stage_parity_element_counts_not_multiple_of_group(N, prec):
         solver = _solver(vx, ev, N, M, prec, c2[:K], q[:, :K], res[:, :K])
         solver.stage(1, 1e-3)
         qg, rg, _ = solver.get_state(with_res=True)
-        qo, ro = orc.stage(q[:, :K], res[:, :K], 1, 1e-3, 0.0)
+        qo, ro = orc.stage(q[:, :K], res[:, :K], 1, 1e-3)
         assert rel_l2(rg, ro) <= TOL_STAGE[prec], (K, rel_l2(rg, ro))
         assert rel_l2(qg, qo) <= TOL_STAGE[prec]
         solver.close()
@@ -291,7 +328,7 @@ def test_stage_parity_extreme_shapes_fp64(N, M):
     solver = _solver(vxyz, etov, N, M, 64, c2, q, res)
     solver.stage(3, 5e-4)
     _, rg, _ = solver.get_state(with_res=True)
-    _, ro = orc.stage(q, res, 3, 5e-4, 0.0)
+    _, ro = orc.stage(q, res, 3, 5e-4)
     assert rel_l2(rg, ro) <= TOL_STAGE[64]
 
 

@@ -30,7 +30,7 @@ def _case(seed=0, source=True):
 def _oracle(vxyz, etov, c2, source, tau=1.0):
     o = AcousticOracle(vxyz, etov, N, M, c2, tau_p=tau, tau_u=tau)
     if source:
-        o.set_point_source(np.array([0.5, 0.5, 0.5]), f0=10.0, t0=0.05)
+        o.set_point_source(np.array([0.5, 0.5, 0.5]), np.random.default_rng(5).uniform(-1.0, 1.0, 40))
     return o
 
 

@@ -389,7 +389,7 @@ def test_point_source_vector_reproduces_point_values():
     N = 4
     orc = AcousticOracle(vxyz, etov, N, 0, np.ones((len(etov), 1)))
     xs = np.array([0.31, 0.62, 0.44])
-    e, vec = orc.set_point_source(xs)
+    e, vec = orc.set_point_source(xs, [1.0])
     lam_s = geometry(vxyz, etov)["grad"][e] @ (xs - vxyz[etov[e, 0]]) + np.array([1.0, 0, 0, 0])
     assert np.all(lam_s >= -1e-12)
     lam, w = tet_rule(2 * N)
