@@ -364,10 +364,13 @@ class Solver:
         return el
 
     def record(self, dt: float, nsteps: int, checkpoint_every: int = 1):
-        """Run nsteps steps keeping checkpoints; returns the traces [nsteps][nrec]."""
+        """Run nsteps steps keeping checkpoints; returns the traces [nsteps][nrec].
+        ``runs`` counts the recorded runs of this solver (bbw_adjoint
+        differentiates the latest one)."""
         tr = np.empty((nsteps, getattr(self, "nrec", 0)))
         _check(lib().bbw_record(self._h, dt, nsteps, checkpoint_every,
                                 _ptr(tr, C.c_double) if tr.size else None), "bbw_record")
+        self.runs = getattr(self, "runs", 0) + 1
         return tr
 
     def adjoint(self, trace_grad, want_q0: bool = False):

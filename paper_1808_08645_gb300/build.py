@@ -83,7 +83,7 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False, c
                     sys.stderr.write(log)
     if todo or not os.path.exists(lib) or any(os.path.getmtime(o) > os.path.getmtime(lib) for o in objs):
         tmp = lib + ".tmp"
-        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcublas"]
+        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
         p = subprocess.run(cmd, capture_output=True, text=True)
         if p.returncode != 0:
             raise RuntimeError(f"link failed:\n{p.stderr}")

@@ -9,32 +9,39 @@
 // part symmetric and linear in (tau_p, tau_u) (the energy argument of the
 // method), so K(tau)^T = -K(-tau) and
 //
-//     L(tau)^T r = -M_w L(-tau) M_w^{-1} r
-//                = -|D| M A_{-tau}( [ |D|^{-1} P~(c^2 . M^{-1} r_p) ; |D|^{-1} M^{-1} r_u ] ),
+//     L(tau)^T r = -M_w L(-tau) M_w^{-1} r = -|D| M A_{-tau}(y),
+//     y = [ |D|^{-1} P~(c^2 . M^{-1} r_p) ; |D|^{-1} M^{-1} r_u ],
 //
 // A_{-tau} being the stage kernel's spatial operator (volume terms plus lifted
-// fluxes, before the weight-adjusted update) with negated penalties. The
-// adjoint stage therefore reuses the forward spatial kernel; only the
-// element-local mass products are added here.
+// fluxes, before the weight-adjusted update) with negated penalties.
 //
 // Adjoint of one LSRK stage s (res' = a_s res + dt (L q + s), q' = q + b_s res'),
-// from the cotangents (qb, rb) of (q', res'):
-//     rt = rb + b_s qb;   qb += dt L^T rt;   rb = a_s rt
-// (rb = a_s rt is folded into the next adjoint stage's rt = a_s rt + b_{s-1} qb);
+// from the cotangents (qbar, rbar) of (q', res'):
+//     rt = rbar + b_s qbar;   qbar += dt L^T rt;   rbar = a_s rt;
 //     gc2[k][beta] += dt (M^{-1} rt_p)_k^T T_beta v_k,
 // with T_beta the mass matrix weighted by the degree-M Bernstein polynomial
-// beta and v = (A_tau q + source) the pressure bracket of the forward stage.
+// beta and v = (A_tau q + source)_p the pressure bracket of the forward stage.
 //
-// A recorded run keeps the state every C steps (checkpoints) and the start
-// time of every step; the backward pass recomputes one checkpoint segment at
-// a time, keeping the five stage inputs of each of its steps (memory: the
-// checkpoints plus 5 C states).
+// Dual variables. With kap = M^{-1} qbar and rho = M^{-1} rbar per element and
+// field (M the reference mass matrix), the recursion has no mass matrix left:
+//     rho_t = a rho + b_s kap,   y = [P~(c^2 rho_t,p) ; rho_t,u] / |D|,
+//     kap  -= dt |D| A_{-tau}(y),  gc2[k][beta] += dt rho_t,p^T T_beta v,
+// receivers inject M^{-1} B(x_r) (their dual vectors, computed once on the
+// host) and the state gradient is M kap at the end. One adjoint stage is three
+// launches of this library's kernels: the pre-kernel (rho_t and y, with the
+// weight-adjusted update of the forward kernel), the spatial kernel in its
+// accumulate mode (kap -= dt |D| A_{-tau}(y)), and the c^2 gradient kernel.
 //
-// The element-local mass products are plain dense matrix products over all
-// elements at once ([N_p x N_p] times [N_p x 4K], and the M_p weighted masses
-// as one strided batch), done by cuBLAS in the solver's precision (no
-// reduced-precision tensor-op modes).
-#include <cublas_v2.h>
+// The gradient term: rho^T T_beta v = int rho v B_beta over the reference
+// element = C_b sum_gamma w_gamma (gamma + beta)! / beta!, with
+// w_gamma = sum_{alpha + alpha' = gamma} (rho_alpha / alpha!) (v_alpha' / alpha'!)
+// the factorial-scaled Bernstein product of rho and v (degree 2N, Sec. 5.1)
+// and C_b = 6 (N!)^2 M! / (2N+M+3)! (Dirichlet moments).
+//
+// A recorded run keeps the state every C steps (checkpoints) and the step
+// counter of every step; the backward pass recomputes one checkpoint segment
+// at a time with the forward stage kernel, which stores the pressure bracket
+// of each stage (memory: the checkpoints plus 5 C pressure fields).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -53,11 +60,13 @@
 using bbw::fail;
 
 struct AdjointData {
-  // receivers: element and Bernstein basis values B_i(lambda(x_r)) [nrec][Np]
+  // receivers: element, Bernstein basis values B_i(lambda(x_r)) [nrec][Np]
+  // (sampling) and their dual vectors M^{-1} B(x_r) (adjoint injection)
   int64_t nrec = 0;
   std::vector<int64_t> rec_elem;
   int64_t* d_rec_elem = nullptr;
   void* d_rec_vec = nullptr;
+  void* d_rec_dual = nullptr;
   // recorded run
   bool recorded = false;
   double dt = 0.0;
@@ -65,31 +74,26 @@ struct AdjointData {
   std::vector<int64_t> k_step;  // the solver's step counter at the start of each step (amplitude samples)
   std::vector<void*> ckpt;      // internal-layout states at steps 0, C, 2C, ...
   double* d_traces = nullptr;   // [nsteps][nrec]
-  // operator tables (real): M^{-1}, M [Np][Np]; T [Mp][Np][Np]
-  void* d_minv = nullptr;
-  void* d_mass = nullptr;
-  void* d_tw = nullptr;
-  void* d_vol = nullptr;    // [K] element volumes
-  void* d_ivol = nullptr;   // [K] 1 / volume
-  void* d_c2u = nullptr;    // [K][Mp] c^2 (for the WADG kernel)
-  // work buffers in the ABI's field-major layout but the solver's internal
-  // element order: [4][K][Np] (qb, rb, y, z, v), [K][Np] (yt), [K][Mp] (gc)
-  void* qb = nullptr;
-  void* rb = nullptr;
-  void* y = nullptr;
-  void* z = nullptr;
-  void* v = nullptr;
-  void* yt = nullptr;
-  void* gc = nullptr;
-  // internal layout: spatial-kernel input/output, stage inputs, segment states, res
+  // gradient tables: pairs (alpha, alpha') of degree-N indices grouped by
+  // gamma = alpha + alpha' (CSR over the degree-2N lattice), 1 / alpha!, and
+  // G[gamma][beta] = C_b (gamma + beta)! / beta!
+  int32_t* d_gptr = nullptr;
+  uint32_t* d_pairs = nullptr;
+  void* d_invf = nullptr;
+  void* d_gw = nullptr;
+  int ngam = 0;
+  // adjoint state (internal layout [G][4][Np][V]): kap, rho, y; the recompute's
+  // state ping-pong and residual; the pressure brackets of every stage of a
+  // segment [5 C][G][Np][V]; the c^2 gradient [K][Mp] (internal element order)
+  void* kap = nullptr;
+  void* rho = nullptr;
   void* yi = nullptr;
-  void* zi = nullptr;
-  void* qs[5] = {};
+  void* qa[2] = {nullptr, nullptr};
   void* rs = nullptr;
-  std::vector<void*> seg;
+  void* brk = nullptr;
+  size_t brk_bytes = 0;
+  void* gc = nullptr;
   double* d_g = nullptr;  // [nsteps][nrec] trace cotangents
-  void* u = nullptr;      // [Mp][K][Np] weighted-mass products T_beta v_p
-  cublasHandle_t blas = nullptr;
 };
 
 namespace {
@@ -109,98 +113,61 @@ __global__ void sample_kernel(const real* __restrict__ q, int64_t nrec, const in
   out[r] = acc;
 }
 
-// qb_p[e_r] += g[r] B_r, receivers in order (threads over coefficients)
+// kap_p[e_r] += g[r] M^{-1} B_r, receivers in order (threads over coefficients)
 template <typename real>
-__global__ void receiver_adjoint_kernel(real* __restrict__ qb, int64_t K, int64_t nrec, const int64_t* __restrict__ el,
-                                        const real* __restrict__ vec, const double* __restrict__ g, int Np) {
+__global__ void receiver_adjoint_kernel(real* __restrict__ kap, int64_t nrec, const int64_t* __restrict__ el,
+                                        const real* __restrict__ dual, const double* __restrict__ g, int Np, int V) {
   for (int i = threadIdx.x; i < Np; i += blockDim.x)
-    for (int64_t r = 0; r < nrec; ++r) qb[el[r] * Np + i] += real(g[r]) * vec[r * Np + i];
+    for (int64_t r = 0; r < nrec; ++r) kap[iidx(el[r], i, 0, Np, V)] += real(g[r]) * dual[r * Np + i];
 }
 
-// x = a x + b y (elementwise)
+// gc[e][b] += dt sum_gamma G[gamma][b] sum_{(a, a') in pairs(gamma)} rho_p[e][a] / a! * v[e][a'] / a'!,
+// one warp per element; rho_p is field 0 of the internal [G][4][Np][V]
+// layout, v the internal pressure layout [G][Np][V].
+constexpr int kAdjWarps = 4;
+constexpr int kMaxMp = 20;
 template <typename real>
-__global__ void axpby_kernel(real* __restrict__ x, const real* __restrict__ y, real a, real b, size_t n) {
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
-    x[i] = a * x[i] + (y ? b * y[i] : real(0));
-}
-
-// user [nf][K][Np] -> internal [G][4][Np][V] (fields >= nf and padding zero),
-// times scale[e] if given
-template <typename real>
-__global__ void to_internal_scaled(const real* __restrict__ in, real* __restrict__ out, int64_t K, int Np, int V,
-                                   const real* __restrict__ scale, size_t n_internal) {
-  for (size_t x = blockIdx.x * size_t(blockDim.x) + threadIdx.x; x < n_internal; x += size_t(gridDim.x) * blockDim.x) {
-    const int v = int(x % V);
-    const size_t r = x / V;
-    const int i = int(r % Np);
-    const size_t r2 = r / Np;
-    const int f = int(r2 % 4);
-    const int64_t e = int64_t(r2 / 4) * V + v;
-    out[x] = e < K ? in[(size_t(f) * K + e) * Np + i] * (scale ? scale[e] : real(1)) : real(0);
+__global__ void __launch_bounds__(32 * kAdjWarps) adj_grad_kernel(
+    const real* __restrict__ rho, const real* __restrict__ v, real* __restrict__ gc, int64_t K, int Np, int Mp, int V,
+    int ngam, const int32_t* __restrict__ gptr, const uint32_t* __restrict__ pairs, const real* __restrict__ invf,
+    const real* __restrict__ gw, real dt) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  real* sm = reinterpret_cast<real*>(sm_raw);
+  const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+  real* rs = sm + size_t(w) * 2 * Np;
+  real* vs = rs + Np;
+  for (int64_t e = int64_t(blockIdx.x) * kAdjWarps + w; e < K; e += int64_t(gridDim.x) * kAdjWarps) {
+    const int64_t g = e / V;
+    const int l = int(e % V);
+    for (int i = lane; i < Np; i += 32) {
+      rs[i] = rho[(size_t(g) * 4 * Np + i) * V + l] * invf[i];
+      vs[i] = v[(size_t(g) * Np + i) * V + l] * invf[i];
+    }
+    __syncwarp();
+    real acc[kMaxMp];
+#pragma unroll
+    for (int b = 0; b < kMaxMp; ++b) acc[b] = real(0);
+    for (int c = lane; c < ngam; c += 32) {
+      real wg = 0;
+      for (int p = gptr[c]; p < gptr[c + 1]; ++p) {
+        const uint32_t ab = pairs[p];
+        wg += rs[ab & 0xffffu] * vs[ab >> 16];
+      }
+#pragma unroll
+      for (int b = 0; b < kMaxMp; ++b)
+        if (b < Mp) acc[b] += wg * gw[size_t(c) * Mp + b];
+    }
+#pragma unroll
+    for (int b = 0; b < kMaxMp; ++b) {
+      if (b >= Mp) break;
+      real x = acc[b];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) gc[size_t(e) * Mp + b] += dt * x;
+    }
+    __syncwarp();
   }
 }
-
-// internal -> user, fields 0..nf-1, times scale[e] if given
-template <typename real>
-__global__ void to_user_scaled(const real* __restrict__ in, real* __restrict__ out, int64_t K, int Np, int V, int nf,
-                               const real* __restrict__ scale) {
-  const size_t n = size_t(nf) * K * Np;
-  for (size_t x = blockIdx.x * size_t(blockDim.x) + threadIdx.x; x < n; x += size_t(gridDim.x) * blockDim.x) {
-    const int i = int(x % Np);
-    const size_t r = x / Np;
-    const int64_t e = int64_t(r % K);
-    const int f = int(r / K);
-    out[x] = in[iidx(e, i, f, Np, V)] * (scale ? scale[e] : real(1));
-  }
-}
-
-// gc[e][b] += alpha sum_i yt[e][i] u[b][e][i]   (u_b = T_b v_p)
-template <typename real>
-__global__ void grad_c2_kernel(const real* __restrict__ u, const real* __restrict__ yt, real* __restrict__ gc,
-                               int64_t K, int Mp, int Np, real alpha) {
-  const size_t n = size_t(K) * Mp;
-  for (size_t x = blockIdx.x * size_t(blockDim.x) + threadIdx.x; x < n; x += size_t(gridDim.x) * blockDim.x) {
-    const int b = int(x % Mp);
-    const int64_t e = int64_t(x / Mp);
-    const real* ub = u + (size_t(b) * K + e) * Np;
-    const real* ye = yt + size_t(e) * Np;
-    real acc = 0;
-    for (int i = 0; i < Np; ++i) acc += ye[i] * ub[i];
-    gc[x] += alpha * acc;
-  }
-}
-
-// Y = alpha A X + beta Y for row-major A [Np][Np] and ncols element rows of
-// Np values (X, Y: [ncols][Np], i.e. column-major Np x ncols).
-cublasStatus_t gemm(cublasHandle_t h, const float* A, int Np, const float* X, float* Y, int64_t ncols, float alpha,
-                    float beta) {
-  return cublasSgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, Np, int(ncols), Np, &alpha, A, Np, X, Np, &beta, Y, Np);
-}
-cublasStatus_t gemm(cublasHandle_t h, const double* A, int Np, const double* X, double* Y, int64_t ncols,
-                    double alpha, double beta) {
-  return cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, Np, int(ncols), Np, &alpha, A, Np, X, Np, &beta, Y, Np);
-}
-// U_b = T_b X for b < Mp (T: [Mp][Np][Np] row-major; U: [Mp][ncols][Np])
-cublasStatus_t gemm_batch(cublasHandle_t h, const float* T, int Np, const float* X, float* U, int64_t ncols, int Mp) {
-  const float one = 1.f, zero = 0.f;
-  return cublasSgemmStridedBatched(h, CUBLAS_OP_T, CUBLAS_OP_N, Np, int(ncols), Np, &one, T, Np,
-                                   static_cast<long long>(Np) * Np, X, Np, 0, &zero, U, Np, static_cast<long long>(Np) * ncols, Mp);
-}
-cublasStatus_t gemm_batch(cublasHandle_t h, const double* T, int Np, const double* X, double* U, int64_t ncols,
-                          int Mp) {
-  const double one = 1.0, zero = 0.0;
-  return cublasDgemmStridedBatched(h, CUBLAS_OP_T, CUBLAS_OP_N, Np, int(ncols), Np, &one, T, Np,
-                                   static_cast<long long>(Np) * Np, X, Np, 0, &zero, U, Np, static_cast<long long>(Np) * ncols, Mp);
-}
-
-#define BBW_BLAS(call)                                                                        \
-  do {                                                                                        \
-    const cublasStatus_t b_ = (call);                                                         \
-    if (b_ != CUBLAS_STATUS_SUCCESS)                                                          \
-      return fail(BBW_ERR_CUDA, std::string(#call) + ": cuBLAS status " + std::to_string(int(b_))); \
-  } while (0)
-
-int blocks_for(size_t n) { return int(std::min<size_t>((n + 255) / 256, 152 * 32)); }
 
 bbw_status dalloc(void** p, size_t bytes) {
   if (*p) return BBW_OK;
@@ -218,48 +185,53 @@ bbw_status upload_real(const std::vector<double>& h, void** d) {
   return BBW_OK;
 }
 
-// mass, inverse mass and weighted masses of the reference element (volume 1)
+// The gradient tables of the degree-2N product (see the file comment).
 template <typename real>
 bbw_status build_tables(bbw_solver* s, AdjointData* a) {
-  if (a->d_minv) return BBW_OK;
+  if (a->d_gptr) return BBW_OK;
   const int N = s->N, M = s->M, Np = s->Np, Mp = s->Mp;
   const auto A = bbw::lattice(N);
   const auto B = bbw::lattice(M);
-  auto mult = [&](int n, const std::array<int, 4>& x) {
-    return bbw::factorial(n) / (bbw::factorial(x[0]) * bbw::factorial(x[1]) * bbw::factorial(x[2]) *
-                                bbw::factorial(x[3]));
+  const auto G2 = bbw::lattice(2 * N);
+  auto f = [](int n) { return bbw::factorial(n); };
+  auto idx2n = [&](const std::array<int, 4>& g) {  // position of gamma in the degree-2N library order
+    return bbw::idx3(2 * N, g[1], g[2], g[3]);
   };
-  std::vector<double> mass(size_t(Np) * Np), minv(size_t(Np) * Np), tw(size_t(Mp) * Np * Np);
-  // Dirichlet integral over the unit-volume reference element:
-  // int lambda^g = 3! g! / (|g| + 3)!
+  const int ngam = int(G2.size());
+  std::vector<std::vector<uint32_t>> by(static_cast<size_t>(ngam));
   for (int i = 0; i < Np; ++i)
     for (int j = 0; j < Np; ++j) {
-      double m = 6.0 / bbw::factorial(2 * N + 3);
-      for (int x = 0; x < 4; ++x) m *= bbw::factorial(A[i][x] + A[j][x]);
-      mass[size_t(i) * Np + j] = mult(N, A[i]) * mult(N, A[j]) * m;
-      for (int b = 0; b < Mp; ++b) {
-        double w = 6.0 / bbw::factorial(2 * N + M + 3);
-        for (int x = 0; x < 4; ++x) w *= bbw::factorial(A[i][x] + A[j][x] + B[b][x]);
-        tw[(size_t(b) * Np + i) * Np + j] = mult(M, B[b]) * mult(N, A[i]) * mult(N, A[j]) * w;
-      }
+      std::array<int, 4> g;
+      for (int x = 0; x < 4; ++x) g[x] = A[size_t(i)][x] + A[size_t(j)][x];
+      by[size_t(idx2n(g))].push_back(uint32_t(i) | (uint32_t(j) << 16));
     }
-  for (int j = 0; j < Np; ++j) {
-    std::vector<double> col(size_t(Np), 0.0);
-    col[size_t(j)] = 1.0;
-    if (!bbw::solve_mass(N, col)) return fail(BBW_ERR_ARG, "mass matrix factorisation failed");
-    for (int i = 0; i < Np; ++i) minv[size_t(i) * Np + j] = col[size_t(i)];
+  std::vector<int32_t> gptr(size_t(ngam) + 1, 0);
+  std::vector<uint32_t> pairs;
+  for (int c = 0; c < ngam; ++c) {
+    gptr[size_t(c)] = int32_t(pairs.size());
+    pairs.insert(pairs.end(), by[size_t(c)].begin(), by[size_t(c)].end());
   }
-  // element arrays in the solver's internal element order
-  std::vector<double> vol(s->vol.size()), ivol(s->vol.size());
-  for (size_t e = 0; e < vol.size(); ++e) {
-    vol[e] = s->vol[size_t(s->user(int64_t(e)))];
-    ivol[e] = 1.0 / vol[e];
+  gptr[size_t(ngam)] = int32_t(pairs.size());
+  const double cb = 6.0 * f(N) * f(N) * f(M) / f(2 * N + M + 3);
+  std::vector<double> gw(size_t(ngam) * Mp);
+  std::vector<double> invf(static_cast<size_t>(Np));
+  for (int c = 0; c < ngam; ++c)
+    for (int b = 0; b < Mp; ++b) {
+      double x = cb;
+      for (int q = 0; q < 4; ++q) x *= f(G2[size_t(c)][q] + B[size_t(b)][q]) / f(B[size_t(b)][q]);
+      gw[size_t(c) * Mp + b] = x;
+    }
+  for (int i = 0; i < Np; ++i) {
+    const auto& ai = A[size_t(i)];
+    invf[size_t(i)] = 1.0 / (f(ai[0]) * f(ai[1]) * f(ai[2]) * f(ai[3]));
   }
-  bbw_status st = upload_real<real>(mass, &a->d_mass);
-  if (st == BBW_OK) st = upload_real<real>(minv, &a->d_minv);
-  if (st == BBW_OK) st = upload_real<real>(tw, &a->d_tw);
-  if (st == BBW_OK) st = upload_real<real>(vol, &a->d_vol);
-  if (st == BBW_OK) st = upload_real<real>(ivol, &a->d_ivol);
+  BBW_CUDA(cudaMalloc(reinterpret_cast<void**>(&a->d_gptr), gptr.size() * sizeof(int32_t)));
+  BBW_CUDA(cudaMemcpy(a->d_gptr, gptr.data(), gptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  BBW_CUDA(cudaMalloc(reinterpret_cast<void**>(&a->d_pairs), pairs.size() * sizeof(uint32_t)));
+  BBW_CUDA(cudaMemcpy(a->d_pairs, pairs.data(), pairs.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+  a->ngam = ngam;
+  bbw_status st = upload_real<real>(gw, &a->d_gw);
+  if (st == BBW_OK) st = upload_real<real>(invf, &a->d_invf);
   return st;
 }
 
@@ -275,21 +247,18 @@ void free_run(AdjointData* a, bool release = false) {
     for (void* p : a->ckpt)
       if (p) cudaFree(p);
     a->ckpt.clear();
-    for (void* p : a->seg)
-      if (p) cudaFree(p);
-    a->seg.clear();
+    if (a->brk) cudaFree(a->brk);
+    a->brk = nullptr;
+    a->brk_bytes = 0;
   }
   if (a->d_traces) cudaFree(a->d_traces);
   a->d_traces = nullptr;
   a->recorded = false;
 }
 
-// One forward stage on explicit buffers: qin -> qout, res updated, time t.
+// The solver's launch parameters for a stage on explicit buffers.
 template <typename real>
-bbw_status forward_stage(bbw_solver* s, const void* qin, void* qout, void* res, int stage, double dt,
-                         int64_t step) {
-  double ca[5], cb[5];
-  bbw_lsrk_coeffs(ca, cb, nullptr);
+bbw::StageParams<real> stage_params(bbw_solver* s, const void* qin, void* qout, void* res) {
   bbw::StageParams<real> P;
   P.qin = static_cast<const real*>(qin);
   P.qout = static_cast<real*>(qout);
@@ -299,106 +268,67 @@ bbw_status forward_stage(bbw_solver* s, const void* qin, void* qout, void* res, 
   P.conn = s->d_conn;
   P.tables = s->op->tables;
   P.G = s->G;
+  P.a = real(0);
+  P.b = real(0);
+  P.dt = real(0);
+  P.tau_p = real(s->tau_p);
+  P.tau_u = real(s->tau_u);
+  P.status = s->d_status;
+  return P;
+}
+
+// One forward stage qin -> qout (res updated) of step `step`, storing its
+// pressure bracket in vout.
+template <typename real>
+bbw_status forward_stage(bbw_solver* s, const void* qin, void* qout, void* res, int stage, double dt, int64_t step,
+                         void* vout) {
+  double ca[5], cb[5];
+  bbw_lsrk_coeffs(ca, cb, nullptr);
+  bbw::StageParams<real> P = stage_params<real>(s, qin, qout, res);
   P.a = real(ca[stage]);
   P.b = real(cb[stage]);
   P.dt = real(dt);
-  P.tau_p = real(s->tau_p);
-  P.tau_u = real(s->tau_u);
   bbw::set_stage_sources<bbw::StageParams<real>, real>(s, P, step, stage, true);
-  P.status = s->d_status;
+  P.vout = static_cast<real*>(vout);
   BBW_CUDA(s->ops->launch_stage(s->M, s->prec == 64, &P, s->grid_stage, s->stream));
   return BBW_OK;
 }
 
-// Spatial operator alone: out = [bracket_p (+ sources at t + c_s dt), rhs_u]
-// of qin (internal layout), penalties sgn * tau.
+// Adjoint of stage `stage` whose forward pressure bracket is vbr.
 template <typename real>
-bbw_status spatial(bbw_solver* s, const void* qin, void* out, double sgn, bool sources, int stage, int64_t step) {
-  bbw::StageParams<real> P;
-  P.qin = static_cast<const real*>(qin);
-  P.qout = static_cast<real*>(out);
-  P.res = static_cast<real*>(out);
-  P.c2 = static_cast<const real*>(s->d_c2);
-  P.geom = static_cast<const real*>(s->d_geom);
-  P.conn = s->d_conn;
-  P.tables = s->op->tables;
-  P.G = s->G;
-  P.a = real(0);
-  P.b = real(0);
-  P.dt = real(0);
-  P.tau_p = real(sgn * s->tau_p);
-  P.tau_u = real(sgn * s->tau_u);
-  bbw::set_stage_sources<bbw::StageParams<real>, real>(s, P, step, stage, sources);
-  P.status = s->d_status;
-  BBW_CUDA(s->ops->launch_spatial(s->M, s->prec == 64, &P, s->grid_stage, s->stream));
-  return BBW_OK;
-}
-
-template <typename real>
-bbw_status wadg_user(bbw_solver* s, const void* in, const void* c2u, void* out) {
-  bbw::WadgParams<real> P;
-  P.rhs = static_cast<const real*>(in);
-  P.c2 = static_cast<const real*>(c2u);
-  P.out = static_cast<real*>(out);
-  P.tables = s->op->tables;
-  P.K = s->K;
-  int team = 0, V = 1, gpc = 1;
-  s->ops->launch_shape(s->M, s->prec == 64, &team, &V, &gpc);
-  const int64_t tiles = (s->K + int64_t(V) * gpc - 1) / (int64_t(V) * gpc);
-  int dev = 0, nsm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = int(std::min<int64_t>(tiles, int64_t(std::max(1, s->op->per_sm_wadg)) * std::max(1, nsm)));
-  BBW_CUDA(s->ops->launch_wadg(s->M, s->prec == 64, &P, std::max(1, grid), s->stream));
-  return BBW_OK;
-}
-
-// Adjoint of stage `stage` of the step starting at time t, whose stage input
-// (internal layout) is qin; updates qb, rb (user layout) and gc.
-template <typename real>
-bbw_status adjoint_stage(bbw_solver* s, AdjointData* a, const void* qin, int stage, double dt, int64_t step) {
-  double ca[5], cb[5], cc[5];
-  bbw_lsrk_coeffs(ca, cb, cc);
-  const int64_t K = s->K;
-  const int Np = s->Np, Mp = s->Mp, V = s->V;
-  const size_t nf = size_t(K) * Np;
-  const int p = s->prec;
-  real* qb = static_cast<real*>(a->qb);
-  real* rb = static_cast<real*>(a->rb);
-  real* y = static_cast<real*>(a->y);
-  real* z = static_cast<real*>(a->z);
-  real* v = static_cast<real*>(a->v);
-  real* yt = static_cast<real*>(a->yt);
-  const real* minv = static_cast<const real*>(a->d_minv);
-  const real* mass = static_cast<const real*>(a->d_mass);
-  const real* vol = static_cast<const real*>(a->d_vol);
-  const real* ivol = static_cast<const real*>(a->d_ivol);
+bbw_status adjoint_stage(bbw_solver* s, AdjointData* a, const void* vbr, int stage, double dt) {
+  double ca[5], cb[5];
+  bbw_lsrk_coeffs(ca, cb, nullptr);
   cudaStream_t st = s->stream;
-  // rt = a_{s+1} rt + b_s qb in rb (rb holds rt of the stage after; at the
-  // last stage of a step the incoming res cotangent is zero, a_0 = 0)
-  const real a_next = stage == 4 ? real(0) : real(ca[stage + 1]);
-  axpby_kernel<real><<<blocks_for(4 * nf), 256, 0, st>>>(rb, qb, a_next, real(cb[stage]), 4 * nf);
-  // yt = M^{-1} rt_p; y = [P~(c2 . yt); M^{-1} rt_u], scaled by 1/|D| into the grouped layout
-  BBW_BLAS(gemm(a->blas, minv, Np, rb, yt, K, real(1), real(0)));
-  bbw_status r = wadg_user<real>(s, yt, a->d_c2u, y);
-  if (r != BBW_OK) return r;
-  BBW_BLAS(gemm(a->blas, minv, Np, rb + nf, y + nf, 3 * K, real(1), real(0)));
-  const size_t ni = s->nstate_internal();
-  to_internal_scaled<real><<<blocks_for(ni), 256, 0, st>>>(y, static_cast<real*>(a->yi), K, Np, V, ivol, ni);
-  BBW_CUDA(cudaGetLastError());
-  // z = |D| A_{-tau}(y); v_p = (A_tau(q_s) + sources)_p
-  r = spatial<real>(s, a->yi, a->zi, -1.0, false, stage, step);
-  if (r != BBW_OK) return r;
-  to_user_scaled<real><<<blocks_for(4 * nf), 256, 0, st>>>(static_cast<const real*>(a->zi), z, K, Np, V, 4, vol);
-  r = spatial<real>(s, qin, a->zi, 1.0, true, stage, step);
-  if (r != BBW_OK) return r;
-  to_user_scaled<real><<<blocks_for(nf), 256, 0, st>>>(static_cast<const real*>(a->zi), v, K, Np, V, 1, nullptr);
-  BBW_CUDA(cudaGetLastError());
-  // qb -= dt M z; gc += dt yt^T T_b v_p
-  BBW_BLAS(gemm(a->blas, mass, Np, z, qb, 4 * K, real(-dt), real(1)));
-  BBW_BLAS(gemm_batch(a->blas, static_cast<const real*>(a->d_tw), Np, v, static_cast<real*>(a->u), K, Mp));
-  grad_c2_kernel<real><<<blocks_for(size_t(K) * Mp), 256, 0, st>>>(static_cast<const real*>(a->u), yt,
-                                                                     static_cast<real*>(a->gc), K, Mp, Np, real(dt));
+  // rho_t = a_{s+1} rho + b_s kap (rho holds rho_t of the stage after; at the
+  // last stage of a step the incoming res cotangent is zero, a_0 = 0); y
+  bbw::AdjPreParams<real> Q;
+  Q.rho = static_cast<real*>(a->rho);
+  Q.kap = static_cast<const real*>(a->kap);
+  Q.c2 = static_cast<const real*>(s->d_c2);
+  Q.geom = static_cast<const real*>(s->d_geom);
+  Q.y = static_cast<real*>(a->yi);
+  Q.tables = s->op->tables;
+  Q.G = s->G;
+  Q.a = stage == 4 ? real(0) : real(ca[stage + 1]);
+  Q.b = real(cb[stage]);
+  BBW_CUDA(s->ops->launch_adj_pre(s->M, s->prec == 64, &Q, s->grid_stage, st));
+  // kap -= dt |D| A_{-tau}(y)
+  bbw::StageParams<real> P = stage_params<real>(s, a->yi, a->kap, a->kap);
+  P.tau_p = real(-s->tau_p);
+  P.tau_u = real(-s->tau_u);
+  P.dt = real(dt);
+  P.accumulate = 1;
+  bbw::set_stage_sources<bbw::StageParams<real>, real>(s, P, 0, stage, false);
+  BBW_CUDA(s->ops->launch_spatial(s->M, s->prec == 64, &P, s->grid_stage, st));
+  // gc += dt rho_t,p^T T_beta v
+  const int threads = 32 * kAdjWarps;
+  const size_t shm = size_t(kAdjWarps) * 2 * s->Np * sizeof(real);
+  const int blocks = int(std::min<int64_t>((s->K + kAdjWarps - 1) / kAdjWarps, 152 * 16));
+  adj_grad_kernel<real><<<blocks, threads, shm, st>>>(
+      static_cast<const real*>(a->rho), static_cast<const real*>(vbr), static_cast<real*>(a->gc), s->K, s->Np, s->Mp,
+      s->V, a->ngam, a->d_gptr, a->d_pairs, static_cast<const real*>(a->d_invf), static_cast<const real*>(a->d_gw),
+      real(dt));
   BBW_CUDA(cudaGetLastError());
   return BBW_OK;
 }
@@ -452,40 +382,21 @@ bbw_status adjoint(bbw_solver* s, const double* g, double* grad_c2, double* grad
   if (st != BBW_OK) return st;
   const int64_t K = s->K;
   const int Np = s->Np, Mp = s->Mp;
-  const size_t nf = size_t(K) * Np, ns = 4 * nf * sizeof(real), bytes = s->nstate_internal() * sizeof(real);
-  for (void** b : {&a->qb, &a->rb, &a->y, &a->z, &a->v}) {
-    st = dalloc(b, ns);
-    if (st != BBW_OK) return st;
-  }
-  for (void** b : {&a->yi, &a->zi, &a->rs}) {
+  const size_t bytes = s->nstate_internal() * sizeof(real);
+  const size_t pbytes = size_t(s->G) * s->V * Np * sizeof(real);  // one pressure field, internal layout
+  for (void** b : {&a->kap, &a->rho, &a->yi, &a->qa[0], &a->qa[1], &a->rs}) {
     st = dalloc(b, bytes);
     if (st != BBW_OK) return st;
   }
-  st = dalloc(&a->yt, nf * sizeof(real));
-  if (st == BBW_OK) st = dalloc(&a->gc, size_t(K) * Mp * sizeof(real));
-  if (st == BBW_OK) st = dalloc(&a->u, size_t(Mp) * nf * sizeof(real));
+  st = dalloc(&a->gc, size_t(K) * Mp * sizeof(real));
   if (st != BBW_OK) return st;
-  if (!a->blas) {
-    BBW_BLAS(cublasCreate(&a->blas));
-    BBW_BLAS(cublasSetMathMode(a->blas, CUBLAS_PEDANTIC_MATH));
-  }
-  BBW_BLAS(cublasSetStream(a->blas, s->stream));
-  if (st != BBW_OK) return st;
-  {  // the current c^2 of the solver, [K][Mp] in the internal element order
-    std::vector<double> c2u(s->c2.size());
-    for (int64_t e = 0; e < K; ++e)
-      for (int b = 0; b < Mp; ++b) c2u[size_t(e) * Mp + b] = s->c2[size_t(s->user(e)) * Mp + b];
-    st = upload_real<real>(c2u, &a->d_c2u);
-    if (st != BBW_OK) return st;
-  }
-  while (a->seg.size() > size_t(a->every) * 5) {  // the five stage inputs of each step of a segment
-    if (a->seg.back()) cudaFree(a->seg.back());
-    a->seg.pop_back();
-  }
-  a->seg.resize(size_t(a->every) * 5, nullptr);
-  for (auto& b : a->seg) {
-    st = dalloc(&b, bytes);
-    if (st != BBW_OK) return st;
+  const size_t need = size_t(a->every) * 5 * pbytes;
+  if (a->brk_bytes < need) {
+    if (a->brk) cudaFree(a->brk);
+    a->brk = nullptr;
+    a->brk_bytes = 0;
+    BBW_CUDA(cudaMalloc(&a->brk, need));
+    a->brk_bytes = need;
   }
   if (a->d_g) cudaFree(a->d_g);
   a->d_g = nullptr;
@@ -495,35 +406,34 @@ bbw_status adjoint(bbw_solver* s, const double* g, double* grad_c2, double* grad
     BBW_CUDA(cudaMemcpy(a->d_g, g, ng * sizeof(double), cudaMemcpyHostToDevice));
   }
   cudaStream_t sm = s->stream;
-  BBW_CUDA(cudaMemsetAsync(a->qb, 0, ns, sm));
-  BBW_CUDA(cudaMemsetAsync(a->rb, 0, ns, sm));
+  BBW_CUDA(cudaMemsetAsync(a->kap, 0, bytes, sm));
+  BBW_CUDA(cudaMemsetAsync(a->rho, 0, bytes, sm));
   BBW_CUDA(cudaMemsetAsync(a->gc, 0, size_t(K) * Mp * sizeof(real), sm));
+  auto bracket = [&](int64_t i) { return static_cast<void*>(static_cast<char*>(a->brk) + size_t(i) * pbytes); };
   const double dt = a->dt;
   const int64_t nseg = int64_t(a->ckpt.size());
   for (int64_t k = nseg - 1; k >= 0; --k) {
     const int64_t n0 = k * a->every, n1 = std::min(a->nsteps, n0 + a->every);
-    // the stage inputs of every step of the segment, from its checkpoint
-    BBW_CUDA(cudaMemcpyAsync(a->seg[0], a->ckpt[size_t(k)], bytes, cudaMemcpyDeviceToDevice, sm));
-    for (int64_t n = n0; n < n1; ++n) {
-      const size_t b5 = size_t(n - n0) * 5;
+    // recompute the segment from its checkpoint, keeping every stage's bracket
+    BBW_CUDA(cudaMemcpyAsync(a->qa[0], a->ckpt[size_t(k)], bytes, cudaMemcpyDeviceToDevice, sm));
+    int cur = 0;
+    for (int64_t n = n0; n < n1; ++n)
       for (int sg = 0; sg < 5; ++sg) {
-        if (sg == 4 && n + 1 == n1) break;  // the segment's final state is not needed
-        void* out = sg < 4 ? a->seg[b5 + sg + 1] : a->seg[b5 + 5];
-        st = forward_stage<real>(s, a->seg[b5 + sg], out, a->rs, sg, dt, a->k_step[size_t(n)]);
+        st = forward_stage<real>(s, a->qa[cur], a->qa[1 - cur], a->rs, sg, dt, a->k_step[size_t(n)],
+                                 bracket((n - n0) * 5 + sg));
         if (st != BBW_OK) return st;
+        cur = 1 - cur;
       }
-    }
     for (int64_t n = n1 - 1; n >= n0; --n) {
       // cotangent of the traces after step n
       if (a->d_g) {
-        receiver_adjoint_kernel<real><<<1, 256, 0, sm>>>(static_cast<real*>(a->qb), K, a->nrec, a->d_rec_elem,
-                                                         static_cast<const real*>(a->d_rec_vec),
-                                                         a->d_g + size_t(n) * a->nrec, Np);
+        receiver_adjoint_kernel<real><<<1, 256, 0, sm>>>(static_cast<real*>(a->kap), a->nrec, a->d_rec_elem,
+                                                         static_cast<const real*>(a->d_rec_dual),
+                                                         a->d_g + size_t(n) * a->nrec, Np, s->V);
         BBW_CUDA(cudaGetLastError());
       }
-      const size_t b5 = size_t(n - n0) * 5;
       for (int sg = 4; sg >= 0; --sg) {
-        st = adjoint_stage<real>(s, a, a->seg[b5 + sg], sg, dt, a->k_step[size_t(n)]);
+        st = adjoint_stage<real>(s, a, bracket((n - n0) * 5 + sg), sg, dt);
         if (st != BBW_OK) return st;
       }
       // the step's res enters only through stage 0 (a_0 = 0): the res
@@ -541,12 +451,35 @@ bbw_status adjoint(bbw_solver* s, const double* g, double* grad_c2, double* grad
       for (int b = 0; b < Mp; ++b) grad_c2[size_t(s->user(e)) * Mp + b] = double(h[size_t(e) * Mp + b]);
   }
   if (grad_q0) {
-    std::vector<real> h(4 * nf);
-    BBW_CUDA(cudaMemcpy(h.data(), a->qb, h.size() * sizeof(real), cudaMemcpyDeviceToHost));
-    for (int f = 0; f < 4; ++f)
-      for (int64_t e = 0; e < K; ++e)
-        for (int i = 0; i < Np; ++i)
-          grad_q0[(size_t(f) * K + size_t(s->user(e))) * Np + i] = double(h[(size_t(f) * K + e) * Np + i]);
+    // qbar = M kap per element and field (the reference mass, in FP64 on the host)
+    const size_t nf = size_t(K) * Np;
+    std::vector<double> kh(4 * nf);
+    void* tmp = nullptr;
+    BBW_CUDA(cudaMalloc(&tmp, 4 * nf * sizeof(double)));
+    cudaError_t e1 = bbw::copy_to_user(a->kap, s->prec, tmp, 64, K, Np, s->V, s->d_inv, sm);
+    if (e1 == cudaSuccess) e1 = cudaMemcpyAsync(kh.data(), tmp, 4 * nf * sizeof(double), cudaMemcpyDeviceToHost, sm);
+    if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(sm);
+    cudaFree(tmp);
+    if (e1 != cudaSuccess) return fail(BBW_ERR_CUDA, std::string("state gradient download: ") + cudaGetErrorString(e1));
+    const auto A = bbw::lattice(s->N);
+    auto f = [](int n) { return bbw::factorial(n); };
+    std::vector<double> mass(size_t(Np) * Np);
+    for (int i = 0; i < Np; ++i)
+      for (int j = 0; j < Np; ++j) {
+        double m = 6.0 / f(2 * s->N + 3) * f(s->N) * f(s->N);
+        for (int x = 0; x < 4; ++x)
+          m *= f(A[size_t(i)][x] + A[size_t(j)][x]) / (f(A[size_t(i)][x]) * f(A[size_t(j)][x]));
+        mass[size_t(i) * Np + j] = m;
+      }
+    for (size_t r = 0; r < 4 * size_t(K); ++r) {
+      const double* x = kh.data() + r * Np;
+      double* y = grad_q0 + r * Np;
+      for (int i = 0; i < Np; ++i) {
+        double acc = 0.0;
+        for (int j = 0; j < Np; ++j) acc += mass[size_t(i) * Np + j] * x[j];
+        y[i] = acc;
+      }
+    }
   }
   return BBW_OK;
 }
@@ -559,11 +492,10 @@ void free_adjoint(bbw_solver* s) {
   AdjointData* a = s->adj;
   if (!a) return;
   free_run(a, true);
-  for (void* p : {static_cast<void*>(a->d_rec_elem), a->d_rec_vec, a->d_minv, a->d_mass, a->d_tw, a->d_vol, a->d_ivol,
-                  a->d_c2u, a->qb, a->rb, a->y, a->z, a->v, a->yt, a->gc, a->yi, a->zi, a->rs, a->qs[0], a->qs[1],
-                  a->qs[2], a->qs[3], a->qs[4], static_cast<void*>(a->d_g), a->u})
+  for (void* p : {static_cast<void*>(a->d_rec_elem), a->d_rec_vec, a->d_rec_dual, static_cast<void*>(a->d_gptr),
+                  static_cast<void*>(a->d_pairs), a->d_invf, a->d_gw, a->kap, a->rho, a->yi, a->qa[0], a->qa[1],
+                  a->rs, a->gc, static_cast<void*>(a->d_g)})
     if (p) cudaFree(p);
-  if (a->blas) cublasDestroy(a->blas);
   delete a;
   s->adj = nullptr;
 }
@@ -577,7 +509,7 @@ bbw_status bbw_set_receivers(bbw_solver* s, int64_t nrec, const double* xyz, int
   if (nrec < 0 || (nrec > 0 && !xyz)) return fail(BBW_ERR_ARG, "bad receiver list");
   AdjointData* a = adj_of(s);
   std::vector<int64_t> el(static_cast<size_t>(nrec), 0);
-  std::vector<double> vec(static_cast<size_t>(nrec) * s->Np, 0.0);
+  std::vector<double> vec(static_cast<size_t>(nrec) * s->Np, 0.0), dual(vec.size(), 0.0);
   const auto A = bbw::lattice(s->N);
   for (int64_t r = 0; r < nrec; ++r) {
     // locate (lowest element index on shared faces) and evaluate the basis
@@ -601,17 +533,21 @@ bbw_status bbw_set_receivers(bbw_solver* s, int64_t nrec, const double* xyz, int
     }
     if (found < 0) return fail(BBW_ERR_ARG, "receiver " + std::to_string(r) + " lies outside the mesh");
     el[size_t(r)] = found;
+    std::vector<double> b(size_t(s->Np));
     for (size_t i = 0; i < A.size(); ++i) {
-      double b = bbw::factorial(s->N) /
+      double v = bbw::factorial(s->N) /
                  (bbw::factorial(A[i][0]) * bbw::factorial(A[i][1]) * bbw::factorial(A[i][2]) * bbw::factorial(A[i][3]));
-      for (int m = 0; m < 4; ++m) b *= std::pow(std::max(lam[m], 0.0), A[i][m]);
-      vec[size_t(r) * s->Np + i] = b;
+      for (int m = 0; m < 4; ++m) v *= std::pow(std::max(lam[m], 0.0), A[i][m]);
+      vec[size_t(r) * s->Np + i] = v;
+      b[i] = v;
     }
+    if (!bbw::solve_mass(s->N, b)) return fail(BBW_ERR_ARG, "mass matrix factorisation failed");
+    std::copy(b.begin(), b.end(), dual.begin() + ptrdiff_t(size_t(r) * s->Np));
   }
-  if (a->d_rec_elem) cudaFree(a->d_rec_elem);
-  if (a->d_rec_vec) cudaFree(a->d_rec_vec);
-  a->d_rec_elem = nullptr;
-  a->d_rec_vec = nullptr;
+  for (void** p : {reinterpret_cast<void**>(&a->d_rec_elem), &a->d_rec_vec, &a->d_rec_dual}) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+  }
   a->nrec = nrec;
   a->rec_elem = el;
   free_run(a);
@@ -621,6 +557,8 @@ bbw_status bbw_set_receivers(bbw_solver* s, int64_t nrec, const double* xyz, int
     for (size_t r = 0; r < el.size(); ++r) slots[r] = s->slot(el[r]);  // internal element order
     BBW_CUDA(cudaMemcpy(a->d_rec_elem, slots.data(), size_t(nrec) * sizeof(int64_t), cudaMemcpyHostToDevice));
     bbw_status st = s->prec == 64 ? upload_real<double>(vec, &a->d_rec_vec) : upload_real<float>(vec, &a->d_rec_vec);
+    if (st == BBW_OK)
+      st = s->prec == 64 ? upload_real<double>(dual, &a->d_rec_dual) : upload_real<float>(dual, &a->d_rec_dual);
     if (st != BBW_OK) return st;
   }
   if (elems) std::copy(el.begin(), el.end(), elems);

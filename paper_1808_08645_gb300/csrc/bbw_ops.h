@@ -29,6 +29,8 @@ struct KernelOps {
   cudaError_t (*launch_spatial)(int M, bool dbl, const void* params, int grid, cudaStream_t s);
   // host-only: build the tables and check them against brute force (nullptr: all agree)
   const char* (*check_tables)(int M, bool dbl, const double* cj);
+  // launch the adjoint stage's pre-kernel; params points to AdjPreParams<float|double>
+  cudaError_t (*launch_adj_pre)(int M, bool dbl, const void* params, int grid, cudaStream_t s);
 };
 
 const KernelOps& ops_n1();

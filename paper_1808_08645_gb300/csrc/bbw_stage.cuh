@@ -77,6 +77,30 @@ struct StageParams {
   int64_t step_host;
   int stage;
   unsigned int* status;           // bit 0: non-finite output
+  // LSRK stage: if set, the pressure bracket of the stage (volume term,
+  // lifted fluxes and sources, before the weight-adjusted update) is also
+  // stored here, [G][Np][V] (the adjoint's recomputed forward run keeps it).
+  real* __restrict__ vout = nullptr;
+  // spatial-only kernel: 0 writes the right-hand side to qout; 1 accumulates
+  // qout -= dt |D| rhs into all four fields (|D| the element volume).
+  int accumulate = 0;
+};
+
+// One stage of the discrete adjoint before its spatial operator, in the
+// dual variables kap = M^{-1} qbar, rho = M^{-1} rbar of the state and
+// residual cotangents (M the reference mass matrix, per element and field):
+//   rho_t = a rho + b kap                       (stored back to rho)
+//   y     = [P~(c2 rho_t,p) ; rho_t,u] / |D|    (the weight-adjusted update of Eq. 4)
+template <typename real>
+struct AdjPreParams {
+  real* __restrict__ rho;         // [G][4][Np][V]
+  const real* __restrict__ kap;   // [G][4][Np][V]
+  const real* __restrict__ c2;    // [G][Mp][V]
+  const real* __restrict__ geom;  // [G][9][V]
+  real* __restrict__ y;           // [G][4][Np][V]
+  const void* __restrict__ tables;
+  int64_t G;
+  real a, b;
 };
 
 template <typename real>
@@ -609,6 +633,21 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
         nr[3 * V] = real(1.5) * gn;
       }
     }
+    // accumulate mode of the spatial kernel: dt |D| per element lane, with
+    // |D| = 1 / (6 det[grad lambda_1; grad lambda_2; grad lambda_3])
+    vt dtvol = vzero<real, V>();
+    if constexpr (SP) {
+      if (P.accumulate) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const real a1 = gm[1][0].get(v), a2 = gm[1][1].get(v), a3 = gm[1][2].get(v);
+          const real b1 = gm[2][0].get(v), b2 = gm[2][1].get(v), b3 = gm[2][2].get(v);
+          const real c1 = gm[3][0].get(v), c2v = gm[3][1].get(v), c3 = gm[3][2].get(v);
+          const real det = a1 * (b2 * c3 - b3 * c2v) - a2 * (b1 * c3 - b3 * c1) + a3 * (b1 * c2v - b2 * c1);
+          dtvol.set(v, P.dt / (real(6) * det));
+        }
+      }
+    }
     cp_async_wait_all();
     team_sync<T>();
 
@@ -838,7 +877,14 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             if constexpr (SP) {
-              vst(qog + size_t((1 + c) * Np + i) * V, rhs[c]);
+              real* o = qog + size_t((1 + c) * Np + i) * V;
+              if (P.accumulate) {
+                vt acc = vld<real, V>(o);
+                vfma(acc, vmuls(real(-1), dtvol), rhs[c]);
+                vst(o, acc);
+              } else {
+                vst(o, rhs[c]);
+              }
             } else {
               vt rn = vmuls(P.dt, rhs[c]);
               vfmas(rn, P.a, rold[r][c]);
@@ -871,7 +917,13 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
               if (sd >= 0) v.set(l, v.get(l) + AMP[l] * P.src_vec[size_t(sd) * Np + i]);
             }
           }
-          vst(qog + size_t(i) * V, v);
+          if (P.accumulate) {
+            vt acc = vld<real, V>(qog + size_t(i) * V);
+            vfma(acc, vmuls(real(-1), dtvol), v);
+            vst(qog + size_t(i) * V, acc);
+          } else {
+            vst(qog + size_t(i) * V, v);
+          }
         }
       }
     } else {
@@ -895,6 +947,7 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
               if (sd >= 0) v.set(l, v.get(l) + AMP[l] * P.src_vec[size_t(sd) * Np + i]);
             }
           }
+          if (P.vout) vst(P.vout + (size_t(g) * Np + i) * V, v);
           vst(A + i * V, vmuls(tab.invfactN[i], v));
         }
       }
@@ -983,6 +1036,63 @@ __global__ void __launch_bounds__(T* GC) wadg_kernel(const WadgParams<real> P) {
     for (int idx = t; idx < V * Np; idx += T) {
       const int v = idx / Np, i = idx - v * Np;
       if (e0 + v < P.K) P.out[size_t(e0) * Np + idx] = R[i * V + v];
+    }
+    team_sync<T>();
+  }
+}
+
+// The adjoint stage's update before its spatial operator (AdjPreParams).
+template <int N, int M, typename real, int T, int V, int GC>
+__global__ void __launch_bounds__(T* GC) adj_pre_kernel(const AdjPreParams<real> P) {
+  using C = StageCfg<N, M, real, T, V, GC>;
+  using Tab = typename C::Tab;
+  using vt = vec<real, V>;
+  constexpr int Np = C::Np, Mp = C::Mp;
+  constexpr int BLK = 4 * Np * V;  // scalars of one group's four fields
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Tab& tab = *reinterpret_cast<const Tab*>(smem);
+  load_tables<C::TAB, C::THREADS>(smem, P.tables);
+  __syncthreads();
+  const int team = threadIdx.x / T;
+  const int t = threadIdx.x % T;
+  real* A = reinterpret_cast<real*>(smem + C::TAB) + team * C::TEAMV * V;
+  real* B = A + C::BUF * V;
+  real* C2S = B + C::BUF * V;  // [Mp]
+  real* IV = C2S + Mp * V;     // [V] 1 / |D| per element lane
+  const int64_t stride = int64_t(gridDim.x) * GC;
+  for (int64_t g = int64_t(blockIdx.x) * GC + team; g < P.G; g += stride) {
+    if (t < V) {  // 1 / |D| = 6 det[grad lambda_1; grad lambda_2; grad lambda_3]
+      const real* gg = P.geom + size_t(g) * 9 * V + t;
+      const real a1 = gg[0], a2 = gg[V], a3 = gg[2 * V], b1 = gg[3 * V], b2 = gg[4 * V], b3 = gg[5 * V],
+                 c1 = gg[6 * V], c2v = gg[7 * V], c3 = gg[8 * V];
+      IV[t] = real(6) * (a1 * (b2 * c3 - b3 * c2v) - a2 * (b1 * c3 - b3 * c1) + a3 * (b1 * c2v - b2 * c1));
+    }
+    for (int idx = t; idx < Mp * V; idx += T) C2S[idx] = P.c2[size_t(g) * Mp * V + idx];
+    team_sync<T>();
+    real* rg = P.rho + size_t(g) * BLK;
+    const real* kg = P.kap + size_t(g) * BLK;
+    real* yg = P.y + size_t(g) * BLK;
+    for (int idx = t; idx < BLK; idx += T) {
+      const real r = P.a * rg[idx] + P.b * kg[idx];
+      rg[idx] = r;
+      const int i = (idx / V) % Np;
+      if (idx < Np * V)
+        A[idx] = r * tab.invfactN[i];
+      else
+        yg[idx] = r * IV[idx % V];
+    }
+    if (t == 0) vst(A + Np * V, vzero<real, V>());
+    vt bh[Mp];
+#pragma unroll
+    for (int b = 0; b < Mp; ++b) bh[b] = vmuls(tab.invfactM[b], vld<real, V>(C2S + b * V));
+    team_sync<T>();
+    vt lv[N + 1][C::RMAX];
+    wadg_group<N, M, real, T, V, C::RMAX>(tab, A, B, bh, true, t, lv);
+    const vt iv = vld<real, V>(IV);
+#pragma unroll
+    for (int r = 0; r < C::RMAX; ++r) {
+      const int i = t + r * T;
+      if (i < Np) vst(yg + size_t(i) * V, vmul(lv[0][r], iv));
     }
     team_sync<T>();
   }

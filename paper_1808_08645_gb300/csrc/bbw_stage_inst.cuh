@@ -37,6 +37,10 @@ template <int M, typename real>
 constexpr auto wadg_fn() {
   return wadg_kernel<kN, M, real, Shape<real>::T, Shape<real>::V, kGC<M, real>>;
 }
+template <int M, typename real>
+constexpr auto adj_pre_fn() {
+  return adj_pre_kernel<kN, M, real, Shape<real>::T, Shape<real>::V, kGC<M, real>>;
+}
 
 
 template <typename F>
@@ -100,6 +104,8 @@ cudaError_t prepare(int M, bool dbl, int* per_sm_stage, int* per_sm_wadg) {
     if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute(spatial_fn<MM, real>(), cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (err != cudaSuccess) return err;
+    err = cudaFuncSetAttribute(adj_pre_fn<MM, real>(), cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (err != cudaSuccess) return err;
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm_stage, ks, C::THREADS, C::SMEM);
     if (err != cudaSuccess) return err;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm_wadg, kw, C::THREADS, C::SMEM);
@@ -133,13 +139,22 @@ cudaError_t launch_wadg(int M, bool dbl, const void* params, int grid, cudaStrea
   });
 }
 
+cudaError_t launch_adj_pre(int M, bool dbl, const void* params, int grid, cudaStream_t s) {
+  return dispatch(M, dbl, [&]<int MM, typename real>() {
+    using C = Cfg<MM, real>;
+    adj_pre_fn<MM, real>()<<<grid, C::THREADS, C::SMEM, s>>>(*static_cast<const AdjPreParams<real>*>(params));
+    return cudaGetLastError();
+  });
+}
+
 }  // namespace
 
 #define BBW_CAT2(a, b) a##b
 #define BBW_CAT(a, b) BBW_CAT2(a, b)
 const KernelOps& BBW_CAT(ops_n, BBW_N)() {
-  static const KernelOps ops = {&tables_size, &build,       &face_maps,      &prepare,     &launch_stage,
-                                &launch_wadg, &launch_shape, &launch_spatial, &check_tables};
+  static const KernelOps ops = {&tables_size,  &build,          &face_maps,    &prepare,
+                                &launch_stage, &launch_wadg,    &launch_shape, &launch_spatial,
+                                &check_tables, &launch_adj_pre};
   return ops;
 }
 

@@ -40,7 +40,7 @@ def _gpu(vxyz, etov, N, M, prec, c2, q0, source=True):
     return s
 
 
-@pytest.mark.parametrize("prec,tol", [(64, 1e-9), (32, 2e-3)])
+@pytest.mark.parametrize("prec,tol", [(64, 1e-9), (32, 1e-4)])
 @pytest.mark.parametrize("N,M", [(2, 1), (4, 2)])
 def test_gradient_matches_oracle_adjoint(N, M, prec, tol):
     vxyz, etov, c2, q0, rng = _case(1, N, M, prec, seed=N)
@@ -128,3 +128,84 @@ def test_autograd_function_gradcheck_and_backward():
     gc, _ = s.adjoint(tr - data.numpy())
     assert np.allclose(c2t.grad.numpy(), gc, rtol=1e-12, atol=1e-14)
     s.close()
+
+
+def test_backward_of_an_earlier_forward_uses_its_own_run():
+    """Two forwards on one solver, then the backward of the first: its gradient
+    is the first run's (the autograd function records that run again)."""
+    import torch
+
+    from paper_1808_08645_gb300.autograd import receiver_traces
+
+    N, M = 2, 1
+    vxyz, etov, c2, q0, rng = _case(1, N, M, 64, seed=23)
+    s = _gpu(vxyz, etov, N, M, 64, c2, q0)
+    c2a = torch.tensor(c2, dtype=torch.float64, requires_grad=True)
+    c2b = torch.tensor(c2 * 1.3, dtype=torch.float64, requires_grad=True)
+    data = torch.tensor(rng.standard_normal((3, len(XR))) * 1e-2)
+    la = 0.5 * ((receiver_traces(s, c2a, q0, 0.01, 3, 2) - data) ** 2).sum()
+    lb = 0.5 * ((receiver_traces(s, c2b, q0, 0.01, 3, 2) - data) ** 2).sum()
+    la.backward()
+    lb.backward()
+    for c2v, got in ((c2, c2a.grad), (c2 * 1.3, c2b.grad)):
+        s.set_c2(c2v)
+        s.set_state(q0)
+        tr = s.record(0.01, 3, 2)
+        gc, _ = s.adjoint(tr - data.numpy())
+        assert np.allclose(got.numpy(), gc, rtol=1e-12, atol=1e-14)
+    assert not np.allclose(c2a.grad.numpy(), c2b.grad.numpy())
+    s.close()
+
+
+def test_gradient_on_the_adjoint_workload_mesh():
+    """The adjoint workload's mesh and degree (16^3 x 6 = 24,576 tets, N = 5,
+    M = 2, 64 receivers on the top face) in FP64, over 20 steps: the adjoint's
+    directional derivative of the L2 misfit matches central differences of
+    GPU forward runs, and FP32 matches FP64."""
+    cfg = inputs.ADJOINT_CONFIG
+    N, M = cfg["N"], cfg["M"]
+    vxyz, etov = inputs.cube_mesh(cfg["hexes"])
+    K = len(etov)
+    c2 = inputs.sample_at_domain_points(vxyz, etov, M, inputs.c2_smooth_random(seed=cfg["model_seed"]))
+    rec = inputs.top_face_receivers()
+    nsteps = 20
+    rng = np.random.default_rng(3)
+
+    # a pressure pulse just below the receivers, so that 20 steps already
+    # give traces that depend on c^2 (plus the workload's point source)
+    q0 = np.zeros((4, K, bb.np_count(N)))
+    q0[0] = inputs.sample_at_domain_points(vxyz, etov, N, inputs.gaussian_pulse((0.5, 0.5, 0.9), 0.1))
+
+    def solver(prec, c2v):
+        s = B.Solver(vxyz, etov, N, M, prec)
+        s.set_c2(c2v)
+        s.set_state(q0)
+        s.set_receivers(rec)
+        return s
+
+    s = solver(64, c2)
+    dt = s.cfl_dt(cfg["cfl"])
+    amp = B.ricker_samples(dt, nsteps, f0=40.0, t0=2 * dt)
+    s.set_point_source(np.array(cfg["source"]), amp)
+    tr = s.record(dt, nsteps, 5)
+    data = tr * 0.9 + 1e-3 * rng.standard_normal(tr.shape) * np.abs(tr).max()
+    gc, _ = s.adjoint(tr - data)
+    s.close()
+
+    def misfit(c2v):
+        t = solver(64, c2v)
+        t.set_point_source(np.array(cfg["source"]), amp)
+        out = t.record(dt, nsteps, 5)
+        t.close()
+        return 0.5 * np.sum((out - data) ** 2)
+
+    d = rng.uniform(-1.0, 1.0, c2.shape) * 0.1
+    eps = 1e-5
+    fd = (misfit(c2 + eps * d) - misfit(c2 - eps * d)) / (2 * eps)
+    assert abs(fd - np.sum(gc * d)) <= 1e-6 * abs(fd)
+    s32 = solver(32, c2)
+    s32.set_point_source(np.array(cfg["source"]), amp)
+    tr32 = s32.record(dt, nsteps, 5)
+    gc32, _ = s32.adjoint(tr32 - data)
+    s32.close()
+    assert rel_l2(gc32, gc) <= 1e-3
