@@ -266,10 +266,15 @@ bbw_status bbw_wadg_update(int N, int M, int precision, int64_t K, const void* r
  * is being captured into a CUDA graph, frameworks that own the whole device
  * memory pool and forbid allocations outside it, latency-critical loops that
  * must not block on the allocator. bbw_wadg_update caches its operator tables
- * in device memory it allocates on first use; this variant instead copies the
+ * in device memory it allocates on first use; this variant instead writes the
  * tables of each call into one fixed 32 KiB array in the library's static
  * device memory (present on every GPU that loads the library until the process
- * exits). It calls no cudaMalloc or cudaFree and no allocating library routine.
+ * exits), passing them as the parameters of a small install kernel launched on
+ * `stream` ahead of the update, so no host memory is read after the call
+ * returns. It calls no cudaMalloc or cudaFree and no allocating library routine.
+ * While another stream of the process is being captured in the global capture
+ * mode, pass a stream other than the legacy default stream (NULL), on which no
+ * work may be enqueued during such a capture.
  *   Arguments, layout and result: as bbw_wadg_update.
  *   Limit: the tables must fit in 32 KiB; every supported (N, M, precision)
  *   does except N = 9 with M = 3, which returns BBW_ERR_ARG with a message.

@@ -67,6 +67,11 @@ struct AdjointData {
   int64_t* d_rec_elem = nullptr;
   void* d_rec_vec = nullptr;
   void* d_rec_dual = nullptr;
+  // the receivers grouped by element (internal index): ue [nue], rptr [nue + 1], rlist [nrec]
+  int64_t nue = 0;
+  int64_t* d_ue = nullptr;
+  int32_t* d_rptr = nullptr;
+  int32_t* d_rlist = nullptr;
   // recorded run
   bool recorded = false;
   double dt = 0.0;
@@ -82,6 +87,8 @@ struct AdjointData {
   void* d_invf = nullptr;
   void* d_gw = nullptr;
   int ngam = 0;
+  bool grad_ready = false;  // the gradient kernel's shared-memory attribute is set
+  int nsm = 0;              // SMs of the device
   // adjoint state (internal layout [G][4][Np][V]): kap, rho, y; the recompute's
   // state ping-pong and residual; the pressure brackets of every stage of a
   // segment [5 C][G][Np][V]; the c^2 gradient [K][Mp] (internal element order)
@@ -102,40 +109,68 @@ __host__ __device__ inline size_t iidx(int64_t e, int i, int f, int Np, int V) {
   return ((size_t(e / V) * 4 + f) * Np + i) * V + size_t(e % V);
 }
 
-// traces: out[r] = sum_i B_r[i] p_{e_r}[i]
+// traces: out[r] = sum_i B_r[i] p_{e_r}[i], one warp per receiver
 template <typename real>
 __global__ void sample_kernel(const real* __restrict__ q, int64_t nrec, const int64_t* __restrict__ el,
                               const real* __restrict__ vec, int Np, int V, double* __restrict__ out) {
-  const int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (r >= nrec) return;
+  const int64_t r = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) / 32;
+  const int lane = threadIdx.x % 32;
+  if (r >= nrec) return;  // warp-uniform
   double acc = 0.0;
-  for (int i = 0; i < Np; ++i) acc += double(vec[r * Np + i]) * double(q[iidx(el[r], i, 0, Np, V)]);
-  out[r] = acc;
+  for (int i = lane; i < Np; i += 32) acc += double(vec[r * Np + i]) * double(q[iidx(el[r], i, 0, Np, V)]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) out[r] = acc;
 }
 
-// kap_p[e_r] += g[r] M^{-1} B_r, receivers in order (threads over coefficients)
+// kap_p[e] += sum_{r at e} g[r] M^{-1} B_r: one block per receiving element,
+// its receivers summed in order (rptr: CSR over the elements ue that hold
+// receivers, rlist: receiver indices), threads over coefficients
 template <typename real>
-__global__ void receiver_adjoint_kernel(real* __restrict__ kap, int64_t nrec, const int64_t* __restrict__ el,
+__global__ void receiver_adjoint_kernel(real* __restrict__ kap, const int64_t* __restrict__ ue,
+                                        const int32_t* __restrict__ rptr, const int32_t* __restrict__ rlist,
                                         const real* __restrict__ dual, const double* __restrict__ g, int Np, int V) {
-  for (int i = threadIdx.x; i < Np; i += blockDim.x)
-    for (int64_t r = 0; r < nrec; ++r) kap[iidx(el[r], i, 0, Np, V)] += real(g[r]) * dual[r * Np + i];
+  const int u = blockIdx.x;
+  for (int i = threadIdx.x; i < Np; i += blockDim.x) {
+    real acc = 0;
+    for (int x = rptr[u]; x < rptr[u + 1]; ++x) acc += real(g[rlist[x]]) * dual[size_t(rlist[x]) * Np + i];
+    kap[iidx(ue[u], i, 0, Np, V)] += acc;
+  }
 }
 
 // gc[e][b] += dt sum_gamma G[gamma][b] sum_{(a, a') in pairs(gamma)} rho_p[e][a] / a! * v[e][a'] / a'!,
-// one warp per element; rho_p is field 0 of the internal [G][4][Np][V]
-// layout, v the internal pressure layout [G][Np][V].
-constexpr int kAdjWarps = 4;
+// one warp per element (lanes over gamma); rho_p is field 0 of the internal
+// [G][4][Np][V] layout, v the internal pressure layout [G][Np][V]. With SMEM
+// the pair table, its row pointers and G are first copied into shared memory
+// (read once per block instead of once per element).
+constexpr int kAdjWarps = 8;
 constexpr int kMaxMp = 20;
-template <typename real>
+template <typename real, bool SMEM>
 __global__ void __launch_bounds__(32 * kAdjWarps) adj_grad_kernel(
     const real* __restrict__ rho, const real* __restrict__ v, real* __restrict__ gc, int64_t K, int Np, int Mp, int V,
-    int ngam, const int32_t* __restrict__ gptr, const uint32_t* __restrict__ pairs, const real* __restrict__ invf,
-    const real* __restrict__ gw, real dt) {
+    int ngam, const int32_t* __restrict__ gptr_g, const uint32_t* __restrict__ pairs_g, const real* __restrict__ invf,
+    const real* __restrict__ gw_g, real dt) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   real* sm = reinterpret_cast<real*>(sm_raw);
   const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
   real* rs = sm + size_t(w) * 2 * Np;
   real* vs = rs + Np;
+  const int32_t* gptr = gptr_g;
+  const uint32_t* pairs = pairs_g;
+  const real* gw = gw_g;
+  if constexpr (SMEM) {
+    const int np2 = Np * Np;
+    real* gws = sm + size_t(kAdjWarps) * 2 * Np;
+    uint32_t* ps = reinterpret_cast<uint32_t*>(gws + size_t(ngam) * Mp);
+    int32_t* gp = reinterpret_cast<int32_t*>(ps + np2);
+    for (int x = threadIdx.x; x < ngam * Mp; x += blockDim.x) gws[x] = gw_g[x];
+    for (int x = threadIdx.x; x < np2; x += blockDim.x) ps[x] = pairs_g[x];
+    for (int x = threadIdx.x; x <= ngam; x += blockDim.x) gp[x] = gptr_g[x];
+    __syncthreads();
+    gptr = gp;
+    pairs = ps;
+    gw = gws;
+  }
   for (int64_t e = int64_t(blockIdx.x) * kAdjWarps + w; e < K; e += int64_t(gridDim.x) * kAdjWarps) {
     const int64_t g = e / V;
     const int l = int(e % V);
@@ -149,7 +184,9 @@ __global__ void __launch_bounds__(32 * kAdjWarps) adj_grad_kernel(
     for (int b = 0; b < kMaxMp; ++b) acc[b] = real(0);
     for (int c = lane; c < ngam; c += 32) {
       real wg = 0;
-      for (int p = gptr[c]; p < gptr[c + 1]; ++p) {
+      const int p1 = gptr[c + 1];
+#pragma unroll 4
+      for (int p = gptr[c]; p < p1; ++p) {
         const uint32_t ab = pairs[p];
         wg += rs[ab & 0xffffu] * vs[ab >> 16];
       }
@@ -324,11 +361,30 @@ bbw_status adjoint_stage(bbw_solver* s, AdjointData* a, const void* vbr, int sta
   // gc += dt rho_t,p^T T_beta v
   const int threads = 32 * kAdjWarps;
   const size_t shm = size_t(kAdjWarps) * 2 * s->Np * sizeof(real);
-  const int blocks = int(std::min<int64_t>((s->K + kAdjWarps - 1) / kAdjWarps, 152 * 16));
-  adj_grad_kernel<real><<<blocks, threads, shm, st>>>(
-      static_cast<const real*>(a->rho), static_cast<const real*>(vbr), static_cast<real*>(a->gc), s->K, s->Np, s->Mp,
-      s->V, a->ngam, a->d_gptr, a->d_pairs, static_cast<const real*>(a->d_invf), static_cast<const real*>(a->d_gw),
-      real(dt));
+  const size_t shm_tab = size_t(a->ngam) * s->Mp * sizeof(real) + size_t(s->Np) * s->Np * 4 + size_t(a->ngam + 1) * 4;
+  const bool in_smem = shm + shm_tab <= size_t(bbw::kSmemPerCta);
+  if (!a->grad_ready) {
+    if (in_smem)
+      BBW_CUDA(cudaFuncSetAttribute(adj_grad_kernel<real, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    int(shm + shm_tab)));
+    int dev = 0;
+    BBW_CUDA(cudaGetDevice(&dev));
+    BBW_CUDA(cudaDeviceGetAttribute(&a->nsm, cudaDevAttrMultiProcessorCount, dev));
+    a->grad_ready = true;
+  }
+  // blocks per SM: as many as the shared memory holds (at most 8)
+  const int per_sm = in_smem ? int(std::max<size_t>(1, std::min<size_t>(8, size_t(bbw::kSmemPerCta) / (shm + shm_tab)))) : 8;
+  const int blocks = int(std::min<int64_t>((s->K + kAdjWarps - 1) / kAdjWarps, int64_t(std::max(a->nsm, 1)) * per_sm));
+  auto launch = [&](auto kern, size_t bytes) {
+    kern<<<blocks, threads, bytes, st>>>(static_cast<const real*>(a->rho), static_cast<const real*>(vbr),
+                                         static_cast<real*>(a->gc), s->K, s->Np, s->Mp, s->V, a->ngam, a->d_gptr,
+                                         a->d_pairs, static_cast<const real*>(a->d_invf),
+                                         static_cast<const real*>(a->d_gw), real(dt));
+  };
+  if (in_smem)
+    launch(adj_grad_kernel<real, true>, shm + shm_tab);
+  else
+    launch(adj_grad_kernel<real, false>, shm);
   BBW_CUDA(cudaGetLastError());
   return BBW_OK;
 }
@@ -361,7 +417,7 @@ bbw_status record(bbw_solver* s, double dt, int64_t nsteps, int64_t every, doubl
     bbw_status st = bbw_step(s, dt, 1);
     if (st != BBW_OK) return st;
     if (a->nrec > 0)
-      sample_kernel<real><<<int((a->nrec + threads - 1) / threads), threads, 0, s->stream>>>(
+      sample_kernel<real><<<int((a->nrec * 32 + threads - 1) / threads), threads, 0, s->stream>>>(
           static_cast<const real*>(s->q[s->cur]), a->nrec, a->d_rec_elem, static_cast<const real*>(a->d_rec_vec),
           s->Np, s->V, a->d_traces + size_t(n) * a->nrec);
   }
@@ -427,9 +483,9 @@ bbw_status adjoint(bbw_solver* s, const double* g, double* grad_c2, double* grad
     for (int64_t n = n1 - 1; n >= n0; --n) {
       // cotangent of the traces after step n
       if (a->d_g) {
-        receiver_adjoint_kernel<real><<<1, 256, 0, sm>>>(static_cast<real*>(a->kap), a->nrec, a->d_rec_elem,
-                                                         static_cast<const real*>(a->d_rec_dual),
-                                                         a->d_g + size_t(n) * a->nrec, Np, s->V);
+        receiver_adjoint_kernel<real><<<int(a->nue), 64, 0, sm>>>(
+            static_cast<real*>(a->kap), a->d_ue, a->d_rptr, a->d_rlist, static_cast<const real*>(a->d_rec_dual),
+            a->d_g + size_t(n) * a->nrec, Np, s->V);
         BBW_CUDA(cudaGetLastError());
       }
       for (int sg = 4; sg >= 0; --sg) {
@@ -492,7 +548,8 @@ void free_adjoint(bbw_solver* s) {
   AdjointData* a = s->adj;
   if (!a) return;
   free_run(a, true);
-  for (void* p : {static_cast<void*>(a->d_rec_elem), a->d_rec_vec, a->d_rec_dual, static_cast<void*>(a->d_gptr),
+  for (void* p : {static_cast<void*>(a->d_rec_elem), a->d_rec_vec, a->d_rec_dual, static_cast<void*>(a->d_ue),
+                  static_cast<void*>(a->d_rptr), static_cast<void*>(a->d_rlist), static_cast<void*>(a->d_gptr),
                   static_cast<void*>(a->d_pairs), a->d_invf, a->d_gw, a->kap, a->rho, a->yi, a->qa[0], a->qa[1],
                   a->rs, a->gc, static_cast<void*>(a->d_g)})
     if (p) cudaFree(p);
@@ -544,10 +601,13 @@ bbw_status bbw_set_receivers(bbw_solver* s, int64_t nrec, const double* xyz, int
     if (!bbw::solve_mass(s->N, b)) return fail(BBW_ERR_ARG, "mass matrix factorisation failed");
     std::copy(b.begin(), b.end(), dual.begin() + ptrdiff_t(size_t(r) * s->Np));
   }
-  for (void** p : {reinterpret_cast<void**>(&a->d_rec_elem), &a->d_rec_vec, &a->d_rec_dual}) {
+  for (void** p : {reinterpret_cast<void**>(&a->d_rec_elem), &a->d_rec_vec, &a->d_rec_dual,
+                   reinterpret_cast<void**>(&a->d_ue), reinterpret_cast<void**>(&a->d_rptr),
+                   reinterpret_cast<void**>(&a->d_rlist)}) {
     if (*p) cudaFree(*p);
     *p = nullptr;
   }
+  a->nue = 0;
   a->nrec = nrec;
   a->rec_elem = el;
   free_run(a);
@@ -556,6 +616,26 @@ bbw_status bbw_set_receivers(bbw_solver* s, int64_t nrec, const double* xyz, int
     std::vector<int64_t> slots(el.size());
     for (size_t r = 0; r < el.size(); ++r) slots[r] = s->slot(el[r]);  // internal element order
     BBW_CUDA(cudaMemcpy(a->d_rec_elem, slots.data(), size_t(nrec) * sizeof(int64_t), cudaMemcpyHostToDevice));
+    // receivers grouped by element, each group in receiver order
+    std::vector<int32_t> order(slots.size());
+    for (size_t r = 0; r < order.size(); ++r) order[r] = int32_t(r);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return slots[size_t(x)] < slots[size_t(y)]; });
+    std::vector<int64_t> ue;
+    std::vector<int32_t> rptr;
+    for (size_t x = 0; x < order.size(); ++x) {
+      if (x == 0 || slots[size_t(order[x])] != slots[size_t(order[x - 1])]) {
+        ue.push_back(slots[size_t(order[x])]);
+        rptr.push_back(int32_t(x));
+      }
+    }
+    rptr.push_back(int32_t(order.size()));
+    a->nue = int64_t(ue.size());
+    BBW_CUDA(cudaMalloc(reinterpret_cast<void**>(&a->d_ue), ue.size() * sizeof(int64_t)));
+    BBW_CUDA(cudaMalloc(reinterpret_cast<void**>(&a->d_rptr), rptr.size() * sizeof(int32_t)));
+    BBW_CUDA(cudaMalloc(reinterpret_cast<void**>(&a->d_rlist), order.size() * sizeof(int32_t)));
+    BBW_CUDA(cudaMemcpy(a->d_ue, ue.data(), ue.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+    BBW_CUDA(cudaMemcpy(a->d_rptr, rptr.data(), rptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    BBW_CUDA(cudaMemcpy(a->d_rlist, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     bbw_status st = s->prec == 64 ? upload_real<double>(vec, &a->d_rec_vec) : upload_real<float>(vec, &a->d_rec_vec);
     if (st == BBW_OK)
       st = s->prec == 64 ? upload_real<double>(dual, &a->d_rec_dual) : upload_real<float>(dual, &a->d_rec_dual);

@@ -7,7 +7,9 @@
 // allocator. bbw_wadg_update gets its operator tables from a per-process cache
 // that allocates device memory on first use of each (N, M, precision); this
 // entry point instead keeps the tables of the current call in one fixed
-// file-scope device array, so it never allocates or frees device memory.
+// file-scope device array, so it never allocates or frees device memory. The
+// tables reach that array through the parameters of an install kernel
+// launched on the caller's stream ahead of the update kernel.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -31,8 +33,25 @@ constexpr int kMaxDevices = 64;
 // tables of the last call; calls that overlap on the GPU race on it.
 static __device__ __align__(256) unsigned char g_wadg_scratch[kScratchBytes];
 
+// The tables travel to the device as the by-value parameter of a small
+// install kernel (two launches of half the capacity each, under the kernel
+// parameter limit), so nothing on the host is read after the launch returns.
+constexpr size_t kChunkBytes = kScratchBytes / 2;
+struct TableChunk {
+  uint32_t offset, bytes;
+  alignas(16) unsigned char data[kChunkBytes];
+};
+
+// chunk.bytes is a multiple of 16 (table blobs are) and offset + bytes <= kScratchBytes
+__global__ void install_tables(const TableChunk chunk) {
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(chunk.data);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(g_wadg_scratch + chunk.offset);
+  for (uint32_t i = threadIdx.x; i < chunk.bytes / 4; i += blockDim.x) dst[i] = src[i];
+}
+
 // Host staging for the tables (no heap allocation), guarded by g_mu.
 alignas(16) unsigned char g_host_tables[kScratchBytes];
+TableChunk g_chunk;
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
 int g_num_sms[kMaxDevices] = {};
@@ -100,10 +119,15 @@ extern "C" bbw_status bbw_wadg_update_noalloc(int N, int M, int precision, int64
   if (st != BBW_OK) return fail(st, "projection constants");
   std::memset(g_host_tables, 0, bytes);
   ops->build_tables(M, dbl, cj, g_host_tables);
-  // From pageable memory the copy returns once the data is staged, so the host
-  // buffer may be reused by the next call.
-  err = cudaMemcpyAsync(g_scratch_ptr[dev], g_host_tables, bytes, cudaMemcpyHostToDevice, s);
-  if (err != cudaSuccess) return fail(BBW_ERR_CUDA, "table upload", err);
+  // the launch copies its parameter, so g_chunk may be refilled at once
+  for (size_t off = 0; off < bytes; off += kChunkBytes) {
+    g_chunk.offset = uint32_t(off);
+    g_chunk.bytes = uint32_t(std::min(kChunkBytes, bytes - off));
+    std::memcpy(g_chunk.data, g_host_tables + off, g_chunk.bytes);
+    install_tables<<<1, 256, 0, s>>>(g_chunk);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return fail(BBW_ERR_CUDA, "table upload", err);
+  }
 
   int team = 0, width = 1, gpc = 1;
   ops->launch_shape(M, dbl, &team, &width, &gpc);

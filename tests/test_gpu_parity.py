@@ -12,6 +12,7 @@ from oracle import bernstein as bb
 from oracle.acoustic import AcousticOracle
 from paper_1808_08645_gb300 import binding as B
 from paper_1808_08645_gb300 import inputs
+from paper_1808_08645_gb300 import project
 
 from parity_util import (TOL_FINAL, TOL_STAGE, oracle_stage_on_patch, random_case,
                          rel_l2, rounded, stage_times)
@@ -193,10 +194,11 @@ def test_final_time_parity_small_config(prec):
     cfg = inputs.PARITY_CONFIG
     N, M = cfg["N"], cfg["M"]
     vxyz, etov = inputs.cube_mesh(cfg["hexes"])
-    c2 = rounded(inputs.sample_at_domain_points(vxyz, etov, M, inputs.c2_config_small), prec)
+    # c^2 and the Gaussian L2-projected per element (the tools layer)
+    c2 = rounded(project.project_c2(vxyz, etov, M, inputs.c2_config_small), prec)
     K, Np = len(etov), bb.np_count(N)
     q0 = np.zeros((4, K, Np))
-    q0[0] = inputs.sample_at_domain_points(vxyz, etov, N, inputs.gaussian_pulse())
+    q0[0] = project.l2_project(vxyz, etov, N, inputs.gaussian_pulse())
     q0 = rounded(q0, prec)
     orc = AcousticOracle(vxyz, etov, N, M, c2)
     dt, nsteps = orc.dt_for(cfg["T"], cfg["cfl"])
@@ -416,4 +418,20 @@ def test_get_state_into_pinned_output_array():
     assert np.array_equal(got, want) and np.shares_memory(got, out)
     with pytest.raises(ValueError):
         s.get_state(out=np.empty(q.size, np.float32))
+    s.close()
+
+
+def test_projected_layer_jump_with_negative_coefficients_is_rejected():
+    """The sweep's medium (smooth field with a planar jump) L2-projected onto
+    P^2 of a coarse 2^3 x 6 mesh undershoots below zero next to the jump;
+    bbw_set_c2 rejects it with BBW_ERR_NONPOS_C2 and keeps the previous c^2."""
+    vxyz, etov = inputs.cube_mesh(2)
+    c2 = project.l2_project(vxyz, etov, 2, inputs.c2_smooth_random(seed=0), q=6)
+    assert (c2 <= 0).any()
+    with pytest.raises(project.NonPositiveC2):
+        project.project_c2(vxyz, etov, 2, inputs.c2_smooth_random(seed=0))
+    s = B.Solver(vxyz, etov, 3, 2, B.F32)
+    with pytest.raises(B.BBWError) as ei:
+        s.set_c2(c2)
+    assert ei.value.status == -3
     s.close()
