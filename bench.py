@@ -616,8 +616,10 @@ def run_adjoint(args):
     nsteps = args.adjoint_steps
     vxyz, etov = inputs.cube_mesh(cfg["hexes"])
     K = len(etov)
-    c2_true = make_c2(M, vxyz, etov, inputs.c2_smooth_random(seed=cfg["true_seed"]))
-    c2 = make_c2(M, vxyz, etov, inputs.c2_smooth_random(seed=cfg["model_seed"]))
+    # media sampled at the domain points: on this mesh the L2 projection of the
+    # seed-0 medium undershoots below zero next to its layer jump
+    c2_true = inputs.sample_at_domain_points(vxyz, etov, M, inputs.c2_smooth_random(seed=cfg["true_seed"]))
+    c2 = inputs.sample_at_domain_points(vxyz, etov, M, inputs.c2_smooth_random(seed=cfg["model_seed"]))
     rec = inputs.top_face_receivers()
     stream = torch.cuda.Stream()
     s = B.Solver(vxyz, etov, N, M, B.F32, stream=stream.cuda_stream)
