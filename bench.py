@@ -754,6 +754,91 @@ def run_elastic_reference(args):
     }
 
 
+def run_surrogate(args):
+    """The neural-operator surrogate: BBWADG runs generate the training and
+    held-out data, the network is trained by the library's kernels, and its
+    trace error on held-out runs (BBWADG as the judge) and its inference time
+    are reported against plain BBWADG."""
+    import torch
+
+    from paper_1808_08645_gb300 import binding as B
+    from paper_1808_08645_gb300 import build as libbuild
+    from paper_1808_08645_gb300 import surrogate as S
+
+    libbuild.build()
+    dcfg = dict(inputs.SURROGATE_CONFIG, grid=args.sur_grid)
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()
+    t = time.perf_counter()
+    X, Y, meta = S.generate(dcfg, 0, args.sur_runs)
+    Xt, Yt, _ = S.generate(dcfg, args.sur_runs, args.sur_test)
+    t_gen = time.perf_counter() - t
+    scale = float(Y.std())
+    net = S.Net(S.default_config(grid=dcfg["grid"], nt=Y.shape[2]), seed=0)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    losses = S.train(net, X, Y, args.sur_iters, scale=scale, lr=args.sur_lr, log_every=max(1, args.sur_iters // 20))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t
+    pred = S.predict(net, Xt, scale)
+    err = S.relative_errors(pred, Yt)
+    # inference time per sample (batches of 8, CUDA events) and one plain BBWADG run
+    xb = Xt[:8].contiguous()
+    for _ in range(3):
+        net.forward(xb)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    reps = 10
+    for _ in range(reps):
+        net.forward(xb)
+    e1.record()
+    e1.synchronize()
+    t_nn = e0.elapsed_time(e1) / 1e3 / (reps * 8)
+    vxyz, etov, rec, dt, amp = S._bbwadg_setup(dcfg)
+    stream = torch.cuda.Stream()
+    sol = B.Solver(vxyz, etov, dcfg["N"], dcfg["M"], B.F32, stream=stream.cuda_stream)
+    sol.set_receivers(rec)
+    run0 = inputs.surrogate_runs(args.sur_runs, 1, dcfg)[0]
+    S.bbwadg_traces(sol, vxyz, etov, dcfg, run0, dt, amp)  # warm-up
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    reps_b = 3
+    for _ in range(reps_b):
+        S.bbwadg_traces(sol, vxyz, etov, dcfg, run0, dt, amp)
+    torch.cuda.synchronize()
+    t_bbw = (time.perf_counter() - t) / reps_b
+    sol.close()
+    # the judge and fallback: a run outside the training box goes to BBWADG
+    c2min = float(X[..., 0].min()) * 0.75 + 1.25
+    c2max = float(X[..., 0].max()) * 0.75 + 1.25
+    sur = S.Surrogate(net, dcfg, scale, float(np.quantile(err, 0.95)), (c2min, c2max))
+    out_run = dict(run0, source=np.array([0.5, 0.5, 0.3]))
+    _, used_out, _ = sur.predict(out_run)
+    _, used_in, _ = sur.predict(run0, tol=float(np.quantile(err, 0.95)))
+    clocks = clk.stop()
+    return {
+        "metric": "surrogate speedup vs plain BBWADG @ receiver-trace L2 error", "impl": "ours",
+        "workload": "surrogate", "value": t_bbw / t_nn, "unit": "x (BBWADG run time / surrogate time per run)",
+        "n_gpus": 1, "steps": args.sur_iters, "warmup": 3, "ms_per_step": 1e3 * t_train / max(args.sur_iters, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (fp32 accumulate)",
+        "data": "synthetic (BBWADG runs)",
+        "config": {"workload": f"neural operator: c2 on a {dcfg['grid']}^3 grid + source xyz -> {len(rec)} "
+                               f"receiver traces x {Y.shape[2]} samples; 4 spectral layers, width 32, "
+                               f"{S.default_config()['modes']} cosine modes; trained on {args.sur_runs} BBWADG "
+                               f"N={dcfg['N']} runs on {dcfg['hexes']}^3 x 6 tets, {args.sur_test} held out",
+                   "iters": args.sur_iters, "batch": 8, "lr": args.sur_lr},
+        "heldout_rel_l2": {"all_traces": float(((pred - Yt).double().norm() / Yt.double().norm()).item()),
+                           "per_run_median": float(np.median(err)), "per_run_p95": float(np.quantile(err, 0.95)),
+                           "per_run_max": float(np.max(err))},
+        "train_runs_rel_l2_all_traces": float(((S.predict(net, X[:256], scale) - Y[:256]).double().norm()
+                                                / Y[:256].double().norm()).item()),
+        "time_s": {"bbwadg_run": t_bbw, "surrogate_per_run": t_nn, "generate": t_gen, "train": t_train},
+        "loss_curve": losses,
+        "fallback": {"out_of_box_source": used_out, "in_box_at_p95_tol": used_in},
+        "clocks": clocks,
+    }
+
+
 def run_elastic(args):
     import torch
 
@@ -890,7 +975,12 @@ def main():
     ap.add_argument("--cpu-reps", type=int, default=15)
     ap.add_argument("--ref-hexes", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["sweep", "batched", "adjoint", "elastic"], default="sweep")
+    ap.add_argument("--workload", choices=["sweep", "batched", "adjoint", "elastic", "surrogate"], default="sweep")
+    ap.add_argument("--sur-runs", type=int, default=inputs.SURROGATE_CONFIG["runs"])
+    ap.add_argument("--sur-test", type=int, default=inputs.SURROGATE_CONFIG["test_runs"])
+    ap.add_argument("--sur-iters", type=int, default=3000)
+    ap.add_argument("--sur-grid", type=int, default=inputs.SURROGATE_CONFIG["grid"])
+    ap.add_argument("--sur-lr", type=float, default=2e-3)
     ap.add_argument("--adjoint-steps", type=int, default=inputs.ADJOINT_CONFIG["steps"])
     ap.add_argument("--instances", type=int, default=inputs.BATCH_CONFIG["instances"])
     args = ap.parse_args()
@@ -900,6 +990,10 @@ def main():
         out = run_adjoint(args) if args.impl == "ours" else {
             "impl": "reference", "workload": "adjoint",
             "unavailable": "the FP64 oracle adjoint is dense (small meshes only); its check is in the tests"}
+    elif args.workload == "surrogate":
+        out = run_surrogate(args) if args.impl == "ours" else {
+            "impl": "reference", "workload": "surrogate",
+            "unavailable": "the surrogate's reference is plain BBWADG, timed in the same line"}
     elif args.workload == "batched":
         out = run_batched(args) if args.impl == "ours" else {
             "impl": "reference", "workload": "batched",

@@ -101,6 +101,14 @@ EXPORTS = {
     "bbw_elastic_advance": (_int, [_p, _d, _d, _dp, _i64p]),
     "bbw_elastic_sync": (_int, [_p]),
     "bbw_elastic_get_time": (_int, [_p, _dp, _i64p]),
+    # include/bbw_nn.h: the surrogate's kernels
+    "bbw_nn_gemm": (_int, [_int, _int, _int, _p, _int, C.c_longlong, _int, _p, _int, C.c_longlong, _int, _p, _int,
+                           C.c_longlong, _int, C.c_float, C.c_float, _p, _p, _int, _int, _p]),
+    "bbw_nn_gelu_backward": (_int, [_p, _p, C.c_longlong, _p]),
+    "bbw_nn_bias_grad": (_int, [_p, _p, C.c_longlong, _int, _p]),
+    "bbw_nn_gather_receivers": (_int, [_p, _p, _p, _p, _int, _int, _int, _int, _int, _int, _int, _p]),
+    "bbw_nn_mse": (_int, [_p, _p, _p, _p, C.c_longlong, _p]),
+    "bbw_nn_adam": (_int, [_p, _p, _p, _p, C.c_longlong, _int, C.c_float, C.c_float, C.c_float, C.c_float, _p]),
 }
 
 

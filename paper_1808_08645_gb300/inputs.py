@@ -27,6 +27,7 @@ __all__ = [
     "PARITY_CONFIG", "SWEEP_CONFIG", "BATCH_CONFIG", "batched_instances", "ADJOINT_CONFIG",
     "top_face_receivers", "ELASTIC_CONFIG", "elastic_media", "elastic_pulse",
     "ricker", "ricker_samples", "manufactured_forcing",
+    "SURROGATE_CONFIG", "surrogate_runs", "grid_centres", "surrogate_features",
 ]
 
 #: the FP64 parity workload: 4^3 hexes x 6 = 384 tets, N=3, M=1, T=0.5
@@ -258,4 +259,46 @@ def manufactured_forcing(c2):
         s = np.sin(np.pi * x)
         return (3.0 - 1.0 / c2(x)) * np.pi * s[:, 0] * s[:, 1] * s[:, 2]
     return field
+
+
+#: the surrogate workload: BBWADG N = 4 runs on 16^3 x 6 tets (the adjoint's
+#: mesh) with 64 receivers on the top face, each run a seeded smooth random
+#: medium (the sweep's recipe with its layer jump, seed 5000 + run) and a
+#: Ricker source (peak frequency f0, delay t0) at a seeded position in the
+#: box [src_lo, src_hi]; traces of `steps` RK steps at the common CFL step of
+#: c^2 <= c2_max, every `every`-th kept (512 samples); the network sees c^2 on
+#: the centres of a grid^3 grid plus the source position
+SURROGATE_CONFIG = dict(runs=4096, test_runs=256, hexes=16, N=4, M=2, steps=512, every=1, f0=25.0, t0=0.04,
+                        src_lo=(0.25, 0.25, 0.55), src_hi=(0.75, 0.75, 0.85), grid=64, c2_max=3.0, cfl=0.5,
+                        sigma=0.05)
+
+
+def surrogate_runs(first: int, n: int, cfg: dict = SURROGATE_CONFIG):
+    """Descriptions (medium seed, source position) of runs first .. first + n - 1."""
+    out = []
+    for i in range(first, first + n):
+        rng = np.random.default_rng(5000 + i)
+        out.append(dict(c2_seed=5000 + i, source=rng.uniform(cfg["src_lo"], cfg["src_hi"])))
+    return out
+
+
+def grid_centres(G: int) -> np.ndarray:
+    """[G^3, 3] cell centres (i + 1/2)/G of a G^3 grid on the unit cube, x outermost."""
+    c = (np.arange(G) + 0.5) / G
+    X, Y, Z = np.meshgrid(c, c, c, indexing="ij")
+    return np.stack([X, Y, Z], -1).reshape(-1, 3)
+
+
+def surrogate_features(c2_field, xs, G: int, sigma: float) -> np.ndarray:
+    """[G, G, G, 6] float32 network input: (c^2 - 1.25)/0.75 on the grid, the
+    coordinates mapped to [-1, 1], a Gaussian bump of width sigma at the
+    source xs and the distance to it (times 2)."""
+    x = grid_centres(G)
+    f = np.empty((len(x), 6), dtype=np.float32)
+    f[:, 0] = (c2_field(x) - 1.25) / 0.75
+    f[:, 1:4] = 2.0 * x - 1.0
+    d2 = np.sum((x - np.asarray(xs)) ** 2, axis=1)
+    f[:, 4] = np.exp(-d2 / (2.0 * sigma ** 2))
+    f[:, 5] = 2.0 * np.sqrt(d2)
+    return f.reshape(G, G, G, 6)
 

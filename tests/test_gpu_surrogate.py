@@ -1,0 +1,154 @@
+"""The surrogate network's kernels on the GPU against the FP64 reference
+network (oracle/fno.py): forward traces and every parameter gradient, the
+GEMM kernel against numpy on ragged shapes, MSE and Adam.
+
+Tolerance: the GEMM rounds both operands to BF16 (unit roundoff 2^-9), so
+each contraction carries a relative error of a few 1e-3 and the network's
+chain of ~10 of them about 1e-2: outputs and gradients are compared in
+relative L2 at 2e-2."""
+import numpy as np
+import pytest
+
+from oracle import fno
+from parity_util import rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-2
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1808_08645_gb300 import build
+    build.build()
+
+
+def _cfg():
+    from paper_1808_08645_gb300 import surrogate as S
+    return S.default_config(grid=8, width=8, modes=(3, 3, 2), layers=2, cin=6, hidden=16, nt=12, receivers=2)
+
+
+@pytest.mark.parametrize("tA,tB", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_gemm_bf16_against_numpy(tA, tB):
+    from paper_1808_08645_gb300 import surrogate as S
+    rng = np.random.default_rng(tA * 2 + tB)
+    for M, N, K, batch, splits in [(70, 45, 37, 3, 1), (5, 33, 130, 2, 1), (33, 17, 3000, 1, 7)]:
+        A = rng.standard_normal((batch, K, M) if tA else (batch, M, K))
+        Bm = rng.standard_normal((batch, N, K) if tB else (batch, K, N))
+        want = np.einsum("bmk,bkn->bmn", A.transpose(0, 2, 1) if tA else A, Bm.transpose(0, 2, 1) if tB else Bm)
+        # BF16-rounded operands give the reference the kernel can reach exactly up to FP32 sums
+        rA = torch.tensor(A, dtype=torch.float32).bfloat16().double().numpy()
+        rB = torch.tensor(Bm, dtype=torch.float32).bfloat16().double().numpy()
+        want_r = np.einsum("bmk,bkn->bmn", rA.transpose(0, 2, 1) if tA else rA, rB.transpose(0, 2, 1) if tB else rB)
+        dA = torch.tensor(A, dtype=torch.float32, device="cuda")
+        dB = torch.tensor(Bm, dtype=torch.float32, device="cuda")
+        dC = torch.zeros((batch, M, N), dtype=torch.float32, device="cuda")
+        S.gemm(M, N, K, dA, M if tA else K, A[0].size, tA, dB, K if tB else N, Bm[0].size, tB, dC, N, M * N,
+               batch=batch, splits=splits)
+        got = dC.double().cpu().numpy()
+        assert rel_l2(got, want_r) < 1e-5
+        assert rel_l2(got, want) < 1e-2
+
+
+def test_forward_and_gradients_match_the_reference_network():
+    from paper_1808_08645_gb300 import surrogate as S
+    cfg = _cfg()
+    rng = np.random.default_rng(1)
+    p = fno.init_params(cfg, seed=2)
+    x = rng.standard_normal((2, 8, 8, 8, 6))
+    dy = rng.standard_normal((2, len(cfg["rx"]), cfg["nt"]))
+    y_ref, cache = fno.forward(p, cfg, x)
+    g_ref = fno.backward(p, cfg, cache, dy)
+    net = S.Net(cfg, params=p)
+    y, c = net.forward(torch.tensor(x, dtype=torch.float32, device="cuda"))
+    assert rel_l2(y.double().cpu().numpy(), y_ref) <= TOL
+    g = net.backward(c, torch.tensor(dy, dtype=torch.float32, device="cuda"))
+    for k in p:
+        assert rel_l2(g[k].double().cpu().numpy(), g_ref[k]) <= TOL, k
+
+
+def test_mse_and_adam_kernels():
+    from paper_1808_08645_gb300 import surrogate as S
+    cfg = _cfg()
+    net = S.Net(cfg, seed=0)
+    rng = np.random.default_rng(3)
+    y = torch.tensor(rng.standard_normal((3, 4, 5)), dtype=torch.float32, device="cuda")
+    t = torch.tensor(rng.standard_normal((3, 4, 5)), dtype=torch.float32, device="cuda")
+    lo, dy = net.loss(y, t)
+    yn, tn = y.double().cpu().numpy(), t.double().cpu().numpy()
+    assert abs(float(lo) - np.mean((yn - tn) ** 2)) < 1e-5
+    assert np.allclose(dy.double().cpu().numpy(), 2 * (yn - tn) / yn.size, atol=1e-6)
+    # two Adam steps against the update in FP64
+    p0 = {k: v.double().cpu().numpy() for k, v in net.p.items()}
+    m = {k: np.zeros_like(v) for k, v in p0.items()}
+    v2 = {k: np.zeros_like(v) for k, v in p0.items()}
+    grads = [{k: rng.standard_normal(v.shape) for k, v in p0.items()} for _ in range(2)]
+    for s, gr in enumerate(grads, 1):
+        for k in net.g:
+            net.g[k].copy_(torch.tensor(gr[k]))
+            m[k] = 0.9 * m[k] + 0.1 * gr[k]
+            v2[k] = 0.999 * v2[k] + 0.001 * gr[k] ** 2
+            # the efficient form of Kingma & Ba: bias corrections folded into the step
+            lr_t = 1e-2 * np.sqrt(1 - 0.999 ** s) / (1 - 0.9 ** s)
+            p0[k] -= lr_t * m[k] / (np.sqrt(v2[k]) + 1e-8)
+        net.adam(lr=1e-2)
+    for k in p0:
+        assert np.allclose(net.p[k].double().cpu().numpy(), p0[k], atol=2e-6), k
+
+
+def test_training_reduces_the_loss_on_a_fixed_batch():
+    from paper_1808_08645_gb300 import surrogate as S
+    cfg = _cfg()
+    net = S.Net(cfg, seed=4)
+    rng = np.random.default_rng(5)
+    x = torch.tensor(rng.standard_normal((2, 8, 8, 8, 6)), dtype=torch.float32, device="cuda")
+    t = torch.tensor(rng.standard_normal((2, len(cfg["rx"]), cfg["nt"])), dtype=torch.float32, device="cuda")
+    first = None
+    for _ in range(60):
+        y, c = net.forward(x)
+        lo, dy = net.loss(y, t)
+        net.backward(c, dy)
+        net.adam(lr=3e-3)
+        first = float(lo) if first is None else first
+    assert float(lo) < 0.5 * first
+
+
+def test_small_pipeline_generate_train_judge_and_fall_back():
+    """A reduced surrogate workload end to end: BBWADG runs make the data, the
+    network fits its training runs, held-out errors are finite, and runs
+    outside the training box (or asked for a tolerance below the calibrated
+    error) are solved by BBWADG (bitwise the direct solve)."""
+    from paper_1808_08645_gb300 import inputs
+    from paper_1808_08645_gb300 import surrogate as S
+    dcfg = dict(inputs.SURROGATE_CONFIG, hexes=3, N=2, steps=48, grid=16)
+    X, Y, meta = S.generate(dcfg, 0, 24, threads=4)
+    Xt, Yt, _ = S.generate(dcfg, 24, 6, threads=2)
+    assert torch.isfinite(Y).all() and float(Y.abs().max()) > 0
+    scale = float(Y.std())
+    net = S.Net(S.default_config(grid=16, width=8, modes=(3, 3, 3), layers=2, hidden=16, nt=Y.shape[2]), seed=1)
+    def train_mse():
+        return float(((S.predict(net, X, scale) - Y) ** 2).mean())
+
+    m0 = train_mse()
+    S.train(net, X, Y, 300, scale=scale, lr=1e-2)
+    assert train_mse() < 0.7 * m0  # it learns its training runs
+    e1 = S.relative_errors(S.predict(net, Xt, scale), Yt)  # held out (far too few runs here to generalise)
+    assert np.isfinite(e1).all()
+    sur = S.Surrogate(net, dcfg, scale, float(np.quantile(e1, 0.95)), (0.4, 3.5))
+    run = inputs.surrogate_runs(24, 1, dcfg)[0]
+    out_run = dict(run, source=np.array([0.5, 0.5, 0.3]))
+    tr, used, _ = sur.predict(out_run)
+    assert used == "bbwadg"
+    vxyz, etov, rec, dt, amp = S._bbwadg_setup(dcfg)
+    from paper_1808_08645_gb300 import binding as B
+    s = B.Solver(vxyz, etov, dcfg["N"], dcfg["M"], B.F32)
+    s.set_receivers(rec)
+    assert np.array_equal(tr, S.bbwadg_traces(s, vxyz, etov, dcfg, out_run, dt, amp))
+    s.close()
+    _, used, _ = sur.predict(run, tol=sur.err)  # the calibrated error is accepted
+    assert used == "surrogate"
+    _, used, _ = sur.predict(run, tol=0.5 * sur.err)  # a tighter tolerance falls back
+    assert used == "bbwadg"
