@@ -45,13 +45,23 @@ bbw_status bbw_nn_bias_grad(const float* dY, float* db, long long rows, int N, v
 
 /*
  * Receiver features from a field u [B][X][Y][Z][C]: out [B][R][C] is the mean
- * of the four grid points (rx[r] + {0,1}, ry[r] + {0,1}) on the top layer
- * z = Z - 1 (int device arrays rx, ry [R]; the 2 x 2 stencils of different
- * receivers must be disjoint). transpose = 1 applies the transpose instead:
- * u += the scatter of out (the backward).
+ * of the eight grid points (rx[r] + {0,1}, ry[r] + {0,1}, rz[r] + {0,1})
+ * (int device arrays rx, ry, rz [R]; the stencils of different receivers must
+ * be disjoint; a stencil not inside the grid gives 0). transpose = 1 applies
+ * the transpose instead: u += the scatter of out (the backward).
  */
-bbw_status bbw_nn_gather_receivers(const float* u, float* out, const int* rx, const int* ry, int B, int X, int Y,
-                                   int Z, int C, int R, int transpose, void* stream);
+bbw_status bbw_nn_gather_receivers(const float* u, float* out, const int* rx, const int* ry, const int* rz, int B,
+                                   int X, int Y, int Z, int C, int R, int transpose, void* stream);
+
+/*
+ * Time-shifted traces: out[i][t] = scale[i] * in[i](t + shift[i]) for rows
+ * i < rows of T samples, in[i](x) the linear interpolation, at the fractional
+ * position x, of the samples extended by zeros (in[i][j] = 0 for j < 0 or
+ * j >= T). shift [rows] (samples, any sign), scale [rows] (NULL: 1); in and
+ * out must not be the same array.
+ */
+bbw_status bbw_nn_shift_traces(const float* in, float* out, const float* shift, const float* scale, long long rows,
+                               int T, void* stream);
 
 /* loss[0] += sum_i (y_i - t_i)^2 / n and, if dy != NULL, dy = 2 (y - t) / n. */
 bbw_status bbw_nn_mse(const float* y, const float* t, float* dy, float* loss, long long n, void* stream);

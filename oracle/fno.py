@@ -9,7 +9,7 @@ cosine basis):
     u_0     = x W_0 + b_0                                   (lift, per grid point)
     pre_l   = u_l W_l + b_l + K_l(u_l),  u_{l+1} = gelu(pre_l),   l < L
     K_l(u)  = Phi ( [Phi^T u]_modes  W_l,mode )            (spectral convolution)
-    r       = mean of u_L over the 2 x 2 top-layer grid points of each receiver
+    r       = mean of u_L over the 2 x 2 x 2 grid points of each receiver
     traces  = gelu(r W_1 + b_1) W_2 + b_2
 
 with Phi the orthonormal DCT-II basis truncated to m_x x m_y x m_z modes
@@ -73,7 +73,7 @@ def forward(p: dict, cfg: dict, x: np.ndarray):
     Px, Py, Pz = _bases(cfg)
     mx, my, mz = cfg["modes"]
     C = cfg["width"]
-    rx, ry = np.asarray(cfg["rx"]), np.asarray(cfg["ry"])
+    rx, ry, rz = np.asarray(cfg["rx"]), np.asarray(cfg["ry"]), np.asarray(cfg["rz"])
     u = x @ p["W0"] + p["b0"]
     us, pres, ss = [u], [], []
     for l in range(cfg["layers"]):
@@ -86,8 +86,11 @@ def forward(p: dict, cfg: dict, x: np.ndarray):
         us.append(u)
         pres.append(pre)
         ss.append(s)
-    top = u[:, :, :, -1, :]
-    r = 0.25 * (top[:, rx, ry] + top[:, rx + 1, ry] + top[:, rx, ry + 1] + top[:, rx + 1, ry + 1])
+    r = 0.0
+    for dx_ in (0, 1):
+        for dy_ in (0, 1):
+            for dz_ in (0, 1):
+                r = r + u[:, rx + dx_, ry + dy_, rz + dz_] / 8.0
     hpre = r @ p["W1"] + p["b1"]
     h = _gelu(hpre)
     y = h @ p["W2"] + p["b2"]
@@ -99,7 +102,7 @@ def backward(p: dict, cfg: dict, cache: dict, dy: np.ndarray) -> dict:
     Px, Py, Pz = _bases(cfg)
     mx, my, mz = cfg["modes"]
     C = cfg["width"]
-    rx, ry = np.asarray(cfg["rx"]), np.asarray(cfg["ry"])
+    rx, ry, rz = np.asarray(cfg["rx"]), np.asarray(cfg["ry"]), np.asarray(cfg["rz"])
     g = {}
     h, hpre, r = cache["h"], cache["hpre"], cache["r"]
     g["W2"] = np.einsum("brh,brt->ht", h, dy)
@@ -111,7 +114,8 @@ def backward(p: dict, cfg: dict, cache: dict, dy: np.ndarray) -> dict:
     du = np.zeros_like(cache["us"][-1])
     for dx_ in (0, 1):
         for dy_ in (0, 1):
-            np.add.at(du, (slice(None), rx + dx_, ry + dy_, -1), 0.25 * dr)
+            for dz_ in (0, 1):
+                np.add.at(du, (slice(None), rx + dx_, ry + dy_, rz + dz_), dr / 8.0)
     for l in reversed(range(cfg["layers"])):
         u, pre, s = cache["us"][l], cache["pres"][l], cache["ss"][l]
         dpre = du * _gelu_grad(pre)

@@ -59,6 +59,10 @@
 
 using bbw::fail;
 
+// warps per block of the c^2 gradient kernel
+constexpr int kGradWarps = 8;
+constexpr int kMaxMp = 20;
+
 struct AdjointData {
   // receivers: element, Bernstein basis values B_i(lambda(x_r)) [nrec][Np]
   // (sampling) and their dual vectors M^{-1} B(x_r) (adjoint injection)
@@ -87,6 +91,7 @@ struct AdjointData {
   void* d_invf = nullptr;
   void* d_gw = nullptr;
   int ngam = 0;
+  int32_t* d_split = nullptr;  // gamma ranges of the gradient kernel's warps [kGradWarps + 1]
   bool grad_ready = false;  // the gradient kernel's shared-memory attribute is set
   int nsm = 0;              // SMs of the device
   // adjoint state (internal layout [G][4][Np][V]): kap, rho, y; the recompute's
@@ -138,55 +143,68 @@ __global__ void receiver_adjoint_kernel(real* __restrict__ kap, const int64_t* _
   }
 }
 
-// gc[e][b] += dt sum_gamma G[gamma][b] sum_{(a, a') in pairs(gamma)} rho_p[e][a] / a! * v[e][a'] / a'!,
-// one warp per element (lanes over gamma); rho_p is field 0 of the internal
-// [G][4][Np][V] layout, v the internal pressure layout [G][Np][V]. With SMEM
-// the pair table, its row pointers and G are first copied into shared memory
-// (read once per block instead of once per element).
-constexpr int kAdjWarps = 8;
-constexpr int kMaxMp = 20;
+// gc[e][b] += dt sum_gamma G[gamma][b] sum_{(a, a') in pairs(gamma)} rho_p[e][a] / a! * v[e][a'] / a'!.
+// A block of kGradWarps warps takes 32 consecutive (internal) elements, one
+// per lane. The operands are staged once per block as [Np][32] columns; warp
+// q walks the gamma range [split.c[q], split.c[q + 1]) (ranges balanced by
+// pair count on the host), all its lanes in step over the same pair list, so
+// table words are broadcast loads and each lane reads only its own column
+// (no bank conflicts, no imbalance between lanes); split [kGradWarps + 1]
+// holds the ranges (device memory). The warps' partial sums
+// are added in warp order (deterministic). rho_p is field 0 of the internal
+// [G][4][Np][V] layout, v the pressure bracket [G][Np][V]. Pair words hold
+// (32 a) | (32 a') << 16, the operand offsets in the columns. With SMEM the
+// tables (G, pairs, row pointers; tab_bytes) are first copied into shared
+// memory, otherwise read from global memory (uniform loads).
 template <typename real, bool SMEM>
-__global__ void __launch_bounds__(32 * kAdjWarps) adj_grad_kernel(
+__global__ void __launch_bounds__(32 * kGradWarps) adj_grad_kernel(
     const real* __restrict__ rho, const real* __restrict__ v, real* __restrict__ gc, int64_t K, int Np, int Mp, int V,
     int ngam, const int32_t* __restrict__ gptr_g, const uint32_t* __restrict__ pairs_g, const real* __restrict__ invf,
-    const real* __restrict__ gw_g, real dt) {
+    const real* __restrict__ gw_g, real dt, int tab_bytes, const int32_t* __restrict__ split) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  real* sm = reinterpret_cast<real*>(sm_raw);
   const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
-  real* rs = sm + size_t(w) * 2 * Np;
-  real* vs = rs + Np;
   const int32_t* gptr = gptr_g;
   const uint32_t* pairs = pairs_g;
   const real* gw = gw_g;
   if constexpr (SMEM) {
-    const int np2 = Np * Np;
-    real* gws = sm + size_t(kAdjWarps) * 2 * Np;
+    real* gws = reinterpret_cast<real*>(sm_raw);
     uint32_t* ps = reinterpret_cast<uint32_t*>(gws + size_t(ngam) * Mp);
-    int32_t* gp = reinterpret_cast<int32_t*>(ps + np2);
+    int32_t* gp = reinterpret_cast<int32_t*>(ps + size_t(Np) * Np);
     for (int x = threadIdx.x; x < ngam * Mp; x += blockDim.x) gws[x] = gw_g[x];
-    for (int x = threadIdx.x; x < np2; x += blockDim.x) ps[x] = pairs_g[x];
+    for (int x = threadIdx.x; x < Np * Np; x += blockDim.x) ps[x] = pairs_g[x];
     for (int x = threadIdx.x; x <= ngam; x += blockDim.x) gp[x] = gptr_g[x];
-    __syncthreads();
     gptr = gp;
     pairs = ps;
     gw = gws;
   }
-  for (int64_t e = int64_t(blockIdx.x) * kAdjWarps + w; e < K; e += int64_t(gridDim.x) * kAdjWarps) {
-    const int64_t g = e / V;
-    const int l = int(e % V);
-    for (int i = lane; i < Np; i += 32) {
-      rs[i] = rho[(size_t(g) * 4 * Np + i) * V + l] * invf[i];
-      vs[i] = v[(size_t(g) * Np + i) * V + l] * invf[i];
+  real* rs0 = reinterpret_cast<real*>(sm_raw + tab_bytes);
+  real* vs0 = rs0 + size_t(Np) * 32;
+  real* part = vs0 + size_t(Np) * 32;  // [kGradWarps][Mp][32]
+  const real* rs = rs0 + lane;
+  const real* vs = vs0 + lane;
+  const int c_lo = split[w], c_hi = split[w + 1];
+  for (int64_t e0 = int64_t(blockIdx.x) * 32; e0 < K; e0 += int64_t(gridDim.x) * 32) {
+    {  // stage the 32 elements' operands, warp w taking rows w, w + 8, ...
+      const int64_t e = e0 + lane;
+      const bool ok = e < K;
+      const int64_t g = ok ? e / V : 0;
+      const int l = ok ? int(e % V) : 0;
+      for (int i = w; i < Np; i += kGradWarps) {
+        const real f = invf[i];
+        rs0[i * 32 + lane] = ok ? rho[(size_t(g) * 4 * Np + i) * V + l] * f : real(0);
+        vs0[i * 32 + lane] = ok ? v[(size_t(g) * Np + i) * V + l] * f : real(0);
+      }
     }
-    __syncwarp();
+    __syncthreads();
     real acc[kMaxMp];
 #pragma unroll
     for (int b = 0; b < kMaxMp; ++b) acc[b] = real(0);
-    for (int c = lane; c < ngam; c += 32) {
-      real wg = 0;
+    int p = gptr[c_lo];
+    for (int c = c_lo; c < c_hi; ++c) {
       const int p1 = gptr[c + 1];
+      real wg = 0;
 #pragma unroll 4
-      for (int p = gptr[c]; p < p1; ++p) {
+      for (; p < p1; ++p) {
         const uint32_t ab = pairs[p];
         wg += rs[ab & 0xffffu] * vs[ab >> 16];
       }
@@ -195,14 +213,16 @@ __global__ void __launch_bounds__(32 * kAdjWarps) adj_grad_kernel(
         if (b < Mp) acc[b] += wg * gw[size_t(c) * Mp + b];
     }
 #pragma unroll
-    for (int b = 0; b < kMaxMp; ++b) {
-      if (b >= Mp) break;
-      real x = acc[b];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      if (lane == 0) gc[size_t(e) * Mp + b] += dt * x;
+    for (int b = 0; b < kMaxMp; ++b)
+      if (b < Mp) part[(size_t(w) * Mp + b) * 32 + lane] = acc[b];
+    __syncthreads();
+    for (int x = threadIdx.x; x < Mp * 32; x += blockDim.x) {
+      const int b = x / 32, ln = x % 32;
+      real sum = 0;
+      for (int q = 0; q < kGradWarps; ++q) sum += part[(size_t(q) * Mp + b) * 32 + ln];
+      if (e0 + ln < K) gc[size_t(e0 + ln) * Mp + b] += dt * sum;
     }
-    __syncwarp();
+    __syncthreads();
   }
 }
 
@@ -240,7 +260,8 @@ bbw_status build_tables(bbw_solver* s, AdjointData* a) {
     for (int j = 0; j < Np; ++j) {
       std::array<int, 4> g;
       for (int x = 0; x < 4; ++x) g[x] = A[size_t(i)][x] + A[size_t(j)][x];
-      by[size_t(idx2n(g))].push_back(uint32_t(i) | (uint32_t(j) << 16));
+      // offsets of the two operands in the warp's staged [Np][32] columns
+      by[size_t(idx2n(g))].push_back(uint32_t(32 * i) | (uint32_t(32 * j) << 16));
     }
   std::vector<int32_t> gptr(size_t(ngam) + 1, 0);
   std::vector<uint32_t> pairs;
@@ -249,6 +270,22 @@ bbw_status build_tables(bbw_solver* s, AdjointData* a) {
     pairs.insert(pairs.end(), by[size_t(c)].begin(), by[size_t(c)].end());
   }
   gptr[size_t(ngam)] = int32_t(pairs.size());
+  // warp q takes the gammas whose cumulative cost (pairs + Mp weights) falls
+  // in its q-th share
+  {
+    std::vector<double> cum(size_t(ngam) + 1, 0.0);
+    for (int c = 0; c < ngam; ++c) cum[size_t(c) + 1] = cum[size_t(c)] + double(gptr[size_t(c) + 1] - gptr[size_t(c)] + Mp);
+    std::vector<int32_t> split(size_t(kGradWarps) + 1, 0);
+    int c = 0;
+    for (int q = 1; q < kGradWarps; ++q) {
+      const double target = cum[size_t(ngam)] * q / kGradWarps;
+      while (c < ngam && cum[size_t(c)] < target) ++c;
+      split[size_t(q)] = c;
+    }
+    split[size_t(kGradWarps)] = ngam;
+    BBW_CUDA(cudaMalloc(reinterpret_cast<void**>(&a->d_split), split.size() * sizeof(int32_t)));
+    BBW_CUDA(cudaMemcpy(a->d_split, split.data(), split.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  }
   const double cb = 6.0 * f(N) * f(N) * f(M) / f(2 * N + M + 3);
   std::vector<double> gw(size_t(ngam) * Mp);
   std::vector<double> invf(static_cast<size_t>(Np));
@@ -359,32 +396,36 @@ bbw_status adjoint_stage(bbw_solver* s, AdjointData* a, const void* vbr, int sta
   bbw::set_stage_sources<bbw::StageParams<real>, real>(s, P, 0, stage, false);
   BBW_CUDA(s->ops->launch_spatial(s->M, s->prec == 64, &P, s->grid_stage, st));
   // gc += dt rho_t,p^T T_beta v
-  const int threads = 32 * kAdjWarps;
-  const size_t shm = size_t(kAdjWarps) * 2 * s->Np * sizeof(real);
-  const size_t shm_tab = size_t(a->ngam) * s->Mp * sizeof(real) + size_t(s->Np) * s->Np * 4 + size_t(a->ngam + 1) * 4;
-  const bool in_smem = shm + shm_tab <= size_t(bbw::kSmemPerCta);
+  const size_t ops = (size_t(2) * s->Np + size_t(kGradWarps) * s->Mp) * 32 * sizeof(real);  // staged operands, partials
+  const size_t tab = (size_t(a->ngam) * s->Mp * sizeof(real) + size_t(s->Np) * s->Np * 4 + size_t(a->ngam + 1) * 4 +
+                      15) / 16 * 16;
+  const size_t cap = size_t(bbw::kSmemPerCta);
+  const bool in_smem = tab + ops <= cap;
+  const size_t bytes = (in_smem ? tab : 0) + ops;
+  if (bytes > cap) return fail(BBW_ERR_ARG, "adjoint gradient: staged operands exceed shared memory");
   if (!a->grad_ready) {
-    if (in_smem)
-      BBW_CUDA(cudaFuncSetAttribute(adj_grad_kernel<real, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    int(shm + shm_tab)));
+    BBW_CUDA(cudaFuncSetAttribute(adj_grad_kernel<real, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  int(cap)));
+    BBW_CUDA(cudaFuncSetAttribute(adj_grad_kernel<real, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  int(cap)));
     int dev = 0;
     BBW_CUDA(cudaGetDevice(&dev));
     BBW_CUDA(cudaDeviceGetAttribute(&a->nsm, cudaDevAttrMultiProcessorCount, dev));
     a->grad_ready = true;
   }
   // blocks per SM: as many as the shared memory holds (at most 8)
-  const int per_sm = in_smem ? int(std::max<size_t>(1, std::min<size_t>(8, size_t(bbw::kSmemPerCta) / (shm + shm_tab)))) : 8;
-  const int blocks = int(std::min<int64_t>((s->K + kAdjWarps - 1) / kAdjWarps, int64_t(std::max(a->nsm, 1)) * per_sm));
-  auto launch = [&](auto kern, size_t bytes) {
-    kern<<<blocks, threads, bytes, st>>>(static_cast<const real*>(a->rho), static_cast<const real*>(vbr),
-                                         static_cast<real*>(a->gc), s->K, s->Np, s->Mp, s->V, a->ngam, a->d_gptr,
-                                         a->d_pairs, static_cast<const real*>(a->d_invf),
-                                         static_cast<const real*>(a->d_gw), real(dt));
+  const int per_sm = int(std::max<size_t>(1, std::min<size_t>(8, cap / bytes)));
+  const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((s->K + 31) / 32, int64_t(std::max(a->nsm, 1)) * per_sm)));
+  auto launch = [&](auto kern) {
+    kern<<<blocks, 32 * kGradWarps, bytes, st>>>(
+        static_cast<const real*>(a->rho), static_cast<const real*>(vbr), static_cast<real*>(a->gc), s->K, s->Np, s->Mp,
+        s->V, a->ngam, a->d_gptr, a->d_pairs, static_cast<const real*>(a->d_invf), static_cast<const real*>(a->d_gw),
+        real(dt), in_smem ? int(tab) : 0, a->d_split);
   };
   if (in_smem)
-    launch(adj_grad_kernel<real, true>, shm + shm_tab);
+    launch(adj_grad_kernel<real, true>);
   else
-    launch(adj_grad_kernel<real, false>, shm);
+    launch(adj_grad_kernel<real, false>);
   BBW_CUDA(cudaGetLastError());
   return BBW_OK;
 }
@@ -550,7 +591,7 @@ void free_adjoint(bbw_solver* s) {
   free_run(a, true);
   for (void* p : {static_cast<void*>(a->d_rec_elem), a->d_rec_vec, a->d_rec_dual, static_cast<void*>(a->d_ue),
                   static_cast<void*>(a->d_rptr), static_cast<void*>(a->d_rlist), static_cast<void*>(a->d_gptr),
-                  static_cast<void*>(a->d_pairs), a->d_invf, a->d_gw, a->kap, a->rho, a->yi, a->qa[0], a->qa[1],
+                  static_cast<void*>(a->d_pairs), static_cast<void*>(a->d_split), a->d_invf, a->d_gw, a->kap, a->rho, a->yi, a->qa[0], a->qa[1],
                   a->rs, a->gc, static_cast<void*>(a->d_g)})
     if (p) cudaFree(p);
   delete a;

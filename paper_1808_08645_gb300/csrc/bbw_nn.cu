@@ -149,35 +149,70 @@ __global__ void bias_grad_kernel(const float* __restrict__ dY, float* __restrict
   atomicAdd(db + n, acc);
 }
 
-// out[b][r][c] = (1/4) sum of the 2 x 2 grid points around receiver r on the
-// top layer (z = Z - 1) of u [B][X][Y][Z][C]; rx, ry: the lower corner.
+// out[b][r][c] = (1/8) sum of the 2 x 2 x 2 grid points (rx[r] + {0,1},
+// ry[r] + {0,1}, rz[r] + {0,1}) of u [B][X][Y][Z][C]; a stencil that does not
+// lie inside the grid gives 0 (and is skipped by the transpose).
+__device__ __forceinline__ bool stencil_ok(int x, int y, int z, int X, int Y, int Z) {
+  return x >= 0 && y >= 0 && z >= 0 && x + 1 < X && y + 1 < Y && z + 1 < Z;
+}
+
 __global__ void gather_receivers_kernel(const float* __restrict__ u, float* __restrict__ out, const int* __restrict__ rx,
-                                        const int* __restrict__ ry, int B, int X, int Y, int Z, int C, int R) {
+                                        const int* __restrict__ ry, const int* __restrict__ rz, int B, int X, int Y,
+                                        int Z, int C, int R) {
   const long long n = (long long)B * R * C;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const int c = int(i % C);
     const int r = int((i / C) % R);
     const long long b = i / ((long long)C * R);
+    const int x0 = rx[r], y0 = ry[r], z0 = rz[r];
     float s = 0.f;
-    for (int dx = 0; dx < 2; ++dx)
-      for (int dy = 0; dy < 2; ++dy)
-        s += u[((((b * X + rx[r] + dx) * Y) + ry[r] + dy) * Z + (Z - 1)) * C + c];
-    out[i] = 0.25f * s;
+    if (stencil_ok(x0, y0, z0, X, Y, Z))
+      for (int dx = 0; dx < 2; ++dx)
+        for (int dy = 0; dy < 2; ++dy)
+          for (int dz = 0; dz < 2; ++dz) s += u[((((b * X + x0 + dx) * Y) + y0 + dy) * Z + z0 + dz) * C + c];
+    out[i] = 0.125f * s;
   }
 }
 
-// the transpose of gather_receivers (the receivers' 2 x 2 stencils are disjoint)
+// the transpose of gather_receivers (the receivers' stencils are disjoint)
 __global__ void scatter_receivers_kernel(const float* __restrict__ gout, float* __restrict__ du,
-                                         const int* __restrict__ rx, const int* __restrict__ ry, int B, int X, int Y,
-                                         int Z, int C, int R) {
+                                         const int* __restrict__ rx, const int* __restrict__ ry,
+                                         const int* __restrict__ rz, int B, int X, int Y, int Z, int C, int R) {
   const long long n = (long long)B * R * C;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const int c = int(i % C);
     const int r = int((i / C) % R);
     const long long b = i / ((long long)C * R);
+    const int x0 = rx[r], y0 = ry[r], z0 = rz[r];
+    if (!stencil_ok(x0, y0, z0, X, Y, Z)) continue;
     for (int dx = 0; dx < 2; ++dx)
       for (int dy = 0; dy < 2; ++dy)
-        du[((((b * X + rx[r] + dx) * Y) + ry[r] + dy) * Z + (Z - 1)) * C + c] += 0.25f * gout[i];
+        for (int dz = 0; dz < 2; ++dz)
+          du[((((b * X + x0 + dx) * Y) + y0 + dy) * Z + z0 + dz) * C + c] += 0.125f * gout[i];
+  }
+}
+
+// out[i][t] = scale[i] * in[i] at the fractional sample t + shift[i]: linear
+// interpolation between samples, the samples extended by zeros
+__global__ void shift_traces_kernel(const float* __restrict__ in, float* __restrict__ out,
+                                    const float* __restrict__ shift, const float* __restrict__ scale, long long rows,
+                                    int T) {
+  const long long n = rows * T;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long row = i / T;
+    const int t = int(i % T);
+    const float x = float(t) + shift[row];
+    const float f = floorf(x);
+    const float w = x - f;
+    float v = 0.f;
+    if (f >= 0.f && f <= float(T - 1)) {
+      const int j = int(f);
+      v = in[row * T + j] * (1.f - w);
+      if (j + 1 < T) v += in[row * T + j + 1] * w;
+    } else if (f == -1.f) {
+      v = in[row * T] * w;
+    }
+    out[i] = (scale ? scale[row] : 1.f) * v;
   }
 }
 
@@ -258,17 +293,28 @@ bbw_status bbw_nn_bias_grad(const float* dY, float* db, long long rows, int N, v
   return BBW_OK;
 }
 
-bbw_status bbw_nn_gather_receivers(const float* u, float* out, const int* rx, const int* ry, int B, int X, int Y,
-                                   int Z, int C, int R, int transpose, void* stream) {
-  if (B < 1 || X < 2 || Y < 2 || Z < 1 || C < 1 || R < 1 || !u || !out || !rx || !ry)
+bbw_status bbw_nn_gather_receivers(const float* u, float* out, const int* rx, const int* ry, const int* rz, int B,
+                                   int X, int Y, int Z, int C, int R, int transpose, void* stream) {
+  if (B < 1 || X < 2 || Y < 2 || Z < 2 || C < 1 || R < 1 || !u || !out || !rx || !ry || !rz)
     return nn_fail(BBW_ERR_ARG, "bad receiver-gather arguments");
   const long long n = (long long)B * R * C;
   if (transpose)
     scatter_receivers_kernel<<<grid_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        out, const_cast<float*>(u), rx, ry, B, X, Y, Z, C, R);
+        out, const_cast<float*>(u), rx, ry, rz, B, X, Y, Z, C, R);
   else
-    gather_receivers_kernel<<<grid_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(u, out, rx, ry, B, X, Y, Z,
-                                                                                        C, R);
+    gather_receivers_kernel<<<grid_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(u, out, rx, ry, rz, B, X, Y,
+                                                                                        Z, C, R);
+  NN_CUDA(cudaGetLastError());
+  return BBW_OK;
+}
+
+bbw_status bbw_nn_shift_traces(const float* in, float* out, const float* shift, const float* scale, long long rows,
+                               int T, void* stream) {
+  if (rows < 0 || T < 1 || (rows > 0 && (!in || !out || !shift)) || in == out)
+    return nn_fail(BBW_ERR_ARG, "bad trace-shift arguments");
+  if (rows == 0) return BBW_OK;
+  const long long n = rows * T;
+  shift_traces_kernel<<<grid_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(in, out, shift, scale, rows, T);
   NN_CUDA(cudaGetLastError());
   return BBW_OK;
 }

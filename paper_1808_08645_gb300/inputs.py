@@ -13,7 +13,8 @@ Recipes (the paper's GMSH meshes and media are not available):
     orientation code occurs.
   * Fields are turned into per-element coefficients by *sampling at domain
     points* x_alpha = sum_i alpha_i v_i / n of each element (the Bezier
-    control-point positions), which is a synthetic recipe, not a projection.
+    control-point positions), which is a synthetic recipe, not a projection;
+    the paper's L2 projection is ``project.py`` (host tools of the package).
 """
 from __future__ import annotations
 
@@ -27,7 +28,7 @@ __all__ = [
     "PARITY_CONFIG", "SWEEP_CONFIG", "BATCH_CONFIG", "batched_instances", "ADJOINT_CONFIG",
     "top_face_receivers", "ELASTIC_CONFIG", "elastic_media", "elastic_pulse",
     "ricker", "ricker_samples", "manufactured_forcing",
-    "SURROGATE_CONFIG", "surrogate_runs", "grid_centres", "surrogate_features",
+    "SURROGATE_CONFIG", "surrogate_runs", "surrogate_receivers", "grid_centres", "surrogate_features",
 ]
 
 #: the FP64 parity workload: 4^3 hexes x 6 = 384 tets, N=3, M=1, T=0.5
@@ -55,6 +56,15 @@ def top_face_receivers(n: int = ADJOINT_CONFIG["receivers"]) -> np.ndarray:
     x = (np.arange(n) + 0.5) / n
     X, Y = np.meshgrid(x, x, indexing="ij")
     return np.stack([X.ravel(), Y.ravel(), np.ones(n * n)], axis=1)
+
+
+def surrogate_receivers(n: int = 8, z: float = 0.9) -> np.ndarray:
+    """n x n receiver points at the cell centres of a uniform grid on the
+    plane at height z (below the p = 0 top wall, so that they record the
+    wave and not the wall's weak residual)."""
+    x = (np.arange(n) + 0.5) / n
+    X, Y = np.meshgrid(x, x, indexing="ij")
+    return np.stack([X.ravel(), Y.ravel(), np.full(n * n, float(z))], axis=1)
 
 
 def batched_instances(n: int = BATCH_CONFIG["instances"], seed: int = 0):
@@ -262,15 +272,18 @@ def manufactured_forcing(c2):
 
 
 #: the surrogate workload: BBWADG N = 4 runs on 16^3 x 6 tets (the adjoint's
-#: mesh) with 64 receivers on the top face, each run a seeded smooth random
-#: medium (the sweep's recipe with its layer jump, seed 5000 + run) and a
-#: Ricker source (peak frequency f0, delay t0) at a seeded position in the
-#: box [src_lo, src_hi]; traces of `steps` RK steps at the common CFL step of
-#: c^2 <= c2_max, every `every`-th kept (512 samples); the network sees c^2 on
-#: the centres of a grid^3 grid plus the source position
-SURROGATE_CONFIG = dict(runs=4096, test_runs=256, hexes=16, N=4, M=2, steps=512, every=1, f0=25.0, t0=0.04,
-                        src_lo=(0.25, 0.25, 0.55), src_hi=(0.75, 0.75, 0.85), grid=64, c2_max=3.0, cfl=0.5,
-                        sigma=0.05)
+#: mesh) with 64 receivers on the plane z = rec_z (``surrogate_receivers``),
+#: each run a seeded smooth random medium (the sweep's recipe with its layer
+#: jump, seed 5000 + run) and a Ricker source (peak frequency f0, delay t0) at
+#: a seeded position in the box [src_lo, src_hi] (above the layer jump);
+#: traces of `steps` RK steps at the common CFL step of c^2 <= c2_max, every
+#: `every`-th kept (512 samples over 0.37 time units, in which the direct
+#: wave reaches the receivers nearest the source); f0 = 12 keeps about 7
+#: nodes per wavelength at the median wave speed of that layer; the network
+#: sees c^2 on the centres of a grid^3 grid plus the source position
+SURROGATE_CONFIG = dict(runs=4096, test_runs=256, hexes=16, N=4, M=2, steps=1024, every=2, f0=12.0, t0=1.0 / 12.0,
+                        src_lo=(0.25, 0.25, 0.55), src_hi=(0.75, 0.75, 0.75), rec_z=0.9, grid=64, c2_max=3.0,
+                        cfl=0.5, sigma=0.05)
 
 
 def surrogate_runs(first: int, n: int, cfg: dict = SURROGATE_CONFIG):

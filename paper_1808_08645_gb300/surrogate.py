@@ -28,24 +28,26 @@ import torch
 
 from . import binding as B
 
-__all__ = ["Net", "default_config", "receiver_corners", "cosine_basis"]
+__all__ = ["Net", "default_config", "receiver_corners", "cosine_basis", "receiver_gain", "straight_ray_times",
+           "encode", "decode", "run_meta", "generate", "train", "predict", "relative_errors", "Surrogate"]
 
 
 def default_config(grid: int = 64, width: int = 32, modes=(6, 6, 6), layers: int = 4, cin: int = 6,
-                   hidden: int = 128, nt: int = 512, receivers: int = 8) -> dict:
-    rx, ry = receiver_corners(grid, receivers)
+                   hidden: int = 128, nt: int = 512, receivers: int = 8, rec_z: float = 0.9) -> dict:
+    rx, ry, rz = receiver_corners(grid, receivers, rec_z)
     return dict(grid=grid, width=width, modes=tuple(modes), layers=layers, cin=cin, hidden=hidden, nt=nt,
-                rx=rx, ry=ry)
+                rx=rx, ry=ry, rz=rz)
 
 
-def receiver_corners(grid: int, n: int):
-    """Lower grid corners of the 2 x 2 top-layer stencils of an n x n receiver
-    grid at the cell centres (i + 1/2)/n of the unit square (grid points at
-    (i + 1/2)/grid), x-major like ``inputs.top_face_receivers``."""
+def receiver_corners(grid: int, n: int, z: float):
+    """Lower grid corners of the 2 x 2 x 2 stencils around an n x n receiver
+    grid at the cell centres (i + 1/2)/n of the plane at height z (grid
+    points at (i + 1/2)/grid), x-major like ``inputs.surrogate_receivers``."""
     c = [int(math.floor(((i + 0.5) / n) * grid - 0.5)) for i in range(n)]
+    zc = min(max(int(math.floor(z * grid - 0.5)), 0), grid - 2)
     rx = [a for a in c for _ in c]
     ry = [b for _ in c for b in c]
-    return rx, ry
+    return rx, ry, [zc] * len(rx)
 
 
 def cosine_basis(n: int, m: int) -> np.ndarray:
@@ -85,6 +87,7 @@ class Net:
         self.phi = [torch.tensor(cosine_basis(G, m), **f32).contiguous() for m in (mx, my, mz)]
         self.rx = torch.tensor(cfg["rx"], dtype=torch.int32, device=self.dev)
         self.ry = torch.tensor(cfg["ry"], dtype=torch.int32, device=self.dev)
+        self.rz = torch.tensor(cfg["rz"], dtype=torch.int32, device=self.dev)
         if params is None:
             params = self.init_params(seed)
         self.p = {k: torch.tensor(np.asarray(v), **f32).contiguous() for k, v in params.items()}
@@ -165,7 +168,8 @@ class Net:
             cache[f"u{l + 1}"] = u
         r = torch.empty(nb * R, C, **e)
         B._check(B.lib().bbw_nn_gather_receivers(u.data_ptr(), r.data_ptr(), self.rx.data_ptr(), self.ry.data_ptr(),
-                                                 nb, G, G, G, C, R, 0, None), "bbw_nn_gather_receivers")
+                                                 self.rz.data_ptr(), nb, G, G, G, C, R, 0, None),
+                 "bbw_nn_gather_receivers")
         h = torch.empty(nb * R, H, **e)
         hpre = torch.empty(nb * R, H, **e)
         gemm(nb * R, H, C, r, C, 0, 0, self.p["W1"], H, 0, 0, h, H, 0, bias=self.p["b1"], pre=hpre, act=1)
@@ -200,7 +204,7 @@ class Net:
         gemm(nb * R, C, H, dh, H, 0, 0, self.p["W1"], H, 0, 1, dr, C, 0)
         du = torch.zeros(P, C, **e)
         B._check(B.lib().bbw_nn_gather_receivers(du.data_ptr(), dr.data_ptr(), self.rx.data_ptr(),
-                                                 self.ry.data_ptr(), nb, G, G, G, C, R, 1, None),
+                                                 self.ry.data_ptr(), self.rz.data_ptr(), nb, G, G, G, C, R, 1, None),
                  "bbw_nn_gather_receivers")
         for l in reversed(range(L)):
             u = cache[f"u{l}"]
@@ -257,12 +261,68 @@ class Net:
 # data, training, evaluation and the BBWADG fallback
 
 
+def receiver_gain(sources, rec, d_ref: float = 0.25) -> np.ndarray:
+    """[n, R] gains d_ref / |x_r - x_s| of the traces (the 1/r spreading of a
+    point source in 3D). The network is trained on the traces divided by
+    them, so near and far receivers and sources weigh alike, and its output
+    is multiplied by them."""
+    s = np.asarray(sources, dtype=np.float64).reshape(-1, 1, 3)
+    r = np.asarray(rec, dtype=np.float64).reshape(1, -1, 3)
+    return d_ref / np.linalg.norm(r - s, axis=2)
+
+
+def straight_ray_times(c2_field, sources, rec, nseg: int = 32) -> np.ndarray:
+    """[n, R] travel times along the straight segments from each source to
+    each receiver through the medium, int ds / c (midpoint rule, nseg
+    pieces). By Fermat's principle the first arrival comes no later; in the
+    smooth layer the sources sit in, the difference is second order."""
+    xs = np.asarray(sources, dtype=np.float64).reshape(-1, 1, 1, 3)
+    xr = np.asarray(rec, dtype=np.float64).reshape(1, -1, 1, 3)
+    u = ((np.arange(nseg) + 0.5) / nseg).reshape(1, 1, -1, 1)
+    pts = xs + u * (xr - xs)
+    c = np.sqrt(np.asarray(c2_field(pts.reshape(-1, 3)), dtype=np.float64)).reshape(pts.shape[:3])
+    length = np.linalg.norm(xr - xs, axis=3)[..., 0]
+    return length * np.mean(1.0 / c, axis=2)
+
+
+def _shift(Y, shift, scale):
+    out = torch.empty_like(Y)
+    rows = Y.numel() // Y.shape[-1]
+    B._check(B.lib().bbw_nn_shift_traces(Y.data_ptr(), out.data_ptr(), shift.data_ptr(), _ptr(scale), rows,
+                                         Y.shape[-1], None), "bbw_nn_shift_traces")
+    return out
+
+
+def encode(Y, meta: dict):
+    """Network targets from traces Y [n, R, T]: every trace moved earlier by its
+    straight-ray travel time (in samples) and divided by its receiver gain, so
+    that the direct arrival sits at the wavelet's own delay and near and far
+    receivers weigh alike."""
+    return _shift(Y.contiguous(), meta["shift"], 1.0 / meta["gain"])
+
+
+def decode(A, meta: dict):
+    """Traces from network outputs A [n, R, T] (the inverse of ``encode`` where
+    the traces are known: samples past the end of the recorded window were
+    zero-filled by ``encode``)."""
+    return _shift(A.contiguous(), -meta["shift"], meta["gain"])
+
+
+def run_meta(dcfg: dict, runs, c2_fields, rec, dt: float, device: str = "cuda") -> dict:
+    """Receiver gains and straight-ray shifts (samples) [n, R] of the runs."""
+    gain = receiver_gain([r["source"] for r in runs], rec)
+    tau = np.stack([straight_ray_times(f, [r["source"]], rec)[0] for r, f in zip(runs, c2_fields)])
+    f32 = dict(dtype=torch.float32, device=device)
+    return dict(gain=torch.tensor(gain, **f32).contiguous(),
+                shift=torch.tensor(tau / (dt * dcfg["every"]), **f32).contiguous())
+
+
 def _bbwadg_setup(dcfg: dict):
     """Mesh, receivers, the common time step (CFL of c^2 <= c2_max) and the
     source amplitude samples of the surrogate workload."""
     from . import inputs
     vxyz, etov = inputs.cube_mesh(dcfg["hexes"])
-    rec = inputs.top_face_receivers()
+    rec = inputs.surrogate_receivers(z=dcfg["rec_z"])
     probe = B.Solver(vxyz, etov, dcfg["N"], dcfg["M"], B.F32)
     probe.set_c2(np.full((len(etov), (dcfg["M"] + 1) * (dcfg["M"] + 2) * (dcfg["M"] + 3) // 6), dcfg["c2_max"]))
     dt = probe.cfl_dt(dcfg["cfl"])
@@ -271,21 +331,31 @@ def _bbwadg_setup(dcfg: dict):
     return vxyz, etov, rec, dt, amp
 
 
-def bbwadg_traces(solver, vxyz, etov, dcfg, run, dt, amp):
-    """Receiver traces [R, T] of one run with a prepared solver (BBWADG, FP32)."""
+def bbwadg_traces(solver, vxyz, etov, dcfg, run, dt, amp, timings: list | None = None):
+    """Receiver traces [R, T] of one run with a prepared solver (BBWADG, FP32);
+    timings (if given) receives the seconds of the time integration alone."""
+    import time
+
     from . import inputs
     field = inputs.c2_smooth_random(run["c2_seed"])
     solver.set_c2(inputs.sample_at_domain_points(vxyz, etov, dcfg["M"], field))
     solver.set_state(np.zeros((4, len(etov), (dcfg["N"] + 1) * (dcfg["N"] + 2) * (dcfg["N"] + 3) // 6)))
     solver.set_point_source(run["source"], amp)
+    if timings is not None:
+        solver.sync()
+        t = time.perf_counter()
     tr = solver.record(dt, dcfg["steps"], dcfg["steps"])
+    if timings is not None:
+        timings.append(time.perf_counter() - t)
     return np.ascontiguousarray(tr[dcfg["every"] - 1::dcfg["every"]].T)
 
 
 def generate(dcfg: dict, first: int, n: int, threads: int = 8, device: str = "cuda"):
-    """(X [n, G, G, G, 6], Y [n, R, T]) on the device for runs first ..
+    """(X [n, G, G, G, 6], Y [n, R, T], meta) on the device for runs first ..
     first + n - 1: each target is a BBWADG run (solvers on `threads` streams
-    run concurrently), each input the run's c^2 on the grid plus its source."""
+    run concurrently), each input the run's c^2 on the grid plus its source;
+    meta holds dt, the runs and their receiver gains and shifts [n, R]
+    (``run_meta``, used by ``encode`` / ``decode``)."""
     import concurrent.futures as cf
     import threading
 
@@ -319,14 +389,15 @@ def generate(dcfg: dict, first: int, n: int, threads: int = 8, device: str = "cu
             Y[j].copy_(torch.from_numpy(tr.astype(np.float32)))
             X[j].copy_(torch.from_numpy(ft))
     torch.cuda.synchronize()
-    return X, Y, dict(dt=dt, runs=runs)
+    meta = run_meta(dcfg, runs, [inputs.c2_smooth_random(r["c2_seed"]) for r in runs], rec, dt, device)
+    return X, Y, dict(meta, dt=dt, runs=runs)
 
 
 def train(net: Net, X, Y, iters: int, batch: int = 8, lr: float = 1e-3, seed: int = 0, scale: float = 1.0,
           log_every: int = 0):
-    """Adam on the mean squared error of scaled traces Y / scale, random
-    batches; the learning rate decays by a cosine to lr / 20. Returns the
-    per-iteration losses (host floats, read every log_every iterations)."""
+    """Adam on the mean squared error of the targets Y / scale (Y: ``encode``d
+    traces), random batches; the learning rate decays by a cosine to lr / 20.
+    Returns the losses (host floats, read every log_every iterations)."""
     rng = np.random.default_rng(seed)
     n = X.shape[0]
     losses = []
@@ -344,13 +415,15 @@ def train(net: Net, X, Y, iters: int, batch: int = 8, lr: float = 1e-3, seed: in
     return losses
 
 
-def predict(net: Net, X, scale: float, batch: int = 8):
-    """Network traces [n, R, T] (physical units) for inputs X."""
+def predict(net: Net, X, scale: float, meta: dict | None = None, batch: int = 8):
+    """Network outputs [n, R, T] for inputs X, times scale; with the runs'
+    meta (``generate``), decoded to traces."""
     out = []
     for k in range(0, X.shape[0], batch):
         y, _ = net.forward(X[k:k + batch].contiguous())
         out.append(y * scale)
-    return torch.cat(out)
+    out = torch.cat(out)
+    return out if meta is None else decode(out, meta)
 
 
 def relative_errors(pred, Y) -> np.ndarray:
@@ -369,9 +442,9 @@ class Surrogate:
     trace error) is at least the calibrated quantile; otherwise the run is
     solved by BBWADG."""
 
-    def __init__(self, net: Net, dcfg: dict, scale: float, calib_err: float, c2_range):
+    def __init__(self, net: Net, dcfg: dict, scale: float, calib_err: float, c2_range, dt: float):
         self.net, self.dcfg, self.scale, self.err = net, dict(dcfg), scale, float(calib_err)
-        self.c2_range = c2_range
+        self.c2_range, self.dt = c2_range, float(dt)
         self._bbw = None
 
     def _in_domain(self, run, feat) -> bool:
@@ -388,7 +461,9 @@ class Surrogate:
         if self._in_domain(run, feat) and (tol is None or tol >= self.err):
             x = torch.from_numpy(feat[None]).to(self.net.dev)
             y, _ = self.net.forward(x)
-            return (y[0] * self.scale).double().cpu().numpy(), "surrogate", self.err
+            rec = inputs.surrogate_receivers(z=self.dcfg["rec_z"])
+            meta = run_meta(self.dcfg, [run], [field], rec, self.dt, device=str(self.net.dev))
+            return decode(y * self.scale, meta)[0].double().cpu().numpy(), "surrogate", self.err
         if self._bbw is None:
             vxyz, etov, rec, dt, amp = _bbwadg_setup(self.dcfg)
             s = B.Solver(vxyz, etov, self.dcfg["N"], self.dcfg["M"], B.F32)

@@ -70,6 +70,31 @@ def test_forward_and_gradients_match_the_reference_network():
         assert rel_l2(g[k].double().cpu().numpy(), g_ref[k]) <= TOL, k
 
 
+def test_shift_traces_kernel():
+    """bbw_nn_shift_traces against numpy's linear interpolation of the
+    zero-extended samples, fractional shifts of both signs and beyond the
+    window; integer shifts there and back restore the overlapping samples."""
+    from paper_1808_08645_gb300 import surrogate as S
+    rng = np.random.default_rng(9)
+    rows, T = 37, 29
+    Y = rng.standard_normal((rows, T))
+    sh = np.concatenate([rng.uniform(-40, 40, rows - 5), [0.0, -0.5, 28.7, -28.3, 3.0]])
+    sc = rng.uniform(0.5, 2.0, rows)
+    xp = np.arange(-1, T + 1)
+    want = np.stack([sc[i] * np.interp(np.arange(T) + sh[i], xp, np.concatenate([[0.0], Y[i], [0.0]]),
+                                       left=0.0, right=0.0) for i in range(rows)])
+    f32 = dict(dtype=torch.float32, device="cuda")
+    meta = dict(shift=torch.tensor(sh, **f32), gain=torch.tensor(1.0 / sc, **f32))
+    got = S.encode(torch.tensor(Y, **f32), meta).double().cpu().numpy()
+    assert np.allclose(got, want, atol=1e-5)
+    ish = np.round(sh)
+    meta = dict(shift=torch.tensor(ish, **f32), gain=torch.tensor(1.0 / sc, **f32))
+    back = S.decode(S.encode(torch.tensor(Y, **f32), meta), meta).double().cpu().numpy()
+    for i in range(rows):
+        keep = (np.arange(T) - ish[i] >= 0) & (np.arange(T) - ish[i] < T)
+        assert np.allclose(back[i][keep], Y[i][keep], atol=1e-5)
+
+
 def test_mse_and_adam_kernels():
     from paper_1808_08645_gb300 import surrogate as S
     cfg = _cfg()
@@ -99,21 +124,43 @@ def test_mse_and_adam_kernels():
         assert np.allclose(net.p[k].double().cpu().numpy(), p0[k], atol=2e-6), k
 
 
-def test_training_reduces_the_loss_on_a_fixed_batch():
+def test_training_follows_the_reference_adam_trajectory():
+    """120 Adam steps on a fixed batch: the GPU loss follows the FP64
+    reference network trained by the same Adam update (within 10 % over the
+    first 90 steps, BF16 operands) and falls below a quarter of its start."""
     from paper_1808_08645_gb300 import surrogate as S
     cfg = _cfg()
-    net = S.Net(cfg, seed=4)
+    p0 = fno.init_params(cfg, seed=4)
     rng = np.random.default_rng(5)
-    x = torch.tensor(rng.standard_normal((2, 8, 8, 8, 6)), dtype=torch.float32, device="cuda")
-    t = torch.tensor(rng.standard_normal((2, len(cfg["rx"]), cfg["nt"])), dtype=torch.float32, device="cuda")
-    first = None
-    for _ in range(60):
+    xn = rng.standard_normal((2, 8, 8, 8, 6))
+    tn = rng.standard_normal((2, len(cfg["rx"]), cfg["nt"]))
+    # the reference: FP64 network, Adam in the efficient form of Kingma & Ba
+    p = {k: v.copy() for k, v in p0.items()}
+    m = {k: np.zeros_like(v) for k, v in p.items()}
+    v2 = {k: np.zeros_like(v) for k, v in p.items()}
+    ref = []
+    for it in range(120):
+        y, c = fno.forward(p, cfg, xn)
+        d = y - tn
+        ref.append(np.mean(d ** 2))
+        g = fno.backward(p, cfg, c, 2 * d / d.size)
+        for k in p:
+            m[k] = 0.9 * m[k] + 0.1 * g[k]
+            v2[k] = 0.999 * v2[k] + 0.001 * g[k] ** 2
+            p[k] -= 3e-3 * np.sqrt(1 - 0.999 ** (it + 1)) / (1 - 0.9 ** (it + 1)) * m[k] / (np.sqrt(v2[k]) + 1e-8)
+    net = S.Net(cfg, params=p0)
+    x = torch.tensor(xn, dtype=torch.float32, device="cuda")
+    t = torch.tensor(tn, dtype=torch.float32, device="cuda")
+    got = []
+    for _ in range(120):
         y, c = net.forward(x)
         lo, dy = net.loss(y, t)
+        got.append(float(lo))
         net.backward(c, dy)
         net.adam(lr=3e-3)
-        first = float(lo) if first is None else first
-    assert float(lo) < 0.5 * first
+    for it in (0, 30, 60, 90):
+        assert abs(got[it] - ref[it]) <= 0.1 * ref[it], (it, got[it], ref[it])
+    assert got[-1] < 0.25 * got[0]
 
 
 def test_small_pipeline_generate_train_judge_and_fall_back():
@@ -125,19 +172,24 @@ def test_small_pipeline_generate_train_judge_and_fall_back():
     from paper_1808_08645_gb300 import surrogate as S
     dcfg = dict(inputs.SURROGATE_CONFIG, hexes=3, N=2, steps=48, grid=16)
     X, Y, meta = S.generate(dcfg, 0, 24, threads=4)
-    Xt, Yt, _ = S.generate(dcfg, 24, 6, threads=2)
+    Xt, Yt, mt = S.generate(dcfg, 24, 6, threads=2)
     assert torch.isfinite(Y).all() and float(Y.abs().max()) > 0
-    scale = float(Y.std())
-    net = S.Net(S.default_config(grid=16, width=8, modes=(3, 3, 3), layers=2, hidden=16, nt=Y.shape[2]), seed=1)
+    assert meta["gain"].shape == (24, 64) and float(meta["gain"].min()) > 0
+    assert meta["shift"].shape == (24, 64) and float(meta["shift"].min()) > 0
+    A = S.encode(Y, meta)
+    scale = float(A.std())
+    net = S.Net(S.default_config(grid=16, width=8, modes=(3, 3, 3), layers=2, hidden=16, nt=Y.shape[2],
+                                 rec_z=dcfg["rec_z"]), seed=1)
+
     def train_mse():
-        return float(((S.predict(net, X, scale) - Y) ** 2).mean())
+        return float(((S.predict(net, X, scale) - A) ** 2).mean())
 
     m0 = train_mse()
-    S.train(net, X, Y, 300, scale=scale, lr=1e-2)
+    S.train(net, X, A, 300, scale=scale, lr=1e-2)
     assert train_mse() < 0.7 * m0  # it learns its training runs
-    e1 = S.relative_errors(S.predict(net, Xt, scale), Yt)  # held out (far too few runs here to generalise)
+    e1 = S.relative_errors(S.predict(net, Xt, scale, mt), Yt)  # held out (far too few runs here to generalise)
     assert np.isfinite(e1).all()
-    sur = S.Surrogate(net, dcfg, scale, float(np.quantile(e1, 0.95)), (0.4, 3.5))
+    sur = S.Surrogate(net, dcfg, scale, float(np.quantile(e1, 0.95)), (0.4, 3.5), meta["dt"])
     run = inputs.surrogate_runs(24, 1, dcfg)[0]
     out_run = dict(run, source=np.array([0.5, 0.5, 0.3]))
     tr, used, _ = sur.predict(out_run)

@@ -6,7 +6,7 @@ import pytest
 
 from oracle import fno
 
-CFG = dict(grid=6, width=3, modes=(2, 3, 2), layers=2, cin=4, hidden=5, nt=4, rx=[0, 3], ry=[1, 2])
+CFG = dict(grid=6, width=3, modes=(2, 3, 2), layers=2, cin=4, hidden=5, nt=4, rx=[0, 3], ry=[1, 2], rz=[4, 1])
 
 
 def test_cosine_basis_is_orthonormal():
@@ -50,9 +50,9 @@ def test_zero_spectral_weights_give_the_pointwise_network():
     for l in range(CFG["layers"]):
         v = u @ p[f"W{l}_pw"] + p[f"b{l}_pw"]
         u = 0.5 * v * (1 + np.vectorize(__import__("math").erf)(v / np.sqrt(2)))
-    top = u[:, :, :, -1]
-    rx, ry = np.array(CFG["rx"]), np.array(CFG["ry"])
-    r = 0.25 * (top[:, rx, ry] + top[:, rx + 1, ry] + top[:, rx, ry + 1] + top[:, rx + 1, ry + 1])
+    # receiver r: the mean over its 2 x 2 x 2 block, written as a block average
+    r = np.stack([u[:, x0:x0 + 2, y0:y0 + 2, z0:z0 + 2].mean(axis=(1, 2, 3))
+                  for x0, y0, z0 in zip(CFG["rx"], CFG["ry"], CFG["rz"])], axis=1)
     hp = r @ p["W1"] + p["b1"]
     h = 0.5 * hp * (1 + np.vectorize(__import__("math").erf)(hp / np.sqrt(2)))
     assert np.allclose(y, h @ p["W2"] + p["b2"], atol=1e-13)
