@@ -315,6 +315,13 @@ bbw_status bbw_set_receivers(bbw_solver* s, int64_t nrec, const double* xyz, int
  * write the receiver traces after every step to traces [nsteps][nrec] (host,
  * may be NULL). The run is kept for bbw_adjoint until the next bbw_record or
  * bbw_set_receivers. Waits for the device.
+ *   checkpoint_every >= 1: memory nsteps / checkpoint_every states; the
+ *   adjoint recomputes each segment once (plus 5 checkpoint_every pressure
+ *   fields). checkpoint_every = 0: no checkpoints; the pressure bracket of
+ *   every stage is kept instead (5 nsteps pressure fields of K N_p values in
+ *   the solver's precision), so the adjoint recomputes nothing; BBW_ERR_ARG
+ *   (with the sizes) if the device lacks the memory. Both give bitwise equal
+ *   gradients.
  */
 bbw_status bbw_record(bbw_solver* s, double dt, int64_t nsteps, int64_t checkpoint_every, double* traces);
 
@@ -395,6 +402,30 @@ bbw_status bbw_batch_clear_sources(bbw_batch* b);
 
 /* The smallest CFL time step over the instances (rule of bbw_cfl_dt). */
 bbw_status bbw_batch_cfl_dt(const bbw_batch* b, double cfl, double* dt);
+
+/* The CFL time step of instance i alone (rule of bbw_cfl_dt). */
+bbw_status bbw_batch_member_cfl_dt(const bbw_batch* b, int i, double cfl, double* dt);
+
+/*
+ * Per-instance time steps and step budgets. dt [n] (NULL: every instance
+ * steps with the dt passed to bbw_batch_step) gives instance i its own step
+ * dt[i]; nsteps [n] (NULL: no budgets) stops instance i after nsteps[i] steps
+ * counted from the last bbw_batch_set_time: from then on its state is carried
+ * over unchanged (its groups cost one copy per stage) while the others go on.
+ * All instances still take the batch's steps together, so amplitude sample
+ * 5 n + s of a source is used at stage s of the batch's n-th step: sample
+ * each instance's wavelet at its own stage times (t + (n + c_s) dt[i]). With
+ * dt[i] the instance's CFL step (bbw_batch_member_cfl_dt) and
+ * nsteps[i] = ceil(T / dt[i]), every instance reaches time T with the
+ * steps it needs instead of those of the smallest CFL step of the batch.
+ * Each instance evolves bitwise as its solo solver does with that dt.
+ * Waits for the batch stream. Errors: BBW_ERR_ARG for a non-finite or
+ * negative dt or a negative budget.
+ */
+bbw_status bbw_batch_set_instance_steps(bbw_batch* b, const double* dt, const int64_t* nsteps);
+
+/* Time and steps taken of instance i (its own dt and budget). */
+bbw_status bbw_batch_instance_time(const bbw_batch* b, int i, double* t, int64_t* steps);
 
 /* Set the common time and reset the step counter (amplitude sample 0 comes next). */
 bbw_status bbw_batch_set_time(bbw_batch* b, double t);

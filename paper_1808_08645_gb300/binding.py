@@ -81,6 +81,9 @@ EXPORTS = {
     "bbw_batch_set_point_source": (_int, [_p, _int, _dp, _dp, _i64, _i64p]),
     "bbw_batch_clear_sources": (_int, [_p]),
     "bbw_batch_cfl_dt": (_int, [_p, _d, _dp]),
+    "bbw_batch_member_cfl_dt": (_int, [_p, _int, _d, _dp]),
+    "bbw_batch_set_instance_steps": (_int, [_p, _dp, _i64p]),
+    "bbw_batch_instance_time": (_int, [_p, _int, _dp, _i64p]),
     "bbw_batch_set_time": (_int, [_p, _d]),
     "bbw_batch_step": (_int, [_p, _d, _i64, _int]),
     "bbw_batch_autotune": (_int, [_p, _int, _ip, _dp]),
@@ -373,7 +376,8 @@ class Solver:
         return el
 
     def record(self, dt: float, nsteps: int, checkpoint_every: int = 1):
-        """Run nsteps steps keeping checkpoints; returns the traces [nsteps][nrec].
+        """Run nsteps steps keeping checkpoints (checkpoint_every = 0: every
+        stage's pressure bracket instead); returns the traces [nsteps][nrec].
         ``runs`` counts the recorded runs of this solver (bbw_adjoint
         differentiates the latest one)."""
         tr = np.empty((nsteps, getattr(self, "nrec", 0)))
@@ -497,6 +501,26 @@ class Batch:
         dt = C.c_double()
         _check(lib().bbw_batch_cfl_dt(self._h, cfl, C.byref(dt)), "bbw_batch_cfl_dt")
         return dt.value
+
+    def member_cfl_dt(self, i: int, cfl: float) -> float:
+        dt = C.c_double()
+        _check(lib().bbw_batch_member_cfl_dt(self._h, i, cfl, C.byref(dt)), "bbw_batch_member_cfl_dt")
+        return dt.value
+
+    def set_instance_steps(self, dt=None, nsteps=None):
+        """Per-instance time steps dt [n] and step budgets nsteps [n] (None:
+        the common dt of ``step`` / no budget)."""
+        d = None if dt is None else _f64(dt)
+        k = None if nsteps is None else np.ascontiguousarray(nsteps, dtype=np.int64)
+        _check(lib().bbw_batch_set_instance_steps(self._h, None if d is None else _ptr(d, C.c_double),
+                                                  None if k is None else _ptr(k, C.c_int64)),
+               "bbw_batch_set_instance_steps")
+
+    def instance_time(self, i: int):
+        t = C.c_double()
+        n = C.c_int64()
+        _check(lib().bbw_batch_instance_time(self._h, i, C.byref(t), C.byref(n)), "bbw_batch_instance_time")
+        return t.value, n.value
 
     def set_time(self, t: float):
         _check(lib().bbw_batch_set_time(self._h, t), "bbw_batch_set_time")

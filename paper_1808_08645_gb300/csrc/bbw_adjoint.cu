@@ -435,11 +435,31 @@ bbw_status record(bbw_solver* s, double dt, int64_t nsteps, int64_t every, doubl
   AdjointData* a = adj_of(s);
   free_run(a);
   const size_t bytes = s->nstate_internal() * sizeof(real);
+  const size_t pbytes = size_t(s->G) * s->V * s->Np * sizeof(real);  // one pressure field, internal layout
   a->dt = dt;
   a->nsteps = nsteps;
   a->every = every;
   a->k_step.assign(size_t(nsteps), 0);
-  const int64_t nck = std::max<int64_t>((nsteps + every - 1) / every, 1);
+  // every == 0: keep the pressure bracket of every stage of the run instead
+  // of checkpoints (the adjoint then recomputes nothing); otherwise release
+  // a bracket buffer larger than the adjoint's segments need
+  const size_t need_brk = every == 0 ? size_t(nsteps) * 5 * pbytes : size_t(every) * 5 * pbytes;
+  if (a->brk && (every == 0 ? a->brk_bytes < need_brk : a->brk_bytes > 2 * need_brk)) {
+    cudaFree(a->brk);
+    a->brk = nullptr;
+    a->brk_bytes = 0;
+  }
+  if (every == 0 && !a->brk) {
+    size_t free_b = 0, total_b = 0;
+    BBW_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    if (need_brk > free_b)
+      return fail(BBW_ERR_ARG, "keeping every stage's pressure bracket needs " + std::to_string(need_brk >> 20) +
+                                   " MiB of device memory, " + std::to_string(free_b >> 20) +
+                                   " MiB are free: use checkpoint_every >= 1");
+    BBW_CUDA(cudaMalloc(&a->brk, need_brk));
+    a->brk_bytes = need_brk;
+  }
+  const int64_t nck = every == 0 ? 0 : std::max<int64_t>((nsteps + every - 1) / every, 1);
   while (int64_t(a->ckpt.size()) > nck) {  // keep the buffers of earlier runs, drop extras
     if (a->ckpt.back()) cudaFree(a->ckpt.back());
     a->ckpt.pop_back();
@@ -452,10 +472,19 @@ bbw_status record(bbw_solver* s, double dt, int64_t nsteps, int64_t every, doubl
   if (a->nrec > 0) BBW_CUDA(cudaMalloc(&a->d_traces, size_t(nsteps) * a->nrec * sizeof(double)));
   const int threads = 128;
   for (int64_t n = 0; n < nsteps; ++n) {
-    if (n % every == 0)
+    if (every > 0 && n % every == 0)
       BBW_CUDA(cudaMemcpyAsync(a->ckpt[size_t(n / every)], s->q[s->cur], bytes, cudaMemcpyDeviceToDevice, s->stream));
     a->k_step[size_t(n)] = s->steps;
-    bbw_status st = bbw_step(s, dt, 1);
+    bbw_status st = BBW_OK;
+    if (every == 0) {
+      for (int sg = 0; sg < 5 && st == BBW_OK; ++sg) {
+        s->vout = static_cast<char*>(a->brk) + size_t(n * 5 + sg) * pbytes;
+        st = bbw_stage(s, sg, dt);
+      }
+      s->vout = nullptr;
+    } else {
+      st = bbw_step(s, dt, 1);
+    }
     if (st != BBW_OK) return st;
     if (a->nrec > 0)
       sample_kernel<real><<<int((a->nrec * 32 + threads - 1) / threads), threads, 0, s->stream>>>(
@@ -487,7 +516,7 @@ bbw_status adjoint(bbw_solver* s, const double* g, double* grad_c2, double* grad
   }
   st = dalloc(&a->gc, size_t(K) * Mp * sizeof(real));
   if (st != BBW_OK) return st;
-  const size_t need = size_t(a->every) * 5 * pbytes;
+  const size_t need = size_t(a->every) * 5 * pbytes;  // 0 when the recorded run kept every bracket
   if (a->brk_bytes < need) {
     if (a->brk) cudaFree(a->brk);
     a->brk = nullptr;
@@ -508,19 +537,22 @@ bbw_status adjoint(bbw_solver* s, const double* g, double* grad_c2, double* grad
   BBW_CUDA(cudaMemsetAsync(a->gc, 0, size_t(K) * Mp * sizeof(real), sm));
   auto bracket = [&](int64_t i) { return static_cast<void*>(static_cast<char*>(a->brk) + size_t(i) * pbytes); };
   const double dt = a->dt;
-  const int64_t nseg = int64_t(a->ckpt.size());
+  const bool kept = a->every == 0;  // the recorded run kept every bracket: one segment, nothing recomputed
+  const int64_t nseg = kept ? 1 : int64_t(a->ckpt.size());
   for (int64_t k = nseg - 1; k >= 0; --k) {
-    const int64_t n0 = k * a->every, n1 = std::min(a->nsteps, n0 + a->every);
-    // recompute the segment from its checkpoint, keeping every stage's bracket
-    BBW_CUDA(cudaMemcpyAsync(a->qa[0], a->ckpt[size_t(k)], bytes, cudaMemcpyDeviceToDevice, sm));
-    int cur = 0;
-    for (int64_t n = n0; n < n1; ++n)
-      for (int sg = 0; sg < 5; ++sg) {
-        st = forward_stage<real>(s, a->qa[cur], a->qa[1 - cur], a->rs, sg, dt, a->k_step[size_t(n)],
-                                 bracket((n - n0) * 5 + sg));
-        if (st != BBW_OK) return st;
-        cur = 1 - cur;
-      }
+    const int64_t n0 = kept ? 0 : k * a->every, n1 = kept ? a->nsteps : std::min(a->nsteps, n0 + a->every);
+    if (!kept) {
+      // recompute the segment from its checkpoint, keeping every stage's bracket
+      BBW_CUDA(cudaMemcpyAsync(a->qa[0], a->ckpt[size_t(k)], bytes, cudaMemcpyDeviceToDevice, sm));
+      int cur = 0;
+      for (int64_t n = n0; n < n1; ++n)
+        for (int sg = 0; sg < 5; ++sg) {
+          st = forward_stage<real>(s, a->qa[cur], a->qa[1 - cur], a->rs, sg, dt, a->k_step[size_t(n)],
+                                   bracket((n - n0) * 5 + sg));
+          if (st != BBW_OK) return st;
+          cur = 1 - cur;
+        }
+    }
     for (int64_t n = n1 - 1; n >= n0; --n) {
       // cotangent of the traces after step n
       if (a->d_g) {
@@ -688,7 +720,8 @@ bbw_status bbw_set_receivers(bbw_solver* s, int64_t nrec, const double* xyz, int
 
 bbw_status bbw_record(bbw_solver* s, double dt, int64_t nsteps, int64_t checkpoint_every, double* traces) {
   if (!s) return fail(BBW_ERR_ARG, "solver is NULL");
-  if (nsteps < 1 || checkpoint_every < 1) return fail(BBW_ERR_ARG, "nsteps and checkpoint_every must be >= 1");
+  if (nsteps < 1 || checkpoint_every < 0)
+    return fail(BBW_ERR_ARG, "nsteps must be >= 1 and checkpoint_every >= 0");
   if (!std::isfinite(dt)) return fail(BBW_ERR_ARG, "dt is not finite");
   return s->prec == 64 ? record<double>(s, dt, nsteps, checkpoint_every, traces)
                        : record<float>(s, dt, nsteps, checkpoint_every, traces);

@@ -502,6 +502,7 @@ bbw_status launch_stage(bbw_solver* s, int stage, double dt) {
   P.tau_u = real(s->tau_u);
   bbw::set_stage_sources<bbw::StageParams<real>, real>(s, P, s->steps, stage, true);
   P.status = s->d_status;
+  P.vout = static_cast<real*>(s->vout);
   BBW_CUDA(s->ops->launch_stage(s->M, s->prec == 64, &P, s->grid_stage, s->stream));
   s->cur = 1 - s->cur;
   s->stages += 1;

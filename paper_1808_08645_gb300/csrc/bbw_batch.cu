@@ -64,6 +64,8 @@ struct bbw_batch {
     std::vector<int64_t> src_elem;       // per member slot: element of its source or -1
     std::vector<std::vector<double>> amp;  // per member slot: its amplitude samples
     int grid0 = 1;                       // persistent grid of the solo solver (CTAs)
+    void* d_dtg = nullptr;               // [G] per-group dt (per-instance time steps) or NULL
+    int64_t* d_stepsg = nullptr;         // [G] per-group step budget or NULL
   };
   int n = 0, M = 0, prec = 32;
   cudaStream_t stream = nullptr;
@@ -83,6 +85,12 @@ struct bbw_batch {
   bool serial = false;
   double grid_factor = 1.0;
   int schedule = 0;
+  // per-instance time steps and step budgets (bbw_batch_set_instance_steps;
+  // empty: the common dt, no budget) and the instances' own times
+  std::vector<double> inst_dt;
+  std::vector<int64_t> inst_steps;
+  std::vector<double> inst_t;
+  bool trial = false;  // autotuner trial steps: per-group dt off (dt = 0)
 };
 
 namespace {
@@ -96,7 +104,8 @@ void free_batch(bbw_batch* b) {
     if (k.side) cudaStreamDestroy(k.side);
     if (k.done) cudaEventDestroy(k.done);
     for (void* p : {static_cast<void*>(k.d_groups), static_cast<void*>(k.d_slots), k.d_vec,
-                    static_cast<void*>(k.d_ser), static_cast<void*>(k.d_amp)})
+                    static_cast<void*>(k.d_ser), static_cast<void*>(k.d_amp), k.d_dtg,
+                    static_cast<void*>(k.d_stepsg)})
       if (p) cudaFree(p);
   }
   if (b->fork) cudaEventDestroy(b->fork);
@@ -152,6 +161,10 @@ bbw_status launch_bucket_step(bbw_batch* b, bbw_batch::Bucket& k, double dt, cud
     P.step_host = 0;
     P.stage = stage;
     P.status = s->d_status;
+    // autotuner trials step with dt = 0 (no per-group dt) but keep the
+    // budgets, so that finished instances stay untouched (residual included)
+    if (!b->trial) P.dt_group = static_cast<const real*>(k.d_dtg);
+    P.steps_group = k.d_stepsg;
     BBW_CUDA(s->ops->launch_stage(s->M, s->prec == 64, &P, s->grid_stage, st));
     cur = 1 - cur;
   }
@@ -339,6 +352,7 @@ bbw_status bbw_batch_create(int n, const int64_t* nverts, const double* const* v
     b->own_stream = true;
   }
   b->members.resize(size_t(n));
+  b->inst_t.assign(size_t(n), 0.0);
   std::map<int, std::vector<int>> by_degree;
   for (int i = 0; i < n; ++i) by_degree[N[i]].push_back(i);
   auto bail = [&](bbw_status st) {
@@ -552,11 +566,13 @@ bbw_status bbw_batch_clear_sources(bbw_batch* b) {
   return BBW_OK;
 }
 
-bbw_status bbw_batch_cfl_dt(const bbw_batch* b, double cfl, double* dt) {
-  if (!b || !dt) return fail(BBW_ERR_ARG, "NULL argument");
+bbw_status bbw_batch_member_cfl_dt(const bbw_batch* b, int i, double cfl, double* dt) {
+  bbw_status st = check_member(b, i);
+  if (st != BBW_OK) return st;
+  if (!dt) return fail(BBW_ERR_ARG, "NULL argument");
   if (!(cfl > 0.0)) return fail(BBW_ERR_ARG, "cfl must be > 0");
   double best = INFINITY;
-  for (int i = 0; i < b->n; ++i) {
+  {
     const auto& m = b->members[size_t(i)];
     const bbw_solver* s = b->buckets[size_t(m.bucket)].s;
     double cmax = 0.0, ratio = 0.0;
@@ -570,6 +586,79 @@ bbw_status bbw_batch_cfl_dt(const bbw_batch* b, double cfl, double* dt) {
     best = std::min(best, cfl / (std::sqrt(cmax) * cn * ratio));
   }
   *dt = best;
+  return BBW_OK;
+}
+
+bbw_status bbw_batch_cfl_dt(const bbw_batch* b, double cfl, double* dt) {
+  if (!b || !dt) return fail(BBW_ERR_ARG, "NULL argument");
+  if (!(cfl > 0.0)) return fail(BBW_ERR_ARG, "cfl must be > 0");
+  double best = INFINITY;
+  for (int i = 0; i < b->n; ++i) {
+    double d = 0.0;
+    bbw_status st = bbw_batch_member_cfl_dt(b, i, cfl, &d);
+    if (st != BBW_OK) return st;
+    best = std::min(best, d);
+  }
+  *dt = best;
+  return BBW_OK;
+}
+
+bbw_status bbw_batch_set_instance_steps(bbw_batch* b, const double* dt, const int64_t* nsteps) {
+  if (!b) return fail(BBW_ERR_ARG, "batch is NULL");
+  for (int i = 0; i < b->n; ++i) {
+    if (dt && !(std::isfinite(dt[i]) && dt[i] >= 0.0)) return fail(BBW_ERR_ARG, "instance dt must be finite and >= 0");
+    if (nsteps && nsteps[i] < 0) return fail(BBW_ERR_ARG, "instance step budget must be >= 0");
+  }
+  BBW_CUDA(cudaStreamSynchronize(b->stream));
+  if (dt)
+    b->inst_dt.assign(dt, dt + b->n);
+  else
+    b->inst_dt.clear();
+  if (nsteps)
+    b->inst_steps.assign(nsteps, nsteps + b->n);
+  else
+    b->inst_steps.clear();
+  for (auto& k : b->buckets) {
+    bbw_solver* s = k.s;
+    const size_t esz = b->prec == 64 ? sizeof(double) : sizeof(float);
+    if (k.d_dtg) cudaFree(k.d_dtg);
+    if (k.d_stepsg) cudaFree(k.d_stepsg);
+    k.d_dtg = nullptr;
+    k.d_stepsg = nullptr;
+    // groups of no member (none exist: members tile the bucket) stay inert: dt 0, budget 0
+    std::vector<double> gdt(size_t(s->G), 0.0);
+    std::vector<int64_t> gst(size_t(s->G), 0);
+    for (int i : k.members) {
+      const auto& m = b->members[size_t(i)];
+      for (int64_t g = m.e0 / s->V; g < (m.e0 + m.K + s->V - 1) / s->V; ++g) {
+        if (dt) gdt[size_t(g)] = dt[i];
+        if (nsteps) gst[size_t(g)] = nsteps[i];
+      }
+    }
+    if (dt) {
+      BBW_CUDA(cudaMalloc(&k.d_dtg, size_t(s->G) * esz));
+      if (b->prec == 64) {
+        BBW_CUDA(cudaMemcpy(k.d_dtg, gdt.data(), gdt.size() * esz, cudaMemcpyHostToDevice));
+      } else {
+        std::vector<float> f(gdt.begin(), gdt.end());
+        BBW_CUDA(cudaMemcpy(k.d_dtg, f.data(), f.size() * esz, cudaMemcpyHostToDevice));
+      }
+    }
+    if (nsteps) {
+      BBW_CUDA(cudaMalloc(reinterpret_cast<void**>(&k.d_stepsg), size_t(s->G) * sizeof(int64_t)));
+      BBW_CUDA(cudaMemcpy(k.d_stepsg, gst.data(), gst.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+    }
+  }
+  invalidate_graphs(b);
+  return BBW_OK;
+}
+
+bbw_status bbw_batch_instance_time(const bbw_batch* b, int i, double* t, int64_t* steps) {
+  bbw_status st = check_member(b, i);
+  if (st != BBW_OK) return st;
+  if (t) *t = b->inst_t[size_t(i)];
+  if (steps)
+    *steps = b->inst_steps.empty() ? b->steps : std::min(b->steps, b->inst_steps[size_t(i)]);
   return BBW_OK;
 }
 
@@ -595,6 +684,10 @@ bbw_status bbw_batch_step(bbw_batch* b, double dt, int64_t nsteps, int use_graph
       k.s->stages += 5;
       k.s->t += dt;
     }
+    if (!b->trial)
+      for (int i = 0; i < b->n; ++i)
+        if (b->inst_steps.empty() || b->steps < b->inst_steps[size_t(i)])
+          b->inst_t[size_t(i)] += b->inst_dt.empty() ? dt : b->inst_dt[size_t(i)];
     b->t += dt;
     b->steps += 1;
   }
@@ -625,6 +718,7 @@ bbw_status bbw_batch_autotune(bbw_batch* b, int steps, int* schedule, double* ms
   // are while the kernels do their full work
   const double saved_t = b->t;
   const int64_t saved_steps = b->steps;
+  b->trial = true;
   float best = INFINITY;
   int best_c = 0;
   bbw_status st = BBW_OK;
@@ -645,6 +739,7 @@ bbw_status bbw_batch_autotune(bbw_batch* b, int steps, int* schedule, double* ms
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  b->trial = false;
   apply(st == BBW_OK ? best_c : 0);
   b->t = saved_t;
   b->steps = saved_steps;
@@ -675,6 +770,7 @@ bbw_status bbw_batch_set_time(bbw_batch* b, double t) {
   BBW_CUDA(cudaMemcpy(b->d_step, &zero, sizeof(int64_t), cudaMemcpyHostToDevice));
   b->t = t;
   b->steps = 0;
+  std::fill(b->inst_t.begin(), b->inst_t.end(), t);
   for (auto& k : b->buckets) {
     k.s->t = t;
     k.s->stages = 0;

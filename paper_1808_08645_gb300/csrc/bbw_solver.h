@@ -83,6 +83,7 @@ struct bbw_solver {
   int64_t steps = 0;  // completed RK steps since the last set_state: amplitude sample 5 steps + stage
   double tau_p = 1.0, tau_u = 1.0;
   AdjointData* adj = nullptr;  // receivers, recorded run, adjoint buffers (bbw_adjoint.cu)
+  void* vout = nullptr;        // if set, the next stage also stores its pressure bracket there (bbw_record)
   // element renumbering for locality: internal slot e holds the caller's
   // element perm[e], inv[perm[e]] = e (empty / NULL: the identity)
   std::vector<int32_t> perm, inv;

@@ -84,6 +84,12 @@ struct StageParams {
   // spatial-only kernel: 0 writes the right-hand side to qout; 1 accumulates
   // qout -= dt |D| rhs into all four fields (|D| the element volume).
   int accumulate = 0;
+  // per-group time steps (batches whose instances step with their own dt):
+  // if set, group g uses dt_group[g] instead of dt; if steps_group is set, a
+  // group whose step budget is used up (step >= steps_group[g], step as for
+  // the sources) is left as it is: q_out = q_in, res untouched.
+  const real* __restrict__ dt_group = nullptr;     // [G]
+  const int64_t* __restrict__ steps_group = nullptr;  // [G]
 };
 
 // One stage of the discrete adjoint before its spatial operator, in the
@@ -577,8 +583,17 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
     js = lo;
   }
   int next_src = js < nsg ? int(P.src_groups[js]) : INT32_MAX;
+  const int64_t step_now = P.step_dev ? *P.step_dev : P.step_host;
 
   for (int64_t g = int64_t(blockIdx.x) * GC + team; g < G; g += stride) {
+    if (P.steps_group && step_now >= P.steps_group[g]) {
+      // the group's instance has taken its steps: carry its state over
+      const real* qg = P.qin + size_t(g) * QV * V;
+      real* og = P.qout + size_t(g) * QV * V;
+      for (int idx = t; idx < QV; idx += T) vst(og + size_t(idx) * V, vld<real, V>(qg + size_t(idx) * V));
+      continue;
+    }
+    const real dtg = P.dt_group ? P.dt_group[g] : P.dt;
     // the team's next group into L2
     if (t == 0 && g + stride < G) {
       const size_t qb = size_t(QV) * V * sizeof(real);
@@ -644,7 +659,7 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
           const real b1 = gm[2][0].get(v), b2 = gm[2][1].get(v), b3 = gm[2][2].get(v);
           const real c1 = gm[3][0].get(v), c2v = gm[3][1].get(v), c3 = gm[3][2].get(v);
           const real det = a1 * (b2 * c3 - b3 * c2v) - a2 * (b1 * c3 - b3 * c1) + a3 * (b1 * c2v - b2 * c1);
-          dtvol.set(v, P.dt / (real(6) * det));
+          dtvol.set(v, dtg / (real(6) * det));
         }
       }
     }
@@ -886,7 +901,7 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
                 vst(o, rhs[c]);
               }
             } else {
-              vt rn = vmuls(P.dt, rhs[c]);
+              vt rn = vmuls(dtg, rhs[c]);
               vfmas(rn, P.a, rold[r][c]);
               vst(resg + size_t((1 + c) * Np + i) * V, rn);
               const vt qn = vaxpy(vld<real, V>(Q + ((1 + c) * Np + i) * V), P.b, rn);
@@ -968,7 +983,7 @@ __global__ void __launch_bounds__(T* GC) stage_kernel(const StageParams<real> P)
       for (int r = 0; r < C::RMAX; ++r) {
         const int i = t + r * T;
         if (i < Np) {
-          vt rn = vmuls(P.dt, lv[0][r]);
+          vt rn = vmuls(dtg, lv[0][r]);
           vfmas(rn, P.a, rold[r]);
           vst(resg + size_t(i) * V, rn);
           const vt qn = vaxpy(vld<real, V>(Q + i * V), P.b, rn);
@@ -1068,18 +1083,30 @@ __global__ void __launch_bounds__(T* GC) adj_pre_kernel(const AdjPreParams<real>
       IV[t] = real(6) * (a1 * (b2 * c3 - b3 * c2v) - a2 * (b1 * c3 - b3 * c1) + a3 * (b1 * c2v - b2 * c1));
     }
     for (int idx = t; idx < Mp * V; idx += T) C2S[idx] = P.c2[size_t(g) * Mp * V + idx];
-    team_sync<T>();
-    real* rg = P.rho + size_t(g) * BLK;
-    const real* kg = P.kap + size_t(g) * BLK;
-    real* yg = P.y + size_t(g) * BLK;
-    for (int idx = t; idx < BLK; idx += T) {
-      const real r = P.a * rg[idx] + P.b * kg[idx];
-      rg[idx] = r;
-      const int i = (idx / V) % Np;
-      if (idx < Np * V)
-        A[idx] = r * tab.invfactN[i];
-      else
-        yg[idx] = r * IV[idx % V];
+    real* __restrict__ rg = P.rho + size_t(g) * BLK;
+    const real* __restrict__ kg = P.kap + size_t(g) * BLK;
+    real* __restrict__ yg = P.y + size_t(g) * BLK;
+    // rho_t = a rho + b kap in vectors of V elements: all of a lane's NV
+    // vector loads are issued before its stores
+    constexpr int NV = (4 * Np + T - 1) / T;
+    vt rv[NV];
+#pragma unroll
+    for (int r = 0; r < NV; ++r) {
+      const int j = t + r * T;
+      if (j < 4 * Np) rv[r] = vaxpy(vmuls(P.b, vld<real, V>(kg + size_t(j) * V)), P.a, vld<real, V>(rg + size_t(j) * V));
+    }
+    team_sync<T>();  // IV and C2S are ready
+    const vt iv0 = vld<real, V>(IV);
+#pragma unroll
+    for (int r = 0; r < NV; ++r) {
+      const int j = t + r * T;
+      if (j < 4 * Np) {
+        vst(rg + size_t(j) * V, rv[r]);
+        if (j < Np)
+          vst(A + j * V, vmuls(tab.invfactN[j], rv[r]));
+        else
+          vst(yg + size_t(j) * V, vmul(rv[r], iv0));
+      }
     }
     if (t == 0) vst(A + Np * V, vzero<real, V>());
     vt bh[Mp];

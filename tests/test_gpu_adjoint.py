@@ -61,14 +61,21 @@ def test_gradient_matches_oracle_adjoint(N, M, prec, tol):
 
 
 def test_checkpoint_spacing_does_not_change_the_gradient():
+    """Checkpoint spacings 1, 3, 7 and 0 (every stage's bracket kept, no
+    recomputation; then a checkpointed run on the same solver, which must
+    not reuse the kept brackets) give bitwise equal gradients."""
     N, M = 3, 2
     vxyz, etov, c2, q0, rng = _case(2, N, M, 32, seed=5)
     g = rng.standard_normal((7, len(XR)))
     out = []
-    for every in (1, 3, 7):
+    for every in (1, 3, 7, 0):
         s = _gpu(vxyz, etov, N, M, 32, c2, q0)
         s.record(2e-3, 7, checkpoint_every=every)
         out.append(s.adjoint(g, want_q0=True))
+        if every == 0:
+            s.set_state(q0)
+            s.record(2e-3, 7, checkpoint_every=2)
+            out.append(s.adjoint(g, want_q0=True))
         s.close()
     for gc, gq in out[1:]:
         assert np.array_equal(gc, out[0][0]) and np.array_equal(gq, out[0][1])

@@ -180,3 +180,37 @@ def test_autotune_keeps_state_and_results():
         assert np.array_equal(b.get_state(i), s.get_state()[0]), i
         s.close()
     b.close()
+
+
+@pytest.mark.parametrize("prec,graph", [(32, True), (64, False)])
+def test_per_instance_dt_and_step_budgets_match_solo_runs(prec, graph):
+    """Each instance steps with its own dt (half its CFL step) and stops after
+    its own step budget; it then equals its solo solver run with that dt for
+    that many steps, bitwise (state and residual), while the batch goes on;
+    an autotuner pass in between leaves all of that unchanged."""
+    insts = _instances(prec, seed=3)
+    b = _batch(insts, prec)
+    n = len(insts)
+    dts = np.array([0.5 * b.member_cfl_dt(i, 0.5) for i in range(n)])
+    assert np.isclose(dts.min(), 0.5 * b.cfl_dt(0.5), rtol=0, atol=0)
+    budgets = np.array([2 + i % 3 for i in range(n)], dtype=np.int64)
+    b.set_instance_steps(dts, budgets)
+    b.step(1.0, 2, graph=graph)  # the common dt is not used
+    b.autotune(1)
+    b.step(1.0, int(budgets.max()) + 1 - 2, graph=graph)
+    b.sync()
+    for i, d in enumerate(insts):
+        t, steps = b.instance_time(i)
+        assert steps == budgets[i] and abs(t - budgets[i] * dts[i]) <= 1e-12 * t
+        s = _solo(d, prec)
+        s.step(float(dts[i]), int(budgets[i]))
+        qs, rs, _ = s.get_state(with_res=True)
+        qb, rb = b.get_state(i, with_res=True)
+        assert np.array_equal(qb, qs), (i, rel_l2(qb, qs))
+        assert np.array_equal(rb, rs), (i, rel_l2(rb, rs))
+        s.close()
+    with pytest.raises(B.BBWError):
+        b.set_instance_steps(np.full(n, np.nan))
+    with pytest.raises(B.BBWError):
+        b.set_instance_steps(None, np.full(n, -1))
+    b.close()
