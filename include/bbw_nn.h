@@ -37,6 +37,18 @@ bbw_status bbw_nn_gemm(int M, int N, int K, const float* A, int lda, long long s
                        int ldb, long long strideB, int transB, float* C, int ldc, long long strideC, int batch,
                        float alpha, float beta, const float* bias, float* pre, int act, int splits, void* stream);
 
+/*
+ * Transform along the innermost spatial axis of `pencils` pencils with C
+ * contiguous channels, by basis [L][m] (m <= 16, L m floats <= 48 KB), in
+ * FP32. expand = 0 contracts: in [pencils][L][C] -> out [pencils][m][C],
+ * out[k] = sum_z basis[z][k] in[z] (beta, pre, act must be 0 / NULL).
+ * expand = 1 expands: in [pencils][m][C] -> out [pencils][L][C],
+ * v = sum_k basis[z][k] in[k] + beta out[z], pre[z] = v (pre may be NULL),
+ * out[z] = act ? GELU(v) : v (act 0 or 1). in and out must not overlap.
+ */
+bbw_status bbw_nn_axis_transform(const float* basis, int L, int m, const float* in, float* out, long long pencils,
+                                 int C, int expand, float beta, float* pre, int act, void* stream);
+
 /* grad[i] *= GELU'(pre[i]) for i < n (the backward of the GELU epilogue). */
 bbw_status bbw_nn_gelu_backward(const float* pre, float* grad, long long n, void* stream);
 

@@ -108,6 +108,7 @@ EXPORTS = {
     "bbw_nn_gemm": (_int, [_int, _int, _int, _p, _int, C.c_longlong, _int, _p, _int, C.c_longlong, _int, _p, _int,
                            C.c_longlong, _int, C.c_float, C.c_float, _p, _p, _int, _int, _p]),
     "bbw_nn_gelu_backward": (_int, [_p, _p, C.c_longlong, _p]),
+    "bbw_nn_axis_transform": (_int, [_p, _int, _int, _p, _p, C.c_longlong, _int, _int, C.c_float, _p, _int, _p]),
     "bbw_nn_bias_grad": (_int, [_p, _p, C.c_longlong, _int, _p]),
     "bbw_nn_gather_receivers": (_int, [_p, _p, _p, _p, _p, _int, _int, _int, _int, _int, _int, _int, _p]),
     "bbw_nn_shift_traces": (_int, [_p, _p, _p, _p, C.c_longlong, _int, _p]),

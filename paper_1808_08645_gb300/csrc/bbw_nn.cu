@@ -43,6 +43,164 @@ __device__ __forceinline__ float gelu_grad(float x) {
   return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
 }
 
+// Tile loaders: each thread holds its share of one op(A) tile (BM x BK, 16
+// values) and one op(B) tile (BK x BN, 8 values) in registers, so that the
+// next tile's global loads are in flight while the current one is multiplied.
+// VEC: 16-byte loads along the operand's contiguous dimension (the caller
+// guarantees a leading dimension, batch stride and base aligned to 4
+// floats); ragged edges fall back to guarded scalar loads.
+template <bool VEC>
+__device__ __forceinline__ void load_a(float (&r)[16], const float* __restrict__ A, int lda, int transA, int M,
+                                       int m0, int k0, int kend, int tid) {
+  if constexpr (VEC) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int idx = tid + q * THREADS;  // 512 quads
+      const int mm = transA ? (idx % 16) * 4 : idx / 8;
+      const int kk = transA ? idx / 16 : (idx % 8) * 4;
+      const int gm = m0 + mm, gk = k0 + kk;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (!transA) {
+        if (gm < M && gk + 3 < kend) {
+          v = *reinterpret_cast<const float4*>(A + (long long)gm * lda + gk);
+        } else if (gm < M) {
+          const float* p = A + (long long)gm * lda;
+          v.x = gk < kend ? p[gk] : 0.f;
+          v.y = gk + 1 < kend ? p[gk + 1] : 0.f;
+          v.z = gk + 2 < kend ? p[gk + 2] : 0.f;
+          v.w = gk + 3 < kend ? p[gk + 3] : 0.f;
+        }
+      } else if (gk < kend) {
+        const float* p = A + (long long)gk * lda;
+        if (gm + 3 < M) {
+          v = *reinterpret_cast<const float4*>(p + gm);
+        } else {
+          v.x = gm < M ? p[gm] : 0.f;
+          v.y = gm + 1 < M ? p[gm + 1] : 0.f;
+          v.z = gm + 2 < M ? p[gm + 2] : 0.f;
+          v.w = gm + 3 < M ? p[gm + 3] : 0.f;
+        }
+      }
+      r[4 * q] = v.x;
+      r[4 * q + 1] = v.y;
+      r[4 * q + 2] = v.z;
+      r[4 * q + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int x = tid + q * THREADS;
+      const int mm = transA ? x % BM : x / BK, kk = transA ? x / BM : x % BK;
+      const int gm = m0 + mm, gk = k0 + kk;
+      float v = 0.f;
+      if (gm < M && gk < kend) v = transA ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk];
+      r[q] = v;
+    }
+  }
+}
+
+template <bool VEC>
+__device__ __forceinline__ void store_a(const float (&r)[16], __nv_bfloat16 (*As)[BK + 8], int transA, int tid) {
+  if constexpr (VEC) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int idx = tid + q * THREADS;
+      const int mm = transA ? (idx % 16) * 4 : idx / 8;
+      const int kk = transA ? idx / 16 : (idx % 8) * 4;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (transA)
+          As[mm + i][kk] = __float2bfloat16_rn(r[4 * q + i]);
+        else
+          As[mm][kk + i] = __float2bfloat16_rn(r[4 * q + i]);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int x = tid + q * THREADS;
+      const int mm = transA ? x % BM : x / BK, kk = transA ? x / BM : x % BK;
+      As[mm][kk] = __float2bfloat16_rn(r[q]);
+    }
+  }
+}
+
+template <bool VEC>
+__device__ __forceinline__ void load_b(float (&r)[8], const float* __restrict__ B, int ldb, int transB, int N, int n0,
+                                       int k0, int kend, int tid) {
+  if constexpr (VEC) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int idx = tid + q * THREADS;  // 256 quads
+      const int nn = transB ? idx / 8 : (idx % 8) * 4;
+      const int kk = transB ? (idx % 8) * 4 : idx / 8;
+      const int gn = n0 + nn, gk = k0 + kk;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (transB) {
+        if (gn < N && gk + 3 < kend) {
+          v = *reinterpret_cast<const float4*>(B + (long long)gn * ldb + gk);
+        } else if (gn < N) {
+          const float* p = B + (long long)gn * ldb;
+          v.x = gk < kend ? p[gk] : 0.f;
+          v.y = gk + 1 < kend ? p[gk + 1] : 0.f;
+          v.z = gk + 2 < kend ? p[gk + 2] : 0.f;
+          v.w = gk + 3 < kend ? p[gk + 3] : 0.f;
+        }
+      } else if (gk < kend) {
+        const float* p = B + (long long)gk * ldb;
+        if (gn + 3 < N) {
+          v = *reinterpret_cast<const float4*>(p + gn);
+        } else {
+          v.x = gn < N ? p[gn] : 0.f;
+          v.y = gn + 1 < N ? p[gn + 1] : 0.f;
+          v.z = gn + 2 < N ? p[gn + 2] : 0.f;
+          v.w = gn + 3 < N ? p[gn + 3] : 0.f;
+        }
+      }
+      r[4 * q] = v.x;
+      r[4 * q + 1] = v.y;
+      r[4 * q + 2] = v.z;
+      r[4 * q + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int x = tid + q * THREADS;
+      const int nn = transB ? x / BK : x % BN, kk = transB ? x % BK : x / BN;
+      const int gn = n0 + nn, gk = k0 + kk;
+      float v = 0.f;
+      if (gn < N && gk < kend) v = transB ? B[(long long)gn * ldb + gk] : B[(long long)gk * ldb + gn];
+      r[q] = v;
+    }
+  }
+}
+
+template <bool VEC>
+__device__ __forceinline__ void store_b(const float (&r)[8], __nv_bfloat16 (*Bt)[BK + 8], int transB, int tid) {
+  if constexpr (VEC) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int idx = tid + q * THREADS;
+      const int nn = transB ? idx / 8 : (idx % 8) * 4;
+      const int kk = transB ? (idx % 8) * 4 : idx / 8;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (transB)
+          Bt[nn][kk + i] = __float2bfloat16_rn(r[4 * q + i]);
+        else
+          Bt[nn + i][kk] = __float2bfloat16_rn(r[4 * q + i]);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int x = tid + q * THREADS;
+      const int nn = transB ? x / BK : x % BN, kk = transB ? x % BK : x / BN;
+      Bt[nn][kk] = __float2bfloat16_rn(r[q]);
+    }
+  }
+}
+
 // C = alpha op(A) op(B) + beta C (+ bias[n]); op(A) is M x K, op(B) is K x N.
 // A row-major M x K (lda) or, transposed, stored K x M; B row-major K x N
 // (ldb) or, transposed, stored N x K. Batch b (blockIdx.z / splits) offsets
@@ -50,8 +208,10 @@ __device__ __forceinline__ float gelu_grad(float x) {
 // among blockIdx.z % splits and the partial products are atomically added
 // to C (beta and the bias must then be applied by the caller).
 // Epilogue (splits == 1): pre (if set) receives the value before the
-// activation; act = 1 applies GELU.
-__global__ void __launch_bounds__(THREADS) gemm_bf16_kernel(const float* __restrict__ A, const float* __restrict__ B,
+// activation; act = 1 applies GELU. VA / VB: 16-byte loads of A / B; VC:
+// 8-byte stores of column pairs of C and pre (ldc, sC even, 8-byte bases).
+template <bool VA, bool VB, bool VC>
+__global__ void __launch_bounds__(THREADS, 4) gemm_bf16_kernel(const float* __restrict__ A, const float* __restrict__ B,
                                                            float* __restrict__ C, const float* __restrict__ bias,
                                                            float* __restrict__ pre, int M, int N, int K, int lda,
                                                            int ldb, int ldc, long long sA, long long sB,
@@ -71,23 +231,19 @@ __global__ void __launch_bounds__(THREADS) gemm_bf16_kernel(const float* __restr
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int g = lane >> 2, tg = lane & 3;
   float acc[4][4] = {};  // 4 n8 tiles x (c0..c3)
+  float ra[16], rb[8];
+  if (kbeg < kend) {
+    load_a<VA>(ra, A, lda, transA, M, m0, kbeg, kend, tid);
+    load_b<VB>(rb, B, ldb, transB, N, n0, kbeg, kend, tid);
+  }
   for (int k0 = kbeg; k0 < kend; k0 += BK) {
-    // stage A tile [BM][BK] and B tile [BN][BK] as BF16
-    for (int x = tid; x < BM * BK; x += THREADS) {
-      const int mm = transA ? x % BM : x / BK, kk = transA ? x / BM : x % BK;
-      const int gm = m0 + mm, gk = k0 + kk;
-      float v = 0.f;
-      if (gm < M && gk < kend) v = transA ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk];
-      As[mm][kk] = __float2bfloat16_rn(v);
-    }
-    for (int x = tid; x < BN * BK; x += THREADS) {
-      const int nn = transB ? x / BK : x % BN, kk = transB ? x % BK : x / BN;
-      const int gn = n0 + nn, gk = k0 + kk;
-      float v = 0.f;
-      if (gn < N && gk < kend) v = transB ? B[(long long)gn * ldb + gk] : B[(long long)gk * ldb + gn];
-      Bt[nn][kk] = __float2bfloat16_rn(v);
-    }
+    store_a<VA>(ra, As, transA, tid);
+    store_b<VB>(rb, Bt, transB, tid);
     __syncthreads();
+    if (k0 + BK < kend) {  // the next tile's loads overlap this tile's products
+      load_a<VA>(ra, A, lda, transA, M, m0, k0 + BK, kend, tid);
+      load_b<VB>(rb, B, ldb, transB, N, n0, k0 + BK, kend, tid);
+    }
 #pragma unroll
     for (int ks = 0; ks < BK; ks += 16) {
       const int r = warp * 16 + g;
@@ -113,21 +269,127 @@ __global__ void __launch_bounds__(THREADS) gemm_bf16_kernel(const float* __restr
 #pragma unroll
   for (int j = 0; j < 4; ++j)
 #pragma unroll
-    for (int h = 0; h < 4; ++h) {
-      const int m = m0 + warp * 16 + g + (h >= 2 ? 8 : 0);
-      const int n = n0 + j * 8 + tg * 2 + (h & 1);
+    for (int hp = 0; hp < 2; ++hp) {  // row g (hp = 0) or g + 8, columns n, n + 1
+      const int m = m0 + warp * 16 + g + 8 * hp;
+      const int n = n0 + j * 8 + tg * 2;
       if (m >= M || n >= N) continue;
+      float v0 = alpha * acc[j][2 * hp], v1 = alpha * acc[j][2 * hp + 1];
       float* c = C + (long long)m * ldc + n;
-      float v = alpha * acc[j][h];
+      const bool two = n + 1 < N;
       if (splits > 1) {
-        atomicAdd(c, v);
+        atomicAdd(c, v0);
+        if (two) atomicAdd(c + 1, v1);
+        continue;
+      }
+      if (VC && two) {
+        if (beta != 0.f) {
+          const float2 o = *reinterpret_cast<const float2*>(c);
+          v0 += beta * o.x;
+          v1 += beta * o.y;
+        }
+        if (bias) {
+          v0 += bias[n];
+          v1 += bias[n + 1];
+        }
+        if (pre) *reinterpret_cast<float2*>(pre + (long long)m * ldc + n) = make_float2(v0, v1);
+        *reinterpret_cast<float2*>(c) = act == 1 ? make_float2(gelu(v0), gelu(v1)) : make_float2(v0, v1);
       } else {
-        if (beta != 0.f) v += beta * *c;
-        if (bias) v += bias[n];
-        if (pre) pre[(long long)m * ldc + n] = v;
-        *c = act == 1 ? gelu(v) : v;
+        for (int h = 0; h < (two ? 2 : 1); ++h) {
+          float v = h ? v1 : v0;
+          if (beta != 0.f) v += beta * c[h];
+          if (bias) v += bias[n + h];
+          if (pre) pre[(long long)m * ldc + n + h] = v;
+          c[h] = act == 1 ? gelu(v) : v;
+        }
       }
     }
+}
+
+// Transform along one axis of pencils (the innermost spatial axis, channels
+// contiguous): basis [L][m] in shared memory, FP32 on the CUDA cores. A
+// thread takes one channel of PP consecutive pencils, so that every basis
+// value it reads from shared memory serves PP products. expand = 0
+// contracts, in [P][L][C] -> out [P][m][C], out[k] = sum_z basis[z][k] in[z];
+// expand = 1 expands, in [P][m][C] -> out [P][L][C],
+// v = sum_k basis[z][k] in[k] + beta out[z], pre[z] = v (if set),
+// out[z] = act ? gelu(v) : v. Both read and write each value of the long
+// side once: bound by HBM, not by arithmetic.
+constexpr int kMaxModes = 16;
+template <int MM, int PP>
+__global__ void __launch_bounds__(256) axis_transform_kernel(const float* __restrict__ basis, int L, int m,
+                                                            const float* __restrict__ in, float* __restrict__ out,
+                                                            long long P, int C, int expand, float beta,
+                                                            float* __restrict__ pre, int act) {
+  extern __shared__ float phi[];  // [L][m]
+  for (int x = threadIdx.x; x < L * m; x += blockDim.x) phi[x] = basis[x];
+  __syncthreads();
+  const long long PQ = (P + PP - 1) / PP;  // pencil quads
+  const long long n = PQ * C;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long p0 = (i / C) * PP;
+    const int c = int(i % C);
+    const int np = P - p0 < PP ? int(P - p0) : PP;  // pencils of this thread (the last quad may be short)
+    if (!expand) {
+      float acc[PP][MM];
+#pragma unroll
+      for (int q = 0; q < PP; ++q)
+#pragma unroll
+        for (int k = 0; k < MM; ++k) acc[q][k] = 0.f;
+      const float* src = in + p0 * L * C + c;
+#pragma unroll 4
+      for (int z = 0; z < L; ++z) {
+        float u[PP];
+#pragma unroll
+        for (int q = 0; q < PP; ++q) u[q] = q < np ? src[((long long)q * L + z) * C] : 0.f;
+#pragma unroll
+        for (int k = 0; k < MM; ++k) {
+          if (k < m) {
+            const float w = phi[z * m + k];
+#pragma unroll
+            for (int q = 0; q < PP; ++q) acc[q][k] += w * u[q];
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < PP; ++q) {
+        if (q >= np) break;
+        float* dst = out + ((p0 + q) * m) * C + c;
+#pragma unroll
+        for (int k = 0; k < MM; ++k)
+          if (k < m) dst[(long long)k * C] = acc[q][k];
+      }
+    } else {
+      float t[PP][MM];
+#pragma unroll
+      for (int q = 0; q < PP; ++q)
+#pragma unroll
+        for (int k = 0; k < MM; ++k) t[q][k] = (q < np && k < m) ? in[((p0 + q) * m + k) * C + c] : 0.f;
+      float* dst = out + p0 * L * C + c;
+      float* pd = pre ? pre + p0 * L * C + c : nullptr;
+#pragma unroll 2
+      for (int z = 0; z < L; ++z) {
+        float v[PP];
+#pragma unroll
+        for (int q = 0; q < PP; ++q) v[q] = (beta != 0.f && q < np) ? beta * dst[((long long)q * L + z) * C] : 0.f;
+#pragma unroll
+        for (int k = 0; k < MM; ++k) {
+          if (k < m) {
+            const float w = phi[z * m + k];
+#pragma unroll
+            for (int q = 0; q < PP; ++q) v[q] += w * t[q][k];
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < PP; ++q) {
+          if (q < np) {
+            const long long o = ((long long)q * L + z) * C;
+            if (pd) pd[o] = v[q];
+            dst[o] = act == 1 ? gelu(v[q]) : v[q];
+          }
+        }
+      }
+    }
+  }
 }
 
 __global__ void gelu_backward_kernel(const float* __restrict__ pre, float* __restrict__ g, long long n) {
@@ -267,8 +529,46 @@ bbw_status bbw_nn_gemm(int M, int N, int K, const float* A, int lda, long long s
   if (M == 0 || N == 0) return BBW_OK;
   const dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch * splits);
   if (grid.y > 65535) return nn_fail(BBW_ERR_ARG, "M beyond the grid limit");
-  gemm_bf16_kernel<<<grid, THREADS, 0, static_cast<cudaStream_t>(stream)>>>(
-      A, B, C, bias, pre, M, N, K, lda, ldb, ldc, strideA, strideB, strideC, transA, transB, alpha, beta, act, splits);
+  // vector paths: the operand's rows (along its contiguous dimension) start on 16 bytes
+  auto al = [](const void* p, unsigned a) { return reinterpret_cast<uintptr_t>(p) % a == 0; };
+  const bool va = lda % 4 == 0 && strideA % 4 == 0 && al(A, 16);
+  const bool vb = ldb % 4 == 0 && strideB % 4 == 0 && al(B, 16);
+  const bool vc = ldc % 2 == 0 && strideC % 2 == 0 && al(C, 8) && (!pre || al(pre, 8));
+  auto launch = [&](auto kern) {
+    kern<<<grid, THREADS, 0, static_cast<cudaStream_t>(stream)>>>(A, B, C, bias, pre, M, N, K, lda, ldb, ldc, strideA,
+                                                                   strideB, strideC, transA, transB, alpha, beta,
+                                                                   act, splits);
+  };
+  if (va && vb)
+    vc ? launch(gemm_bf16_kernel<true, true, true>) : launch(gemm_bf16_kernel<true, true, false>);
+  else if (va)
+    vc ? launch(gemm_bf16_kernel<true, false, true>) : launch(gemm_bf16_kernel<true, false, false>);
+  else if (vb)
+    vc ? launch(gemm_bf16_kernel<false, true, true>) : launch(gemm_bf16_kernel<false, true, false>);
+  else
+    vc ? launch(gemm_bf16_kernel<false, false, true>) : launch(gemm_bf16_kernel<false, false, false>);
+  NN_CUDA(cudaGetLastError());
+  return BBW_OK;
+}
+
+bbw_status bbw_nn_axis_transform(const float* basis, int L, int m, const float* in, float* out, long long pencils,
+                                 int C, int expand, float beta, float* pre, int act, void* stream) {
+  if (L < 1 || m < 1 || m > kMaxModes || C < 1 || pencils < 0 || (expand != 0 && expand != 1) ||
+      (act != 0 && act != 1) || !basis || !in || !out || (!expand && (pre || act || beta != 0.f)))
+    return nn_fail(BBW_ERR_ARG, "bad axis-transform arguments");
+  if ((long long)L * m * sizeof(float) > 48 * 1024) return nn_fail(BBW_ERR_ARG, "axis-transform basis beyond 48 KB");
+  if (pencils == 0) return BBW_OK;
+  const size_t shm = size_t(L) * m * sizeof(float);
+  auto launch = [&](auto kern, int pp) {
+    const long long n = (pencils + pp - 1) / pp * C;
+    const int blocks = int(std::min<long long>((n + 255) / 256, 152LL * 16));
+    kern<<<blocks, 256, shm, static_cast<cudaStream_t>(stream)>>>(basis, L, m, in, out, pencils, C, expand, beta, pre,
+                                                                   act);
+  };
+  if (m <= 8)
+    launch(axis_transform_kernel<8, 4>, 4);
+  else
+    launch(axis_transform_kernel<16, 2>, 2);
   NN_CUDA(cudaGetLastError());
   return BBW_OK;
 }

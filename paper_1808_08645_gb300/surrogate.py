@@ -7,14 +7,16 @@ dense layers to the trace samples. It is trained on runs of this library's
 BBWADG solver, which also judges its error on held-out runs and is its
 fallback (``Surrogate.predict``).
 
-Every contraction, forward and backward, is a call of ``bbw_nn_gemm`` (BF16
-tensor cores, FP32 accumulation); GELU backward, bias gradients, the
-receiver gather and its transpose, the loss and Adam are the library's other
-``bbw_nn_*`` kernels. torch tensors only hold device memory; this module is
-argument marshalling and the order of the calls. The spectral transform of
-one layer is separable: three batched GEMMs per direction (z, y, x) with the
-truncated DCT-II matrices, one batched GEMM over the modes for the mode
-weights, three GEMMs back.
+The contractions, forward and backward, are calls of ``bbw_nn_gemm`` (BF16
+tensor cores, FP32 accumulation), except the transforms along z, the
+innermost axis: they touch every grid value for a 64 -> 6 contraction and
+run as FP32 pencil kernels (``bbw_nn_axis_transform``), bound by HBM. GELU
+backward, bias gradients, the receiver gather and its transpose, the loss
+and Adam are the library's other ``bbw_nn_*`` kernels. torch tensors only
+hold device memory; this module is argument marshalling and the order of
+the calls. The spectral transform of one layer is separable: one transform
+per direction (z, y, x) with the truncated DCT-II matrices, one batched GEMM
+over the modes for the mode weights, three transforms back.
 
 Layouts: fields [B, X, Y, Z, C] (C fastest) viewed as a [B X Y Z, C] matrix;
 modes [B, mx, my, mz, C]; receiver features [B, R, C]; traces [B, R, T].
@@ -71,8 +73,15 @@ def gemm(M, N, K, A, lda, sA, tA, Bm, ldb, sB, tB, Cm, ldc, sC, batch=1, alpha=1
              "bbw_nn_gemm")
 
 
+def axis(basis, L, m, x, out, pencils, C, expand=0, beta=0.0, pre=None, act=0, stream=None):
+    """bbw_nn_axis_transform: along the innermost spatial axis (FP32 pencils)."""
+    B._check(B.lib().bbw_nn_axis_transform(basis.data_ptr(), L, m, x.data_ptr(), out.data_ptr(), pencils, C, expand,
+                                           beta, _ptr(pre), act, stream), "bbw_nn_axis_transform")
+
+
 def _splits(k: int) -> int:
-    return int(min(1024, max(1, k // 8192)))
+    """K-splits of a weight-gradient GEMM: about 2048 rows per thread block."""
+    return int(min(1024, max(1, k // 2048)))
 
 
 class Net:
@@ -128,7 +137,7 @@ class Net:
         s3 = torch.empty(nb * nm * C, **e)
         t3 = torch.empty(nb * nm * C, **e)
         # forward transform z, y, x: S = Phi^T u along each axis
-        gemm(mz, C, G, Pz, mz, 0, 1, u, C, G * C, 0, s1, C, mz * C, batch=nb * G * G)
+        axis(Pz, G, mz, u, s1, nb * G * G, C)
         gemm(my, mz * C, G, Py, my, 0, 1, s1, mz * C, G * mz * C, 0, s2, mz * C, my * mz * C, batch=nb * G)
         gemm(mx, my * mz * C, G, Px, mx, 0, 1, s2, my * mz * C, G * my * mz * C, 0, s3, my * mz * C,
              mx * my * mz * C, batch=nb)
@@ -141,7 +150,7 @@ class Net:
         gemm(G, my * mz * C, mx, Px, mx, 0, 0, t3, my * mz * C, nm * C, 0, t2, my * mz * C, G * my * mz * C,
              batch=nb)
         gemm(G, mz * C, my, Py, my, 0, 0, t2, mz * C, my * mz * C, 0, t1, mz * C, G * mz * C, batch=nb * G)
-        gemm(G, C, mz, Pz, mz, 0, 0, t1, C, mz * C, 0, out, C, G * C, batch=nb * G * G, beta=1.0, pre=pre, act=1)
+        axis(Pz, G, mz, t1, out, nb * G * G, C, expand=1, beta=1.0, pre=pre, act=1)
         cache[f"s3_{l}"] = s3
 
     def forward(self, x, cache: dict | None = None):
@@ -219,7 +228,7 @@ class Net:
             dt1 = torch.empty(nb * G * G * mz * C, **e)
             dt2 = torch.empty(nb * G * my * mz * C, **e)
             dt3 = torch.empty(nb * nm * C, **e)
-            gemm(mz, C, G, Pz, mz, 0, 1, dpre, C, G * C, 0, dt1, C, mz * C, batch=nb * G * G)
+            axis(Pz, G, mz, dpre, dt1, nb * G * G, C)
             gemm(my, mz * C, G, Py, my, 0, 1, dt1, mz * C, G * mz * C, 0, dt2, mz * C, my * mz * C, batch=nb * G)
             gemm(mx, my * mz * C, G, Px, mx, 0, 1, dt2, my * mz * C, G * my * mz * C, 0, dt3, my * mz * C,
                  nm * C, batch=nb)
@@ -232,7 +241,7 @@ class Net:
             gemm(G, my * mz * C, mx, Px, mx, 0, 0, ds3, my * mz * C, nm * C, 0, ds2, my * mz * C,
                  G * my * mz * C, batch=nb)
             gemm(G, mz * C, my, Py, my, 0, 0, ds2, mz * C, my * mz * C, 0, ds1, mz * C, G * mz * C, batch=nb * G)
-            gemm(G, C, mz, Pz, mz, 0, 0, ds1, C, mz * C, 0, dprev, C, G * C, batch=nb * G * G, beta=1.0)
+            axis(Pz, G, mz, ds1, dprev, nb * G * G, C, expand=1, beta=1.0)
             du = dprev
         gemm(cfg["cin"], C, P, cache["x"], cfg["cin"], 0, 1, du, C, 0, 0, self.g["W0"], C, 0, splits=_splits(P))
         self._bias(du, self.g["b0"], P, C)

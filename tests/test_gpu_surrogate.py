@@ -53,6 +53,60 @@ def test_gemm_bf16_against_numpy(tA, tB):
         assert rel_l2(got, want) < 1e-2
 
 
+@pytest.mark.parametrize("tA,tB", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_gemm_vector_paths_with_ragged_edges(tA, tB):
+    """Operands padded to leading dimensions that are multiples of 4 floats
+    (the 16-byte load path) while M, N, K are not multiples of the tile or of
+    4: partial quads at every edge, an odd N for the scalar store path, and
+    split-K."""
+    from paper_1808_08645_gb300 import surrogate as S
+    rng = np.random.default_rng(10 + tA * 2 + tB)
+    for M, N, K, batch, splits in [(70, 44, 38, 2, 1), (67, 45, 61, 1, 1), (33, 30, 2050, 1, 5)]:
+        pm, pn, pk = -(-M // 4) * 4 + 4, -(-N // 4) * 4 + 4, -(-K // 4) * 4 + 4  # padded leading dims
+        Ap = rng.standard_normal((batch, pk, pm) if tA else (batch, pm, pk))
+        Bp = rng.standard_normal((batch, pn, pk) if tB else (batch, pk, pn))
+        A = Ap[:, :K, :M] if tA else Ap[:, :M, :K]
+        Bm = Bp[:, :N, :K] if tB else Bp[:, :K, :N]
+        rA = torch.tensor(A, dtype=torch.float32).bfloat16().double().numpy()
+        rB = torch.tensor(Bm, dtype=torch.float32).bfloat16().double().numpy()
+        want = np.einsum("bmk,bkn->bmn", rA.transpose(0, 2, 1) if tA else rA, rB.transpose(0, 2, 1) if tB else rB)
+        dA = torch.tensor(Ap, dtype=torch.float32, device="cuda")
+        dB = torch.tensor(Bp, dtype=torch.float32, device="cuda")
+        ldc = N + (N % 2)
+        dC = torch.zeros((batch, M, ldc), dtype=torch.float32, device="cuda")
+        S.gemm(M, N, K, dA, Ap.shape[2], Ap[0].size, tA, dB, Bp.shape[2], Bp[0].size, tB, dC, ldc, M * ldc,
+               batch=batch, splits=splits)
+        got = dC.double().cpu().numpy()[:, :, :N]
+        assert rel_l2(got, want) < 1e-5, (M, N, K)
+
+
+def test_axis_transform_against_numpy():
+    """bbw_nn_axis_transform: contraction and expansion along the innermost
+    axis with beta, the pre-activation copy and GELU, FP32."""
+    from math import erf
+
+    from paper_1808_08645_gb300 import surrogate as S
+    rng = np.random.default_rng(12)
+    f32 = dict(dtype=torch.float32, device="cuda")
+    for P, L, m, C in [(37, 64, 6, 32), (5, 9, 16, 3), (1, 1, 1, 1)]:
+        basis = rng.standard_normal((L, m))
+        x = rng.standard_normal((P, L, C))
+        want = np.einsum("zk,pzc->pkc", basis, x)
+        out = torch.full((P, m, C), float("nan"), **f32)
+        S.axis(torch.tensor(basis, **f32), L, m, torch.tensor(x, **f32), out, P, C)
+        assert np.allclose(out.double().cpu().numpy(), want, rtol=1e-5, atol=1e-5 * np.abs(want).max())
+        t = rng.standard_normal((P, m, C))
+        o0 = rng.standard_normal((P, L, C))
+        v = np.einsum("zk,pkc->pzc", basis, t) + 0.5 * o0
+        o = torch.tensor(o0, **f32)
+        pre = torch.empty_like(o)
+        S.axis(torch.tensor(basis, **f32), L, m, torch.tensor(t, **f32), o, P, C, expand=1, beta=0.5, pre=pre, act=1)
+        gelu = np.vectorize(lambda a: 0.5 * a * (1.0 + erf(a / np.sqrt(2.0))))
+        tol = 1e-5 * max(1.0, np.abs(v).max())
+        assert np.allclose(pre.double().cpu().numpy(), v, rtol=1e-5, atol=tol)
+        assert np.allclose(o.double().cpu().numpy(), gelu(v), rtol=1e-5, atol=tol)
+
+
 def test_forward_and_gradients_match_the_reference_network():
     from paper_1808_08645_gb300 import surrogate as S
     cfg = _cfg()
