@@ -366,25 +366,36 @@ __global__ void __launch_bounds__(256) axis_transform_kernel(const float* __rest
         for (int k = 0; k < MM; ++k) t[q][k] = (q < np && k < m) ? in[((p0 + q) * m + k) * C + c] : 0.f;
       float* dst = out + p0 * L * C + c;
       float* pd = pre ? pre + p0 * L * C + c : nullptr;
-#pragma unroll 2
-      for (int z = 0; z < L; ++z) {
-        float v[PP];
+      constexpr int ZC = 8;  // z values per chunk: all of a chunk's loads are issued before its stores
+      for (int z0 = 0; z0 < L; z0 += ZC) {
+        float o[ZC][PP];
 #pragma unroll
-        for (int q = 0; q < PP; ++q) v[q] = (beta != 0.f && q < np) ? beta * dst[((long long)q * L + z) * C] : 0.f;
+        for (int zz = 0; zz < ZC; ++zz)
 #pragma unroll
-        for (int k = 0; k < MM; ++k) {
-          if (k < m) {
-            const float w = phi[z * m + k];
+          for (int q = 0; q < PP; ++q)
+            o[zz][q] = (beta != 0.f && q < np && z0 + zz < L) ? dst[((long long)q * L + z0 + zz) * C] : 0.f;
 #pragma unroll
-            for (int q = 0; q < PP; ++q) v[q] += w * t[q][k];
+        for (int zz = 0; zz < ZC; ++zz) {
+          const int z = z0 + zz;
+          if (z >= L) break;
+          float v[PP];
+#pragma unroll
+          for (int q = 0; q < PP; ++q) v[q] = beta != 0.f ? beta * o[zz][q] : 0.f;
+#pragma unroll
+          for (int k = 0; k < MM; ++k) {
+            if (k < m) {
+              const float w = phi[z * m + k];
+#pragma unroll
+              for (int q = 0; q < PP; ++q) v[q] += w * t[q][k];
+            }
           }
-        }
 #pragma unroll
-        for (int q = 0; q < PP; ++q) {
-          if (q < np) {
-            const long long o = ((long long)q * L + z) * C;
-            if (pd) pd[o] = v[q];
-            dst[o] = act == 1 ? gelu(v[q]) : v[q];
+          for (int q = 0; q < PP; ++q) {
+            if (q < np) {
+              const long long off = ((long long)q * L + z) * C;
+              if (pd) pd[off] = v[q];
+              dst[off] = act == 1 ? gelu(v[q]) : v[q];
+            }
           }
         }
       }
