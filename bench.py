@@ -815,7 +815,7 @@ def _meta_rows(meta: dict, n: int) -> dict:
 def run_surrogate(args):
     """The neural-operator surrogate: BBWADG runs generate the training and
     held-out data, the network is trained by the library's kernels, and its
-    trace error on held-out runs (BBWADG as the judge) and its inference time
+    trace error on held-out runs (measured against BBWADG) and its inference time
     are reported against plain BBWADG."""
     import torch
 
@@ -890,7 +890,7 @@ def run_surrogate(args):
     t_nn_e2e = (time.perf_counter() - t) / 8
     h2d = xh.numel() * 4 / 8
     d2h = out8.numel() * 4 / 8
-    # the judge and fallback: a run outside the training box goes to BBWADG
+    # the fallback: a run outside the training box goes to BBWADG
     c2min = float(X[..., 0].min()) * 0.75 + 1.25
     c2max = float(X[..., 0].max()) * 0.75 + 1.25
     sur = S.Surrogate(net, dcfg, scale, float(np.quantile(err, 0.95)), (c2min, c2max), meta["dt"])

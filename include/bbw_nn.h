@@ -2,7 +2,7 @@
  * bbw_nn.h -- C ABI of the neural-operator surrogate's GPU kernels
  * (libbbwadg.so). The paper has no counterpart: the surrogate is a learned
  * map from a c^2 field and a source position to receiver traces, trained on
- * runs of this library's BBWADG solver, which also judges its error and is its
+ * runs of this library's BBWADG solver, which also measures its error and is its
  * fallback. The network is composed from these calls (binding: surrogate.py).
  *
  * All pointers are caller-owned device memory (FP32 unless stated); every call

@@ -4,7 +4,7 @@ The learned part (the paper has none): a Fourier-type neural operator on a
 G^3 grid (G = 64, width 32, four spectral layers in a truncated orthonormal
 cosine basis), a decoder that reads the top layer at the receivers, and two
 dense layers to the trace samples. It is trained on runs of this library's
-BBWADG solver, which also judges its error on held-out runs and is its
+BBWADG solver, which also measures its error on held-out runs and is its
 fallback (``Surrogate.predict``).
 
 The contractions, forward and backward, are calls of ``bbw_nn_gemm`` (BF16
@@ -442,7 +442,7 @@ def relative_errors(pred, Y) -> np.ndarray:
 
 
 class Surrogate:
-    """The trained network with BBWADG as its judge and fallback.
+    """The trained network with BBWADG as its error reference and fallback.
 
     ``predict(run, tol)`` returns (traces [R, T], "surrogate" | "bbwadg", err)
     where err is the held-out error quantile the surrogate is trusted to: the

@@ -217,7 +217,7 @@ def test_training_follows_the_reference_adam_trajectory():
     assert got[-1] < 0.25 * got[0]
 
 
-def test_small_pipeline_generate_train_judge_and_fall_back():
+def test_small_pipeline_generate_train_calibrate_and_fall_back():
     """A reduced surrogate workload end to end: BBWADG runs make the data, the
     network fits its training runs, held-out errors are finite, and runs
     outside the training box (or asked for a tolerance below the calibrated
