@@ -177,3 +177,29 @@ def test_elastic_argument_and_mesh_errors_need_no_device():
     assert L.bbw_elastic_get_time(None, None, None) == -1
     assert L.bbw_elastic_info(None, None, None, None, None, None, None) == -1
     L.bbw_elastic_destroy(None)  # no-op
+
+
+def test_surrogate_and_batch_argument_errors_need_no_device():
+    """The bbw_nn_* calls and the per-instance batch calls validate their
+    arguments on the host and return BBW_ERR_ARG (-1) before any device work."""
+    L = B.lib()
+    p = 4096  # a dummy non-NULL address: never dereferenced on these paths
+    # GEMM: negative sizes, NULL matrices, split-K with an epilogue, batch x splits beyond the grid
+    assert L.bbw_nn_gemm(-1, 4, 4, p, 4, 0, 0, p, 4, 0, 0, p, 4, 0, 1, 1.0, 0.0, None, None, 0, 1, None) == -1
+    assert L.bbw_nn_gemm(4, 4, 4, None, 4, 0, 0, p, 4, 0, 0, p, 4, 0, 1, 1.0, 0.0, None, None, 0, 1, None) == -1
+    assert L.bbw_nn_gemm(4, 4, 4, p, 4, 0, 0, p, 4, 0, 0, p, 4, 0, 1, 1.0, 1.0, None, None, 0, 2, None) == -1
+    assert L.bbw_nn_gemm(4, 4, 4, p, 4, 0, 0, p, 4, 0, 0, p, 4, 0, 1, 1.0, 0.0, None, None, 2, 1, None) == -1
+    assert L.bbw_nn_gemm(4, 4, 4, p, 4, 0, 0, p, 4, 0, 0, p, 4, 0, 1000, 1.0, 0.0, None, None, 0, 100, None) == -1
+    # transforms: modes beyond 16, a contraction with an epilogue
+    assert L.bbw_nn_axis_transform(p, 64, 17, p, p + 64, 1, 32, 0, 0.0, None, 0, None) == -1
+    assert L.bbw_nn_axis_transform(p, 64, 6, p, p + 64, 1, 32, 0, 1.0, None, 0, None) == -1
+    # shifts in place, bias gradients of width 0, receivers without arrays
+    assert L.bbw_nn_shift_traces(p, p, p, None, 3, 8, None) == -1
+    assert L.bbw_nn_bias_grad(p, p, 10, 0, None) == -1
+    assert L.bbw_nn_gather_receivers(p, p, None, p, p, 1, 8, 8, 8, 4, 2, 0, None) == -1
+    assert L.bbw_nn_mse(p, p, None, None, 10, None) == -1
+    assert L.bbw_nn_adam(p, p, p, p, 10, 0, 1e-3, 0.9, 0.999, 1e-8, None) == -1
+    # per-instance batch calls on a NULL batch
+    assert L.bbw_batch_set_instance_steps(None, None, None) == -1
+    assert L.bbw_batch_instance_time(None, 0, None, None) == -1
+    assert L.bbw_batch_member_cfl_dt(None, 0, 0.5, None) == -1
