@@ -576,8 +576,13 @@ bbw_status bbw_nn_axis_transform(const float* basis, int L, int m, const float* 
     kern<<<blocks, 256, shm, static_cast<cudaStream_t>(stream)>>>(basis, L, m, in, out, pencils, C, expand, beta, pre,
                                                                    act);
   };
-  if (m <= 8)
+  // contraction: four pencils per thread (the basis reads from shared memory
+  // bound it); expansion: two (its loads and stores bound it, and fewer
+  // registers keep more warps resident)
+  if (m <= 8 && !expand)
     launch(axis_transform_kernel<8, 4>, 4);
+  else if (m <= 8)
+    launch(axis_transform_kernel<8, 2>, 2);
   else
     launch(axis_transform_kernel<16, 2>, 2);
   NN_CUDA(cudaGetLastError());
