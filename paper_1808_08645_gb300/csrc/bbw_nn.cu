@@ -1,10 +1,11 @@
 // bbw_nn.cu -- kernels of the neural-operator surrogate (the learned part
 // that maps a c^2 field and a source position to receiver traces; the paper
-// has no counterpart). Every dense contraction of the network, forward and
-// backward, is one call of a batched GEMM on the BF16 tensor cores with FP32
-// accumulation (mma.sync m16n8k16); the rest are elementwise, gather and
-// optimiser kernels. Tensors are FP32 in memory; the GEMM rounds its operands
-// to BF16 when it stages them into shared memory.
+// has no counterpart). The dense contractions of the network, forward and
+// backward, are calls of a batched GEMM on the BF16 tensor cores with FP32
+// accumulation (mma.sync m16n8k16), except the transforms along the
+// innermost spatial axis, which run as FP32 pencil kernels; the rest are
+// elementwise, gather and optimiser kernels. Tensors are FP32 in memory; the
+// GEMM rounds its operands to BF16 when it stages them into shared memory.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -576,13 +577,8 @@ bbw_status bbw_nn_axis_transform(const float* basis, int L, int m, const float* 
     kern<<<blocks, 256, shm, static_cast<cudaStream_t>(stream)>>>(basis, L, m, in, out, pencils, C, expand, beta, pre,
                                                                    act);
   };
-  // contraction: four pencils per thread (the basis reads from shared memory
-  // bound it); expansion: two (its loads and stores bound it, and fewer
-  // registers keep more warps resident)
-  if (m <= 8 && !expand)
+  if (m <= 8)
     launch(axis_transform_kernel<8, 4>, 4);
-  else if (m <= 8)
-    launch(axis_transform_kernel<8, 2>, 2);
   else
     launch(axis_transform_kernel<16, 2>, 2);
   NN_CUDA(cudaGetLastError());
