@@ -130,10 +130,17 @@ class ClockSampler:
 # GPU arm
 
 def make_c2(M: int, vxyz, etov, c2_field):
-    """c^2 of the sweep workload: the L2 projection of the medium onto P^M per
-    element, every Bernstein coefficient checked positive (tools layer)."""
+    """(c2, recipe) of the sweep workload: the L2 projection of the medium onto
+    P^M per element, every Bernstein coefficient checked positive (tools
+    layer). On meshes where the projection of the layer jump undershoots
+    below zero (coarser than the default 32^3 hexes, e.g. 16^3), the medium
+    is sampled at the domain points instead, and the recipe says so."""
     from paper_1808_08645_gb300 import project
-    return project.project_c2(vxyz, etov, M, c2_field)
+    try:
+        return project.project_c2(vxyz, etov, M, c2_field), "L2 projection onto P^M"
+    except project.NonPositiveC2:
+        return (inputs.sample_at_domain_points(vxyz, etov, M, c2_field),
+                "sampled at the domain points (the L2 projection has a coefficient <= 0 on this mesh)")
 
 
 def make_workload(N: int, M: int, vxyz, etov, c2, pulse):
@@ -173,7 +180,7 @@ def run_gpu(args):
     pulse = inputs.gaussian_pulse()
     stream = torch.cuda.Stream()
     solvers, host_q0 = {}, {}
-    c2p = make_c2(M, vxyz, etov, field)
+    c2p, c2_recipe = make_c2(M, vxyz, etov, field)
     for N in Ns:
         c2, q0 = make_workload(N, M, vxyz, etov, c2p, pulse)
         s = B.Solver(vxyz, etov, N, M, B.F32, stream=stream.cuda_stream)
@@ -262,7 +269,7 @@ def run_gpu(args):
                 "workload": f"BBWADG acoustic LSRK4 stage sweep, {args.hexes}^3 hexes x 6 = {K} "
                             f"affine tets, N={Ns[0]}..{Ns[-1]}, M={M}, smooth random c2 in [0.5,2] "
                             "with planar layer jump, Ricker point source",
-                "mesh_elements": K, "Ns": Ns, "M": M,
+                "mesh_elements": K, "Ns": Ns, "M": M, "c2": c2_recipe,
                 "step": "one LSRK4 step (5 stages) per degree, interleaved by stage",
                 "l2": "inputs larger than L2: between two stages of one degree the other "
                       "degrees stream >= 6 GB through the 129 MB L2",
