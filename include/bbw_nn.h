@@ -30,7 +30,11 @@ extern "C" {
  * erf form). splits > 1 divides K among that many thread blocks that add their
  * partial products atomically into C (for very long K, e.g. weight gradients);
  * then bias, pre, act must be unset and beta 0 (C accumulates: clear it
- * first). Errors: BBW_ERR_ARG for bad sizes, NULL matrices or grid limits
+ * first; the order of the atomic additions, and so the last bits of C, may
+ * differ between calls). splits <= 1024. An operand whose rows start on 16
+ * bytes (leading dimension and stride multiples of 4 floats, 16-byte base)
+ * is loaded 16 bytes at a time, otherwise element by element (same result).
+ * Errors: BBW_ERR_ARG for bad sizes, NULL matrices or grid limits
  * (batch x splits <= 65535, M <= 64 x 65535).
  */
 bbw_status bbw_nn_gemm(int M, int N, int K, const float* A, int lda, long long strideA, int transA, const float* B,
